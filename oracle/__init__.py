@@ -1,0 +1,283 @@
+"""CPU oracle for GTS-Reuse meshlet compression -- TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, sequential restatement of Kuth et al., "Towards Practical
+Meshlet Compression" (VMV 2024), written in C (``oracle/*.c``, see
+``oracle.h`` for the format and the section each step follows) and wrapped
+here with ctypes.  Only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package.  It shares no code with
+the library in ``paper_2404_06359_gb300``; the two meet only in the seeded
+input generators (``paper_2404_06359_gb300.meshgen``) and in the blob format.
+
+Pinned by ``tests/test_oracle_*.py`` against textbook strip/fan definitions,
+brute-force enumeration, round trips to the input mesh, the paper's
+degenerate-per-restart ratio (Tab. 1), exact size accounting and the
+quantisation bounds of Sec. 4.4.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SOURCES = ["meshletize.c", "stripify.c", "encode.c", "decode.c"]
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` with gcc (no FP contraction, portable flags)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES] + [os.path.join(_HERE, "oracle.h")]
+    if not force and os.path.exists(_LIB_PATH):
+        if os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(s) for s in srcs):
+            return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-o", tmp] + [os.path.join(_HERE, s) for s in _SOURCES] + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Blob(C.Structure):
+    _fields_ = [("n_meshlets", C.c_uint32), ("n_grids", C.c_uint32),
+                ("payload_bytes", C.c_uint64), ("total_tris", C.c_uint64),
+                ("total_verts", C.c_uint64), ("restarts", C.c_uint64),
+                ("degenerates", C.c_uint64), ("conn_bits", C.c_uint64),
+                ("reuse_entries", C.c_uint64), ("desc", C.POINTER(C.c_uint8)),
+                ("payload", C.POINTER(C.c_uint8)), ("grids", C.POINTER(C.c_uint8)),
+                ("vmap", C.POINTER(C.c_uint32))]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB_PATH)
+            P = C.c_void_p
+            u32, u64 = C.c_uint32, C.c_uint64
+            L.orc_meshletize.argtypes = [u32, P, u32, P, P, u32, P, P, P, P]
+            L.orc_stripify.argtypes = [P, P, u32, P, P, P, P, P]
+            L.orc_encode.argtypes = [P, u32, P, P, P, u32, P, u32, P, u32, C.POINTER(C.POINTER(_Blob))]
+            L.orc_blob_free.argtypes = [C.POINTER(_Blob)]
+            L.orc_blob_free.restype = None
+            L.orc_dequant32.argtypes = [u32, C.c_float, C.c_float]
+            L.orc_dequant32.restype = C.c_float
+            L.orc_decode_meshlet.argtypes = [P, P, u64, P, u32, P, P, P]
+            L.orc_decode.argtypes = [P, u32, P, u64, P, u32, u32, u32, P, P, P, P]
+            L.orc_decode_cull.argtypes = [P, u32, P, u64, P, u32, u32, u32, P, P, P, P, P]
+            _lib = L
+        return _lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise OracleError(f"{what} failed with status {rc}")
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+# --------------------------------------------------------------------------
+# blob container (the oracle's own; the library has a separate one)
+# --------------------------------------------------------------------------
+@dataclass
+class Blob:
+    desc: np.ndarray      # uint8 [M, 32]
+    payload: np.ndarray   # uint8 [bytes]
+    grids: np.ndarray     # uint8 [G, 32]
+    stats: dict = field(default_factory=dict)
+
+    @property
+    def n_meshlets(self) -> int:
+        return int(self.desc.shape[0])
+
+    @property
+    def n_grids(self) -> int:
+        return int(self.grids.shape[0])
+
+    def fields(self) -> dict:
+        """Descriptor fields as numpy arrays (format in oracle.h)."""
+        w = self.desc.view(np.uint32).reshape(-1, 8)
+        return {
+            "off16": w[:, 0], "vertex_base": w[:, 1], "tri_base": w[:, 2],
+            "V": w[:, 3] & 0xFFFF, "Tp": w[:, 3] >> 16,
+            "w": w[:, 4] & 0xFF, "b": (w[:, 4] >> 8) & 0xFF, "grid": w[:, 4] >> 16,
+            "L": w[:, 5:8],
+        }
+
+    @property
+    def total_tris(self) -> int:
+        return int(self.fields()["Tp"].astype(np.int64).sum())
+
+    @property
+    def total_verts(self) -> int:
+        return int(self.fields()["V"].astype(np.int64).sum())
+
+
+def meshletize(tris: np.ndarray, n_verts: int, limits, tri_class: np.ndarray | None = None):
+    """Greedy meshlets; returns (mtri uint32[T], mstart uint32[M+1], n_grown)."""
+    tris = np.ascontiguousarray(tris, np.uint32)
+    lim = np.ascontiguousarray(np.asarray(limits, np.uint32).reshape(-1))
+    nt = tris.shape[0]
+    cls = None if tri_class is None else np.ascontiguousarray(tri_class, np.uint8)
+    mtri = np.zeros(nt, np.uint32)
+    mstart = np.zeros(nt + 1, np.uint32)
+    nm, ng = C.c_uint32(0), C.c_uint32(0)
+    _check(lib().orc_meshletize(n_verts, _p(tris), nt, _p(cls), _p(lim), lim.size // 2,
+                                _p(mtri), _p(mstart), C.byref(nm), C.byref(ng)), "orc_meshletize")
+    return mtri, mstart[: nm.value + 1].copy(), ng.value
+
+
+def stripify(tris: np.ndarray, ids: np.ndarray):
+    """Greedy strip of tris[ids]; returns (stream, flags, order, T', strips)."""
+    tris = np.ascontiguousarray(tris, np.uint32)
+    ids = np.ascontiguousarray(ids, np.uint32)
+    T = ids.size
+    stream = np.zeros(5 * T + 8, np.uint32)
+    flags = np.zeros(5 * T + 8, np.uint8)
+    order = np.zeros(T, np.uint32)
+    tp, ns = C.c_uint32(0), C.c_uint32(0)
+    _check(lib().orc_stripify(_p(tris), _p(ids), T, _p(stream), _p(flags), _p(order),
+                              C.byref(tp), C.byref(ns)), "orc_stripify")
+    return stream[: tp.value + 2].copy(), flags[: tp.value].copy(), order, tp.value, ns.value
+
+
+def encode(pos: np.ndarray, tris: np.ndarray, mtri: np.ndarray, mstart: np.ndarray,
+           bits, reuse_mode: int = 0, perm: np.ndarray | None = None, mesh_id: int = 0) -> Blob:
+    pos = np.ascontiguousarray(pos, np.float32)
+    tris = np.ascontiguousarray(tris, np.uint32)
+    nm = mstart.size - 1
+    bits = np.ascontiguousarray(np.broadcast_to(np.asarray(bits, np.uint8), (nm,)))
+    perm = None if perm is None else np.ascontiguousarray(perm, np.uint32)
+    out = C.POINTER(_Blob)()
+    _check(lib().orc_encode(_p(pos), pos.shape[0], _p(tris), _p(np.ascontiguousarray(mtri, np.uint32)),
+                            _p(np.ascontiguousarray(mstart, np.uint32)), nm, _p(bits), reuse_mode,
+                            _p(perm), mesh_id, C.byref(out)), "orc_encode")
+    b = out.contents
+    try:
+        desc = np.ctypeslib.as_array(b.desc, (b.n_meshlets * 32,)).copy().reshape(-1, 32) \
+            if b.n_meshlets else np.zeros((0, 32), np.uint8)
+        payload = np.ctypeslib.as_array(b.payload, (b.payload_bytes,)).copy() \
+            if b.payload_bytes else np.zeros(0, np.uint8)
+        grids = np.ctypeslib.as_array(b.grids, (b.n_grids * 32,)).copy().reshape(-1, 32) \
+            if b.n_grids else np.zeros((0, 32), np.uint8)
+        stats = {k: int(getattr(b, k)) for k in ("total_tris", "total_verts", "restarts",
+                                                  "degenerates", "conn_bits", "reuse_entries")}
+        stats["vmap"] = np.ctypeslib.as_array(b.vmap, (b.total_verts,)).copy() \
+            if b.total_verts else np.zeros(0, np.uint32)
+    finally:
+        lib().orc_blob_free(out)
+    return Blob(desc, payload, grids, stats)
+
+
+def encode_mesh(mesh, limits=(64, 126), bits=16, reuse_mode: int = 0, perm=None,
+                mesh_id: int = 0) -> Blob:
+    """meshletize + encode of a ``meshgen.Mesh``; ``bits`` scalar or callable(n)->array."""
+    lim = np.asarray(limits, np.uint32).reshape(-1)
+    mtri, mstart, ng = meshletize(mesh.tris, mesh.n_verts, lim, mesh.tri_class)
+    nm = mstart.size - 1
+    b = bits(nm) if callable(bits) else np.full(nm, bits, np.uint8)
+    p = perm(nm) if callable(perm) else perm
+    blob = encode(mesh.pos, mesh.tris, mtri, mstart, b, reuse_mode, p, mesh_id)
+    blob.stats["grown_meshlets"] = ng
+    blob.stats["input_tris"] = mesh.n_tris
+    blob.stats["mtri"], blob.stats["mstart"] = mtri, mstart
+    return blob
+
+
+def concat(blobs: list[Blob]) -> Blob:
+    """One batch from several single-mesh blobs (offsets rebased, mesh ids
+    renumbered in list order)."""
+    descs, pays, grids = [], [], []
+    off16 = vb = tb = gb = 0
+    stats = {k: 0 for k in ("total_tris", "total_verts", "restarts", "degenerates",
+                            "conn_bits", "reuse_entries", "input_tris")}
+    vmaps = []
+    for i, b in enumerate(blobs):
+        d = b.desc.copy().view(np.uint32).reshape(-1, 8)
+        d[:, 0] += off16
+        d[:, 1] += vb
+        d[:, 2] += tb
+        d[:, 4] = (d[:, 4] & 0xFFFF) | (((d[:, 4] >> 16) + gb) << 16)
+        g = b.grids.copy().view(np.uint32).reshape(-1, 8)
+        g[:, 7] = i
+        descs.append(d.view(np.uint8).reshape(-1, 32))
+        pays.append(b.payload)
+        grids.append(g.view(np.uint8).reshape(-1, 32))
+        f = b.fields()
+        off16 += b.payload.size // 16
+        vb += int(f["V"].astype(np.int64).sum())
+        tb += int(f["Tp"].astype(np.int64).sum())
+        gb += b.n_grids
+        for k in stats:
+            stats[k] += int(b.stats.get(k, 0))
+        if "vmap" in b.stats:
+            vmaps.append(b.stats["vmap"])
+    if len(vmaps) == len(blobs):
+        stats["vmap_per_mesh"] = vmaps
+    return Blob(np.concatenate(descs), np.concatenate(pays), np.concatenate(grids), stats)
+
+
+def dequant32(g: int, G: float, D: float) -> float:
+    return float(lib().orc_dequant32(int(g), float(np.float32(G)), float(np.float32(D))))
+
+
+def decode_meshlet(blob: Blob, m: int):
+    """(local uint8 [T',3], pos float32 [V,3], pos64 float64 [V,3]) of meshlet m."""
+    f = blob.fields()
+    tp, V = int(f["Tp"][m]), int(f["V"][m])
+    loc = np.zeros(3 * 256, np.uint8)
+    pos = np.zeros(3 * 256, np.float32)
+    pos64 = np.zeros(3 * 256, np.float64)
+    d = np.ascontiguousarray(blob.desc[m])
+    _check(lib().orc_decode_meshlet(_p(d), _p(blob.payload), blob.payload.size, _p(blob.grids),
+                                    blob.n_grids, _p(loc), _p(pos), _p(pos64)), "orc_decode_meshlet")
+    return loc[: 3 * tp].reshape(-1, 3), pos[: 3 * V].reshape(-1, 3), pos64[: 3 * V].reshape(-1, 3)
+
+
+def decode(blob: Blob, first: int = 0, count: int | None = None, want_pos64: bool = True):
+    """Whole-batch outputs: local uint8 [T'_total,3], global uint32 [T'_total,3],
+    pos float32 [V_total,3], pos64 float64 [V_total,3] (meshlets outside the
+    range are left zero)."""
+    if count is None:
+        count = blob.n_meshlets - first
+    T, V = blob.total_tris, blob.total_verts
+    loc = np.zeros(3 * T, np.uint8)
+    glob = np.zeros(3 * T, np.uint32)
+    pos = np.zeros(3 * V, np.float32)
+    pos64 = np.zeros(3 * V, np.float64) if want_pos64 else None
+    _check(lib().orc_decode(_p(blob.desc), blob.n_meshlets, _p(blob.payload), blob.payload.size,
+                            _p(blob.grids), blob.n_grids, first, count, _p(loc), _p(glob),
+                            _p(pos), _p(pos64)), "orc_decode")
+    return (loc.reshape(-1, 3), glob.reshape(-1, 3), pos.reshape(-1, 3),
+            None if pos64 is None else pos64.reshape(-1, 3))
+
+
+def decode_cull(blob: Blob, vp: np.ndarray, first: int = 0, count: int | None = None):
+    """(survivor triples uint32 [n,3] in meshlet order, pos float32 [V_total,3],
+    frustum pass flags uint8 [M])."""
+    if count is None:
+        count = blob.n_meshlets - first
+    T, V = blob.total_tris, blob.total_verts
+    out = np.zeros(3 * T + 3, np.uint32)
+    pos = np.zeros(3 * V, np.float32)
+    passed = np.zeros(blob.n_meshlets, np.uint8)
+    cnt = C.c_uint64(0)
+    vp = np.ascontiguousarray(np.asarray(vp, np.float32).reshape(16))
+    _check(lib().orc_decode_cull(_p(blob.desc), blob.n_meshlets, _p(blob.payload),
+                                 blob.payload.size, _p(blob.grids), blob.n_grids, first, count,
+                                 _p(vp), _p(out), C.byref(cnt), _p(pos), _p(passed)),
+           "orc_decode_cull")
+    return out[: 3 * cnt.value].reshape(-1, 3), pos.reshape(-1, 3), passed

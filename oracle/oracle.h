@@ -1,0 +1,127 @@
+/*
+ * CPU oracle for GTS-Reuse meshlet compression
+ * (Kuth et al., "Towards Practical Meshlet Compression", VMV 2024).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, sequential restatement of
+ * the method used to check the library.  Only the test suite, the smoke check
+ * and the benchmark's CPU-baseline leg may load it.  It shares no code,
+ * header or constant with the library: every format constant below is
+ * restated here on purpose.
+ *
+ * Pipeline (all host memory, plain C99, compiled with -ffp-contract=off):
+ *   orc_meshletize   greedy meshlet growth under (V~, T~) limits (Sec. 3),
+ *                    plus the split of meshlets whose strip, restarts
+ *                    included, exceeds T~ (Sec. 4.2, last paragraph).
+ *   orc_stripify     greedy generalized triangle strip of one meshlet with
+ *                    one L/R flag per triangle (Sec. 2) and restarts emulated
+ *                    by four degenerate triangles (Sec. 4.2).
+ *   orc_encode       first-appearance relabelling, increment flags and reuse
+ *                    buffer (Sec. 4.3), crack-free global-grid fixed-point
+ *                    positions (Sec. 4.4), packed into the blob format.
+ *   orc_decode_*     sequential strip walk (Sec. 2) -- deliberately NOT the
+ *                    parallel closed form the GPU uses (Sec. 4.2/4.3) -- and
+ *                    dequantisation to FP32 and FP64 (Sec. 4.4).
+ *   orc_decode_cull  the same decode followed by a frustum test per meshlet
+ *                    and a back-face/degenerate test per triangle.
+ *
+ * Blob format (little-endian):
+ *   descriptor, 32 B per meshlet:
+ *     u32 payload offset in 16-byte units, u32 vertex_base, u32 tri_base,
+ *     u16 V, u16 T' (triangles incl. degenerates), u8 reuse width w,
+ *     u8 position bits b, u16 grid id, u32 L[3] (meshlet minimum on the grid)
+ *   payload block per meshlet, u32 words, bits LSB-first, padded to 16 B:
+ *     ceil(T'/32) L/R words (bit k = 1: triangle k entered across the right
+ *     edge), ceil(T'/32) increment words (bit k = 1: new vertex),
+ *     ceil(R*w/32) reuse words, ceil(3*V*b/32) position words
+ *     (vertex v channel c at bit (3v+c)*b).  Bit 0 of both flag words is 0.
+ *   grid entry, 32 B: f32 G[3], u32 b, f32 Delta[3], u32 mesh id.
+ */
+#ifndef ORACLE_H
+#define ORACLE_H
+#include <stddef.h>
+#include <stdint.h>
+
+enum {
+  ORC_OK = 0,
+  ORC_ERR_ARG = 1,
+  ORC_ERR_LIMIT = 2,
+  ORC_ERR_CORRUPT = 3,
+  ORC_ERR_NOMEM = 5
+};
+
+/* Greedy meshletization.  Triangles are grouped into meshlets of at most
+ * limits[2c] vertices and limits[2c+1] triangles for class c = tri_class[t]
+ * (tri_class may be NULL: one class).  out_tri receives all triangle ids
+ * grouped by meshlet, out_start (n_tris + 1 entries) the group starts.
+ * Meshlets whose strip needs more than limits[2c+1] triangles once restart
+ * degenerates are added are split in halves of their strip order.
+ * *out_n_grown = meshlets before splitting. */
+int orc_meshletize(uint32_t n_verts, const uint32_t *tris, uint32_t n_tris,
+                   const uint8_t *tri_class, const uint32_t *limits,
+                   uint32_t n_classes, uint32_t *out_tri, uint32_t *out_start,
+                   uint32_t *out_n_meshlets, uint32_t *out_n_grown);
+
+/* Greedy strip of the T triangles tris[ids[i]] (i = list position).
+ * stream: T' + 2 global vertex ids; flags: T' entries (0 = L, 1 = R; entry 0
+ * is 0); strip_order: the T list positions in strip order.
+ * Capacity needed: stream 5*T, flags 5*T. */
+int orc_stripify(const uint32_t *tris, const uint32_t *ids, uint32_t T,
+                 uint32_t *stream, uint8_t *flags, uint32_t *strip_order,
+                 uint32_t *out_tp, uint32_t *out_strips);
+
+typedef struct {
+  uint32_t n_meshlets;
+  uint32_t n_grids;
+  uint64_t payload_bytes;
+  uint64_t total_tris;  /* sum of T' */
+  uint64_t total_verts; /* sum of V  */
+  uint64_t restarts;
+  uint64_t degenerates;
+  uint64_t conn_bits;   /* sum of 2 T' + w R */
+  uint64_t reuse_entries;
+  uint8_t *desc;
+  uint8_t *payload;
+  uint8_t *grids;
+  uint32_t *vmap; /* input vertex id of every decoded vertex (total_verts) */
+} orc_blob;
+
+/* Encode the meshlets (mtri/mstart as produced by orc_meshletize) of one mesh.
+ * bits[m]: position bits of meshlet m (1..32).  reuse_mode 0: w = 8,
+ * reuse_mode 1: w = ceil(log2 V).  perm (may be NULL): blob slot p holds
+ * meshlet perm[p].  mesh_id is written into the grid entries. */
+int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
+               const uint32_t *mtri, const uint32_t *mstart,
+               uint32_t n_meshlets, const uint8_t *bits, uint32_t reuse_mode,
+               const uint32_t *perm, uint32_t mesh_id, orc_blob **out);
+void orc_blob_free(orc_blob *b);
+
+/* FP32 dequantisation of a grid coordinate g (Sec. 4.4):
+ *   x = fmaf((float)(g & 0xFFF), D, fmaf((float)(g >> 12), D * 4096, G)). */
+float orc_dequant32(uint32_t g, float G, float D);
+
+/* Sequential decode of one meshlet (descriptor desc32) into
+ * local[3*T'] u8 indices, pos[3*V] FP32 and pos64[3*V] FP64 (may be NULL). */
+int orc_decode_meshlet(const uint8_t *desc32, const uint8_t *payload,
+                       uint64_t payload_bytes, const uint8_t *grids,
+                       uint32_t n_grids, uint8_t *local, float *pos,
+                       double *pos64);
+
+/* Decode meshlets [first, first + count) into whole-batch outputs placed at
+ * each meshlet's tri_base / vertex_base (any output may be NULL). */
+int orc_decode(const uint8_t *desc, uint32_t n_meshlets, const uint8_t *payload,
+               uint64_t payload_bytes, const uint8_t *grids, uint32_t n_grids,
+               uint32_t first, uint32_t count, uint8_t *local, uint32_t *global,
+               float *pos, double *pos64);
+
+/* Decode + cull meshlets [first, first + count).  vp: row-major 4x4 clip
+ * matrix.  Surviving triangles are appended to tri_out as global u32 triples
+ * (meshlet order, then triangle order); *count_io is the running count in
+ * triangles.  Positions are written only for meshlets that pass the frustum
+ * test; pass_out[m] (may be NULL) receives 1 for those. */
+int orc_decode_cull(const uint8_t *desc, uint32_t n_meshlets,
+                    const uint8_t *payload, uint64_t payload_bytes,
+                    const uint8_t *grids, uint32_t n_grids, uint32_t first,
+                    uint32_t count, const float *vp, uint32_t *tri_out,
+                    uint64_t *count_io, float *pos, uint8_t *pass_out);
+
+#endif
