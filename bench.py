@@ -1,0 +1,414 @@
+"""Benchmark: batched GTS-Reuse meshlet decode on GB300.
+
+Default workload (cfg2): 256 seeded UV-spheres/tori, ~16.2 M triangles,
+meshlets 64/126, 16-bit positions, 8-bit reuse indices, decoded to u8 local +
+u32 global indices + FP32 positions by one persistent launch replayed from a
+CUDA graph.  One step = one decode of the whole batch (inputs resident in
+HBM); L2 is flushed (256 MB write) between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 1|2|3|4]
+  python bench.py --impl reference ...   # the CPU oracle, same metric
+
+Prints one JSON line (rank 0).  Under torchrun each rank decodes its own
+seeded batch (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "decoded Gtps (bit-exact) & % of HBM roofline vs plain decode; p50/p99 latency"
+WORKLOADS = {
+    1: "cfg1: 64x64-quad jittered grid, 8,192 triangles, meshlets 64/126, b=16, w=8, "
+       "u8 local + f32 positions, plain one-launch decode",
+    2: "cfg2: 256 seeded UV-spheres/tori, T log-uniform 10k-200k (16.2M triangles), meshlets "
+       "64/126, b=16, w=8, u8 local + u32 global + f32 positions, one persistent launch (CUDA graph)",
+    3: "cfg3: 50M-triangle disc height field, 3 sectors at 64/126, 128/128, 256/256, w=ceil(log2 V), "
+       "b in {12,16,20} per meshlet, shuffled, u8 + u32 + f32, one persistent launch (CUDA graph)",
+    4: "cfg4: cfg2 generator grown to >=50M triangles, fused decode + frustum/back-face cull + "
+       "compaction, 64 camera poses, one CUDA graph",
+}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# DRAM bytes per launch of the decode kernel from one ncu capture, valid only
+# while the kernel sources hash to `sources`; scaled by decoded triangle slots.
+NCU_TRAFFIC = {}
+
+
+def _kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for p in ("paper_2404_06359_gb300/csrc/device/kernels.cu",
+              "paper_2404_06359_gb300/csrc/device/decode_warp.cuh"):
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        phys = device_index
+        if vis:
+            try:
+                phys = int(vis.split(",")[device_index])
+            except ValueError:
+                phys = device_index
+        self.cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                    "-i", str(phys), "-lms", "50"]
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except Exception:
+                self.proc.kill()
+            self.t.join(1)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _allreduce_max(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def build_workload(cfg: int, rank: int):
+    from paper_2404_06359_gb300 import workloads as W
+    if cfg == 1:
+        blob, meshes = W.cfg1()
+        return blob, meshes, None
+    if cfg == 2:
+        blob, meshes = W.cfg2(rank)
+        return blob, meshes, None
+    if cfg == 3:
+        blob, meshes = W.cfg3(rank)
+        return blob, meshes, None
+    if cfg == 4:
+        return W.cfg4(rank)
+    raise SystemExit(f"unknown config {cfg}")
+
+
+def cpu_oracle_baseline(blob, budget_s: float = 10.0):
+    """The oracle's sequential decode on a bounded prefix of the batch."""
+    import oracle as O
+    a = blob.arrays()
+    ob = O.Blob(a["desc"], a["payload"], a["grids"])
+    f = ob.fields()
+    n = ob.n_meshlets
+    lib = O.lib()
+    tl = np.zeros(3 * 256, np.uint8)
+    tp = np.zeros(3 * 256, np.float32)
+    import ctypes as C
+    t0 = time.perf_counter()
+    m = 0
+    tris = 0
+    desc = ob.desc
+    pay_p = ob.payload.ctypes.data_as(C.c_void_p)
+    grd_p = ob.grids.ctypes.data_as(C.c_void_p)
+    tl_p, tp_p = tl.ctypes.data_as(C.c_void_p), tp.ctypes.data_as(C.c_void_p)
+    while m < n and time.perf_counter() - t0 < budget_s:
+        end = min(n, m + 256)
+        for i in range(m, end):
+            d = desc[i]
+            rc = lib.orc_decode_meshlet(d.ctypes.data_as(C.c_void_p), pay_p, ob.payload.size, grd_p,
+                                        ob.n_grids, tl_p, tp_p, None)
+            if rc != 0:
+                raise RuntimeError("oracle decode failed")
+            t = tl[: 3 * int(f["Tp"][i])].reshape(-1, 3)
+            tris += int(((t[:, 0] != t[:, 1]) & (t[:, 1] != t[:, 2]) & (t[:, 0] != t[:, 2])).sum())
+        m = end
+    dt = time.perf_counter() - t0
+    return {"value": tris / dt / 1e9, "unit": "Gtps", "cores": 1, "kind": "oracle",
+            "sample": f"first {m} of {n} meshlets ({tris} input triangles) of the same batch, "
+                      f"sequential C decode + FP32 dequant, {dt:.1f} s, 1 thread"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    blob, meshes, _ = build_workload(args.config, 0)
+    per = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_baseline(blob, budget_s=max(1.0, args.ref_seconds / max(1, args.steps)))
+        if i >= args.warmup:
+            per.append(r["value"])
+    v = float(np.mean(per))
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gtps", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u32/f32", "data": "synthetic",
+           "config": {"workload": WORKLOADS[args.config]},
+           "cpu_baseline": {"value": v, "unit": "Gtps", "cores": 1, "kind": "oracle",
+                            "sample": r["sample"]},
+           "e2e": {"value": v, "unit": "Gtps", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+    from paper_2404_06359_gb300 import codec as mc
+    from paper_2404_06359_gb300 import workloads as W
+
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    t_build = time.time()
+    blob, meshes, vps = build_workload(args.config, rank)
+    t_build = time.time() - t_build
+    stats = blob.stats()
+    db = mc.DeviceBatch(blob, "cuda")
+    arrays = blob.arrays()
+    input_tris = stats["input_tris"]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    scratch = mc.new_scratch()
+    cull = args.config == 4
+    want_local = True
+    want_global = args.config != 1
+    out = db.outputs(want_local, want_global)
+    nbytes = W.algorithmic_bytes(stats, arrays["desc"], want_local, want_global)
+    extra = {}
+    with torch.cuda.stream(stream):
+        if cull:
+            T, V = stats["total_tris"], stats["total_verts"]
+            tri = torch.empty(3 * T + 3, dtype=torch.int32, device="cuda")
+            d_vps = torch.from_numpy(np.ascontiguousarray(vps, np.float32)).cuda()
+            counts = torch.zeros(len(vps), dtype=torch.int32, device="cuda")
+            graph = mc.mc_graph_capture_cull(db, d_vps, len(vps), tri, counts, out["pos"],
+                                             out["status"], scratch, None, stream)
+            launches_per_step = len(vps)
+            tune = None
+        elif args.config == 1:
+            graph = None
+            launches_per_step = 1
+            tune = {"warps_per_cta": 4}
+        else:
+            tune, tune_ms = mc.mc_autotune(db, out["local"], out["global"], out["pos"], out["status"],
+                                           scratch, stream)
+            graph = mc.mc_graph_capture_batch(db, out["local"], out["global"], out["pos"],
+                                              out["status"], scratch, None, stream)
+            launches_per_step = 1
+            extra["tuning"] = {"warps_per_cta": tune.warps_per_cta, "ctas_per_sm": tune.ctas_per_sm,
+                               "meshlets_per_grab": tune.meshlets_per_grab}
+
+        def step():
+            if graph is not None:
+                graph.launch(stream)
+            else:
+                mc.mc_decode_plain(db, 0, stats["n_meshlets"], out["local"],
+                                   out["global"] if want_global else None, out["pos"], out["status"],
+                                   tune, stream)
+
+        for _ in range(args.warmup):
+            step()
+            flush.zero_()
+        torch.cuda.synchronize()
+        _barrier(ws)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        n0 = mc.mc_launch_count()
+        with ClockSampler(local) as clk:
+            for e0, e1 in evs:
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                flush.zero_()
+            torch.cuda.synchronize()
+        launches = mc.mc_launch_count() - n0
+        _barrier(ws)
+        torch.cuda.synchronize()
+        times = np.array([e0.elapsed_time(e1) for e0, e1 in evs])  # ms
+        total_ms = _allreduce_max(float(times.sum()), ws)
+        status = int(out["status"].item())
+        assert status == 0, f"device status {status:#x}"
+
+        # plain one-launch-per-mesh decoder on the same batch (the baseline)
+        plain = None
+        if not cull and args.config != 1 and args.plain_steps > 0:
+            pt = []
+            for i in range(args.plain_steps + 2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for msh in db.meshes:
+                    mc.mc_decode_plain(db, msh["first_meshlet"], msh["n_meshlets"], out["local"],
+                                       out["global"], out["pos"], out["status"], None, stream)
+                e1.record(stream)
+                flush.zero_()
+                torch.cuda.synchronize()
+                if i >= 2:
+                    pt.append(e0.elapsed_time(e1))
+            pms = float(np.mean(pt))
+            plain = {"value": input_tris / (pms * 1e-3) / 1e9, "unit": "Gtps", "ms_per_step": pms,
+                     "launches_per_step": len(db.meshes)}
+
+        # end to end through the C ABI with host buffers (pinned), copies timed
+        e2e = None
+        if not cull and args.e2e_steps > 0:
+            T, V = stats["total_tris"], stats["total_verts"]
+            d_desc = torch.empty(32 * stats["n_meshlets"], dtype=torch.uint8, device="cuda")
+            d_pay = torch.empty(stats["payload_bytes"], dtype=torch.uint8, device="cuda")
+            d_grid = torch.empty(32 * stats["n_grids"], dtype=torch.uint8, device="cuda")
+            h_loc = torch.empty(3 * T, dtype=torch.uint8).pin_memory()
+            h_glob = torch.empty(3 * T, dtype=torch.int32).pin_memory() if want_global else None
+            h_pos = torch.empty(3 * V, dtype=torch.float32).pin_memory()
+            et = []
+            for i in range(args.e2e_steps + 2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                mc.mc_decode_batch_host(blob, d_desc, d_pay, d_grid, out["local"],
+                                        out["global"] if want_global else None, out["pos"],
+                                        out["status"], scratch, h_loc, h_glob, h_pos, tune, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if i >= 2:
+                    et.append(e0.elapsed_time(e1))
+            ems = _allreduce_max(float(np.mean(et)), ws)
+            e2e = {"value": ws * input_tris / (ems * 1e-3) / 1e9, "unit": "Gtps", "ms_per_step": ems,
+                   "h2d_bytes_per_step": int(32 * stats["n_meshlets"] + stats["payload_bytes"]
+                                             + 32 * stats["n_grids"]),
+                   "d2h_bytes_per_step": int(3 * T + (12 * T if want_global else 0) + 12 * V)}
+
+    ms_step = total_ms / args.steps
+    value = ws * input_tris * args.steps / (total_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    per_launch_s = (times.mean() * 1e-3) / launches_per_step
+    bytes_per_launch = nbytes["total"] if not cull else None
+    roof = None
+    if bytes_per_launch:
+        ach = bytes_per_launch / per_launch_s / 1e9
+        tr = NCU_TRAFFIC.get(_kernel_hash())
+        traffic = None
+        if tr and args.config in tr:
+            traffic = int(tr[args.config] * stats["total_tris"])
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": traffic,
+                "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS hbm_gbs)",
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "bytes_per_input_triangle": round(bytes_per_launch / input_tris, 2)}
+    else:
+        counts_np = counts.cpu().numpy()
+        extra["cull"] = {"kept_fraction_mean": float(counts_np.mean() / input_tris),
+                         "views": len(vps)}
+    res = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Gtps", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.config], "input_triangles": input_tris,
+                   "decoded_triangle_slots": stats["total_tris"], "vertices": stats["total_verts"],
+                   "meshlets": stats["n_meshlets"], "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"{ws} independent replica(s), no collective"},
+        "latency_ms": {"p50": round(float(np.percentile(times, 50)), 5),
+                       "p99": round(float(np.percentile(times, 99)), 5)},
+        "roofline": roof, "gpu_launches": int(launches), "clocks": clk.summary(),
+        "plain": plain, "e2e": e2e, "build_s": round(t_build, 1),
+    }
+    res.update(extra)
+    if rank == 0 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_oracle_baseline(blob, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

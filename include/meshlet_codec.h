@@ -1,0 +1,298 @@
+/*
+ * meshlet_codec.h -- C ABI of the GB300 GTS-Reuse meshlet codec.
+ *
+ * Implements the data-parallel decode of Kuth et al., "Towards Practical
+ * Meshlet Compression" (VMV 2024) on NVIDIA GB300 (sm_103a), plus the host
+ * preprocessing that produces its input.
+ *
+ *   host    mc_meshletize  split a triangle mesh into meshlets (Sec. 3)
+ *           mc_encode      generalized triangle strips with one L/R flag per
+ *                          triangle (Sec. 2, 4.2), index reuse packing
+ *                          (Sec. 4.3), crack-free fixed-point positions
+ *                          (Sec. 4.4)
+ *   device  mc_decode_*    parallel decode of many meshlets to u8 local and
+ *                          u32 global triangle indices and FP32 positions
+ *                          (Sec. 3, 4.2-4.4), optionally fused with culling.
+ *
+ * Conventions shared by every call:
+ *   - Host objects (mc_meshlets, mc_blob) are created and freed by the
+ *     library.  Device buffers are allocated by the caller and are never
+ *     freed or reallocated by the library.
+ *   - Device calls are asynchronous on the caller's CUDA stream (`stream` is
+ *     a cudaStream_t; NULL = legacy default stream) and never synchronise.
+ *   - Argument errors are returned synchronously (MC_ERR_INVALID_ARG,
+ *     MC_ERR_LIMIT); launch failures as MC_ERR_CUDA.  Errors found by a
+ *     kernel (corrupt stream, exceeded capacity) are OR-ed as bit masks
+ *     (1u << mc_status) into the caller's device status word *d_status,
+ *     which the caller reads after synchronising.  The kernels never trap.
+ *   - No call falls back to a CPU implementation.
+ *
+ * Blob format (little-endian; the device reads it as is):
+ *   descriptor, 32 bytes per meshlet (mc_desc below);
+ *   payload block per meshlet, u32 words, bits LSB-first, 16-byte aligned:
+ *     ceil(T'/32) L/R words     bit k = 1: triangle k is entered across the
+ *                               right edge (b,c) of triangle k-1, 0: left edge
+ *                               (c,a) (Sec. 2); bit 0 is 0
+ *     ceil(T'/32) increment words  bit k = 1: the strip entry of triangle k is
+ *                               a vertex not seen before (Sec. 4.3); bit 0 is 0
+ *     ceil(R*w/32) reuse words  R = T' - V + 2 entries of w bits (Sec. 4.3)
+ *     ceil(3*V*b/32) position words  vertex v channel c at bit (3v+c)*b
+ *   grid entry, 32 bytes (mc_grid below): FP32 origin G and step Delta of
+ *     the global quantisation grid of one mesh at one bit width (Sec. 4.4).
+ */
+#ifndef MESHLET_CODEC_H
+#define MESHLET_CODEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MC_OK = 0,
+  MC_ERR_INVALID_ARG = 1, /* bad pointer, size or parameter */
+  MC_ERR_LIMIT = 2,       /* a meshlet or grid coordinate exceeds the format */
+  MC_ERR_CORRUPT = 3,     /* the bitstream contradicts itself */
+  MC_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  MC_ERR_OOM = 5,         /* host allocation failed */
+  MC_ERR_TIMEOUT = 6      /* a bounded device wait gave up */
+} mc_status;
+
+/* Human-readable name of a status code (static storage). */
+const char *mc_status_string(mc_status s);
+
+/* Library version string (static storage). */
+const char *mc_version(void);
+
+/* ------------------------------------------------------------------ format */
+
+/* Per-meshlet descriptor, 32 bytes (Sec. 3: a meshlet stores the offset of
+ * its vertex block and of its index data).  tri_base / vertex_base place the
+ * meshlet's decoded triangles and vertices in the batch-wide outputs. */
+typedef struct {
+  uint32_t payload_off16; /* payload block offset, in 16-byte units */
+  uint32_t vertex_base;   /* first decoded vertex; global index = base + local */
+  uint32_t tri_base;      /* first decoded triangle (T' slots incl. degenerates) */
+  uint16_t n_verts;       /* V, 3..256 */
+  uint16_t n_tris;        /* T' = triangles incl. restart degenerates, 1..256 */
+  uint8_t reuse_bits;     /* w, 1..8, 2^w >= V */
+  uint8_t pos_bits;       /* b, 1..32 */
+  uint16_t grid;          /* index of the mc_grid entry */
+  uint32_t L[3];          /* meshlet minimum on the global grid (Sec. 4.4) */
+} mc_desc;
+
+/* Global quantisation grid (Sec. 4.4): x = G + g * Delta for grid coordinate
+ * g = L + q.  One entry per mesh and position bit width. */
+typedef struct {
+  float G[3];
+  uint32_t pos_bits;
+  float delta[3];
+  uint32_t mesh_id;
+} mc_grid;
+
+/* -------------------------------------------------------------------- host */
+
+typedef struct mc_meshlets mc_meshlets; /* opaque, library-owned */
+typedef struct mc_blob mc_blob;         /* opaque, library-owned */
+
+typedef struct {
+  uint32_t max_verts; /* V~, 3..256 (Sec. 3) */
+  uint32_t max_tris;  /* T~, 1..256; bounds T' including degenerates (Sec. 4.2) */
+} mc_limits;
+
+/* Split a triangle mesh into meshlets (Sec. 3) -- deterministic greedy growth
+ * from the lowest-index unassigned triangle, preferring frontier triangles
+ * that add no vertex, then the earliest to join the frontier -- and split
+ * every meshlet whose strip, restart degenerates included, exceeds T~ into
+ * the two halves of its strip order (Sec. 4.2).
+ *   tri_idx   n_tris x 3 vertex indices (< n_verts), counter-clockwise
+ *   tri_class optional n_tris class ids (< n_classes): meshlets never mix
+ *             classes and use limits[class]; NULL = all class 0
+ *   n_threads worker threads (0 = hardware concurrency)
+ * Returns MC_ERR_INVALID_ARG for out-of-range or repeated vertex indices. */
+mc_status mc_meshletize(const uint32_t *tri_idx, uint32_t n_tris, uint32_t n_verts,
+                        const uint8_t *tri_class, const mc_limits *limits,
+                        uint32_t n_classes, uint32_t n_threads, mc_meshlets **out);
+
+/* Number of meshlets, and their triangle grouping: out_tri (n_tris ids, may
+ * be NULL) grouped by meshlet, out_start (count + 1 offsets, may be NULL). */
+uint32_t mc_meshlets_count(const mc_meshlets *m);
+mc_status mc_meshlets_get(const mc_meshlets *m, uint32_t *out_tri, uint32_t *out_start);
+void mc_meshlets_free(mc_meshlets *m);
+
+typedef struct {
+  uint32_t pos_bits;              /* b for every meshlet (1..32) ... */
+  const uint8_t *pos_bits_per_meshlet; /* ... or one b per meshlet (may be NULL) */
+  uint32_t reuse_mode;            /* 0: w = 8 (Sec. 3), 1: w = ceil(log2 V) */
+  const uint32_t *order;          /* optional: blob slot p holds meshlet order[p] */
+  uint32_t mesh_id;               /* written into the grid entries */
+  uint32_t n_threads;             /* 0 = hardware concurrency */
+} mc_encode_params;
+
+/* Encode the meshlets of one mesh (Sec. 4.2-4.4) into a blob.
+ *   pos_xyz  n_verts x 3 FP32 positions
+ * Per meshlet: greedy generalized triangle strip (restart = four degenerate
+ * triangles), first-appearance vertex numbering, L/R + increment flags,
+ * reuse entries; positions on the global grid with Delta = w/(2^b - 1)
+ * rounded up to FP32 (w = largest meshlet extent at that b), grid coordinate
+ * floor((x - G)/Delta + 1/2), stored relative to the meshlet minimum L.
+ * MC_ERR_LIMIT if a grid coordinate exceeds 32 bits. */
+mc_status mc_encode(const mc_meshlets *m, const float *pos_xyz, uint32_t n_verts,
+                    const mc_encode_params *p, mc_blob **out);
+
+/* Concatenate blobs into one batch: payload offsets, vertex/triangle bases
+ * and grid ids are rebased; grid mesh ids become the blob's list position. */
+mc_status mc_blob_concat(const mc_blob *const *blobs, uint32_t n, mc_blob **out);
+
+typedef struct {
+  uint32_t first_meshlet, n_meshlets; /* blob slots of this mesh */
+  uint64_t tri_base, n_tris;          /* decoded triangle range (T') */
+  uint64_t vertex_base, n_verts;      /* decoded vertex range */
+  uint64_t input_tris;                /* triangles of the input mesh */
+} mc_mesh_info;
+
+/* Read-only view of a blob (pointers stay valid until mc_blob_free). */
+typedef struct {
+  const mc_desc *desc;       uint32_t n_meshlets;
+  const uint8_t *payload;    uint64_t payload_bytes;
+  const mc_grid *grids;      uint32_t n_grids;
+  const mc_mesh_info *meshes; uint32_t n_meshes;
+  const uint32_t *vertex_map; /* input vertex id of each decoded vertex */
+  uint64_t total_tris;        /* sum of T' (decoded triangle slots) */
+  uint64_t total_verts;       /* sum of V */
+  uint64_t input_tris;        /* sum of input triangles */
+  uint64_t restarts;          /* strip restarts (each = 4 degenerates) */
+  uint64_t split_meshlets;    /* meshlets added by splitting */
+  uint64_t conn_bits;         /* sum of 2 T' + w R (flags + reuse) */
+  uint64_t pos_bits_total;    /* sum of 3 V b */
+  uint32_t max_block_words;   /* largest payload block, u32 words */
+  uint32_t max_tris;          /* largest T' */
+} mc_blob_view_t;
+
+mc_status mc_blob_view(const mc_blob *b, mc_blob_view_t *v);
+void mc_blob_free(mc_blob *b);
+
+/* ------------------------------------------------------------------ device */
+
+/* A batch resident in device memory (caller-owned): the three blob arrays. */
+typedef struct {
+  const mc_desc *desc;
+  const uint8_t *payload;
+  const mc_grid *grids;
+  uint32_t n_meshlets;
+  uint32_t n_grids;
+  uint64_t payload_bytes;
+  uint64_t total_tris;  /* capacity of the outputs, triangles (sum of T') */
+  uint64_t total_verts; /* capacity of the outputs, vertices (sum of V) */
+  uint32_t max_block_words; /* from mc_blob_view (sizes shared-memory staging) */
+} mc_device_batch;
+
+/* Launch shape; zero fields take the library defaults or the autotuned
+ * values.  checked = 1 selects the kernel variant that validates every
+ * stream entry (reuse index < vertices seen, flag/count consistency) and
+ * reports MC_ERR_CORRUPT instead of decoding garbage. */
+typedef struct {
+  uint32_t warps_per_cta;     /* 1..32 */
+  uint32_t ctas_per_sm;       /* persistent CTAs per SM */
+  uint32_t meshlets_per_grab; /* work-queue granularity (persistent kernels) */
+  uint32_t checked;
+} mc_tuning;
+
+/* Bytes of device scratch the persistent kernels need (work-queue counters).
+ * The scratch must be zero before its first use; every kernel that uses it
+ * leaves it zeroed when it completes. */
+size_t mc_scratch_bytes(void);
+
+/* Plain decode: one launch over meshlets [first, first + count), one warp per
+ * meshlet (the baseline; a per-mesh decode issues one call per mesh).
+ * Outputs (any of d_local / d_global may be NULL, d_pos may not):
+ *   d_local  u8  [3 * total_tris]  local triangle indices, meshlet m at
+ *            3 * tri_base(m); degenerates are kept (Sec. 4.2)
+ *   d_global u32 [3 * total_tris]  vertex_base(m) + local
+ *   d_pos    f32 [3 * total_verts] FP32 positions (Sec. 4.4)
+ * Triangle k with flag R is (I[k+1], old, I[k+2]), with flag L
+ * (old, I[k+1], I[k+2]), where I is the strip stream (I[0..2] = 0,1,2) and
+ * old = I[j+1] for the last j < k whose flag differs from flag k (I[0] if
+ * none) -- the bit scan of Sec. 4.2; I[k+2] is the inclusive add-scan of the
+ * increment flags (+2) or reuse entry k+1-s (Sec. 4.3). */
+mc_status mc_decode_plain(const mc_device_batch *b, uint32_t first, uint32_t count,
+                          uint8_t *d_local, uint32_t *d_global, float *d_pos,
+                          uint32_t *d_status, const mc_tuning *t, void *stream);
+
+/* Batched decode: all meshlets of the batch in one persistent launch whose
+ * warps pull meshlets from a device work queue in d_scratch
+ * (mc_scratch_bytes(), zeroed before first use).  Same outputs as
+ * mc_decode_plain over the whole batch.  t = NULL: autotuned shape (or the
+ * default if mc_autotune has not run for this batch signature). */
+mc_status mc_decode_batch(const mc_device_batch *b, uint8_t *d_local, uint32_t *d_global,
+                          float *d_pos, uint32_t *d_status, void *d_scratch,
+                          const mc_tuning *t, void *stream);
+
+/* Fused decode + cull + compaction in one persistent launch.
+ *   d_view_proj  16 FP32, row-major clip matrix: clip = M [x y z 1]^T
+ *   d_tri_out    u32 [3 * total_tris]: surviving triangles as global index
+ *                triples, compacted in unspecified order
+ *   d_tri_count  u32, receives the number of surviving triangles (the
+ *                running count lives in d_scratch during the launch)
+ *   d_pos        f32 [3 * total_verts], written for meshlets that pass the
+ *                frustum test only
+ * A meshlet is skipped when all 8 corners of its quantisation box
+ * [L, L + 2^b - 1] lie outside one clip plane (-w <= x, y, z <= w); a
+ * triangle is dropped when two of its indices coincide (restart
+ * degenerates) or when all three clip w are positive and the determinant of
+ * its (x, y, w) clip rows is not positive (back-facing, counter-clockwise
+ * front faces).  Decoded indices never leave the chip except as survivors. */
+mc_status mc_decode_cull(const mc_device_batch *b, const float *d_view_proj,
+                         uint32_t *d_tri_out, uint32_t *d_tri_count, float *d_pos,
+                         uint32_t *d_status, void *d_scratch, const mc_tuning *t,
+                         void *stream);
+
+/* ------------------------------------------------------------------ runtime */
+
+/* Time candidate launch shapes of mc_decode_batch on this batch (the outputs
+ * are overwritten) and remember the fastest for batches with the same
+ * signature (meshlet count, payload size, largest block) on this device.
+ * Synchronises `stream`.  best (may be NULL) receives the chosen shape,
+ * best_ms (may be NULL) its time. */
+mc_status mc_autotune(const mc_device_batch *b, uint8_t *d_local, uint32_t *d_global,
+                      float *d_pos, uint32_t *d_status, void *d_scratch, void *stream,
+                      mc_tuning *best, float *best_ms);
+
+/* CUDA-graph wrapper: mc_graph_capture_batch records one mc_decode_batch
+ * launch (with fixed pointers) into an executable graph; mc_graph_launch
+ * replays it on a stream. */
+typedef struct mc_graph mc_graph;
+mc_status mc_graph_capture_batch(const mc_device_batch *b, uint8_t *d_local,
+                                 uint32_t *d_global, float *d_pos, uint32_t *d_status,
+                                 void *d_scratch, const mc_tuning *t, void *stream,
+                                 mc_graph **out);
+/* Same for the fused culling kernel: the graph holds one launch per matrix in
+ * d_view_projs (n_views x 16 FP32); launch i writes d_tri_count[i] (n_views
+ * entries) and overwrites the same d_tri_out / d_pos. */
+mc_status mc_graph_capture_cull(const mc_device_batch *b, const float *d_view_projs,
+                                uint32_t n_views, uint32_t *d_tri_out, uint32_t *d_tri_count,
+                                float *d_pos, uint32_t *d_status, void *d_scratch,
+                                const mc_tuning *t, void *stream, mc_graph **out);
+mc_status mc_graph_launch(mc_graph *g, void *stream);
+void mc_graph_free(mc_graph *g);
+
+/* Host-buffer decode (end to end): copies the host blob arrays of `v` into
+ * the caller's device buffers d_desc / d_payload / d_grids, decodes with
+ * mc_decode_batch and copies the outputs back into h_local / h_global /
+ * h_pos (NULL = not copied).  Host buffers should be pinned.  Asynchronous
+ * on `stream`. */
+mc_status mc_decode_batch_host(const mc_blob_view_t *v, mc_desc *d_desc, uint8_t *d_payload,
+                               mc_grid *d_grids, uint8_t *d_local, uint32_t *d_global,
+                               float *d_pos, uint32_t *d_status, void *d_scratch,
+                               uint8_t *h_local, uint32_t *h_global, float *h_pos,
+                               const mc_tuning *t, void *stream);
+
+/* Kernel launches this library has issued since load (all entry points). */
+uint64_t mc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MESHLET_CODEC_H */

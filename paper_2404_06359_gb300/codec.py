@@ -1,0 +1,397 @@
+"""Python binding of ``libmeshletcodec.so`` (argument marshalling only).
+
+Every function named ``mc_*`` is the C entry point of the same name in
+``include/meshlet_codec.h``; PyTorch tensors supply device memory and CUDA
+streams.  All computation happens in the library: there is no Python or CPU
+fallback, and importing this module fails loudly if the library cannot be
+built or loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+u8, u16, u32, u64 = C.c_uint8, C.c_uint16, C.c_uint32, C.c_uint64
+P = C.c_void_p
+
+
+class mc_limits(C.Structure):
+    _fields_ = [("max_verts", u32), ("max_tris", u32)]
+
+
+class mc_encode_params(C.Structure):
+    _fields_ = [("pos_bits", u32), ("pos_bits_per_meshlet", P), ("reuse_mode", u32),
+                ("order", P), ("mesh_id", u32), ("n_threads", u32)]
+
+
+class mc_mesh_info(C.Structure):
+    _fields_ = [("first_meshlet", u32), ("n_meshlets", u32), ("tri_base", u64), ("n_tris", u64),
+                ("vertex_base", u64), ("n_verts", u64), ("input_tris", u64)]
+
+
+class mc_blob_view_t(C.Structure):
+    _fields_ = [("desc", P), ("n_meshlets", u32), ("payload", P), ("payload_bytes", u64),
+                ("grids", P), ("n_grids", u32), ("meshes", C.POINTER(mc_mesh_info)),
+                ("n_meshes", u32), ("vertex_map", P), ("total_tris", u64), ("total_verts", u64),
+                ("input_tris", u64), ("restarts", u64), ("split_meshlets", u64),
+                ("conn_bits", u64), ("pos_bits_total", u64), ("max_block_words", u32),
+                ("max_tris", u32)]
+
+
+class mc_device_batch(C.Structure):
+    _fields_ = [("desc", P), ("payload", P), ("grids", P), ("n_meshlets", u32), ("n_grids", u32),
+                ("payload_bytes", u64), ("total_tris", u64), ("total_verts", u64),
+                ("max_block_words", u32)]
+
+
+class mc_tuning(C.Structure):
+    _fields_ = [("warps_per_cta", u32), ("ctas_per_sm", u32), ("meshlets_per_grab", u32),
+                ("checked", u32)]
+
+
+STATUS = {0: "MC_OK", 1: "MC_ERR_INVALID_ARG", 2: "MC_ERR_LIMIT", 3: "MC_ERR_CORRUPT",
+          4: "MC_ERR_CUDA", 5: "MC_ERR_OOM", 6: "MC_ERR_TIMEOUT"}
+MC_ERR_CORRUPT = 3
+MC_ERR_TIMEOUT = 6
+
+# every entry point of include/meshlet_codec.h: (name, restype, argtypes)
+_SIGS = [
+    ("mc_status_string", C.c_char_p, [C.c_int]),
+    ("mc_version", C.c_char_p, []),
+    ("mc_meshletize", C.c_int, [P, u32, u32, P, C.POINTER(mc_limits), u32, u32, C.POINTER(P)]),
+    ("mc_meshlets_count", u32, [P]),
+    ("mc_meshlets_get", C.c_int, [P, P, P]),
+    ("mc_meshlets_free", None, [P]),
+    ("mc_encode", C.c_int, [P, P, u32, C.POINTER(mc_encode_params), C.POINTER(P)]),
+    ("mc_blob_concat", C.c_int, [C.POINTER(P), u32, C.POINTER(P)]),
+    ("mc_blob_view", C.c_int, [P, C.POINTER(mc_blob_view_t)]),
+    ("mc_blob_free", None, [P]),
+    ("mc_scratch_bytes", C.c_size_t, []),
+    ("mc_decode_plain", C.c_int, [C.POINTER(mc_device_batch), u32, u32, P, P, P, P,
+                                  C.POINTER(mc_tuning), P]),
+    ("mc_decode_batch", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P,
+                                  C.POINTER(mc_tuning), P]),
+    ("mc_decode_cull", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P, P,
+                                 C.POINTER(mc_tuning), P]),
+    ("mc_autotune", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P, P,
+                              C.POINTER(mc_tuning), C.POINTER(C.c_float)]),
+    ("mc_graph_capture_batch", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P,
+                                         C.POINTER(mc_tuning), P, C.POINTER(P)]),
+    ("mc_graph_capture_cull", C.c_int, [C.POINTER(mc_device_batch), P, u32, P, P, P, P, P,
+                                        C.POINTER(mc_tuning), P, C.POINTER(P)]),
+    ("mc_graph_launch", C.c_int, [P, P]),
+    ("mc_graph_free", None, [P]),
+    ("mc_decode_batch_host", C.c_int, [C.POINTER(mc_blob_view_t), P, P, P, P, P, P, P, P,
+                                       P, P, P, C.POINTER(mc_tuning), P]),
+    ("mc_launch_count", u64, []),
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded library (built on first use if needed)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            for name, res, args in _SIGS:
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+        return _lib
+
+
+def exported_names() -> list[str]:
+    return [s[0] for s in _SIGS]
+
+
+class CodecError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise CodecError(st, what)
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(P)
+
+
+def _tptr(t):
+    return None if t is None else P(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return P(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return P(stream)
+    return P(stream.cuda_stream)
+
+
+def _tuning(t):
+    if t is None:
+        return None
+    if isinstance(t, mc_tuning):
+        return C.byref(t)
+    return C.byref(mc_tuning(**t))
+
+
+def mc_status_string(st: int) -> str:
+    return lib().mc_status_string(st).decode()
+
+
+def mc_version() -> str:
+    return lib().mc_version().decode()
+
+
+def mc_scratch_bytes() -> int:
+    return int(lib().mc_scratch_bytes())
+
+
+def mc_launch_count() -> int:
+    return int(lib().mc_launch_count())
+
+
+# ------------------------------------------------------------------- host
+class Meshlets:
+    """Owns an ``mc_meshlets*``."""
+
+    def __init__(self, handle, n_tris):
+        self._h = handle
+        self.n_tris = n_tris
+
+    @property
+    def count(self) -> int:
+        return int(lib().mc_meshlets_count(self._h))
+
+    def get(self):
+        tri = np.zeros(self.n_tris, np.uint32)
+        start = np.zeros(self.count + 1, np.uint32)
+        _check(lib().mc_meshlets_get(self._h, _np_ptr(tri), _np_ptr(start)), "mc_meshlets_get")
+        return tri, start
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().mc_meshlets_free(self._h)
+            self._h = None
+
+
+def mc_meshletize(tris: np.ndarray, n_verts: int, limits=((64, 126),), tri_class=None,
+                  n_threads: int = 0) -> Meshlets:
+    tris = np.ascontiguousarray(tris, np.uint32)
+    lim = np.asarray(limits, np.uint32).reshape(-1, 2)
+    arr = (mc_limits * lim.shape[0])(*[mc_limits(int(a), int(b)) for a, b in lim])
+    cls = None if tri_class is None else np.ascontiguousarray(tri_class, np.uint8)
+    h = P()
+    _check(lib().mc_meshletize(_np_ptr(tris), tris.shape[0], n_verts, _np_ptr(cls), arr,
+                               lim.shape[0], n_threads, C.byref(h)), "mc_meshletize")
+    return Meshlets(h, tris.shape[0])
+
+
+class Blob:
+    """Owns an ``mc_blob*``; ``view()`` exposes its arrays as numpy views."""
+
+    def __init__(self, handle):
+        self._h = handle
+        self._view = None
+
+    def view(self) -> mc_blob_view_t:
+        if self._view is None:
+            v = mc_blob_view_t()
+            _check(lib().mc_blob_view(self._h, C.byref(v)), "mc_blob_view")
+            self._view = v
+        return self._view
+
+    def arrays(self) -> dict:
+        """Copies of desc (uint8 [M,32]), payload, grids (uint8 [G,32]),
+        vertex_map and the per-mesh table."""
+        v = self.view()
+
+        def grab(ptr, n, dt):
+            if n == 0:
+                return np.zeros(0, dt)
+            return np.ctypeslib.as_array(C.cast(ptr, C.POINTER(np.ctypeslib.as_ctypes_type(dt))),
+                                         (n,)).copy()
+        meshes = [{k: int(getattr(v.meshes[i], k)) for k, _ in mc_mesh_info._fields_}
+                  for i in range(v.n_meshes)]
+        return {
+            "desc": grab(v.desc, 32 * v.n_meshlets, np.uint8).reshape(-1, 32),
+            "payload": grab(v.payload, v.payload_bytes, np.uint8),
+            "grids": grab(v.grids, 32 * v.n_grids, np.uint8).reshape(-1, 32),
+            "vertex_map": grab(v.vertex_map, v.total_verts, np.uint32),
+            "meshes": meshes,
+        }
+
+    def stats(self) -> dict:
+        v = self.view()
+        keys = ("n_meshlets", "payload_bytes", "n_grids", "n_meshes", "total_tris", "total_verts",
+                "input_tris", "restarts", "split_meshlets", "conn_bits", "pos_bits_total",
+                "max_block_words", "max_tris")
+        return {k: int(getattr(v, k)) for k in keys}
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().mc_blob_free(self._h)
+            self._h = None
+
+
+def mc_encode(meshlets: Meshlets, pos: np.ndarray, pos_bits=16, reuse_mode: int = 0, order=None,
+              mesh_id: int = 0, n_threads: int = 0) -> Blob:
+    pos = np.ascontiguousarray(pos, np.float32)
+    per = None
+    if np.ndim(pos_bits) > 0:
+        per = np.ascontiguousarray(pos_bits, np.uint8)
+    order = None if order is None else np.ascontiguousarray(order, np.uint32)
+    p = mc_encode_params(int(pos_bits) if per is None else 0, _np_ptr(per), reuse_mode,
+                         _np_ptr(order), mesh_id, n_threads)
+    h = P()
+    _check(lib().mc_encode(meshlets._h, _np_ptr(pos), pos.shape[0], C.byref(p), C.byref(h)),
+           "mc_encode")
+    return Blob(h)
+
+
+def mc_blob_concat(blobs: list[Blob]) -> Blob:
+    arr = (P * len(blobs))(*[b._h for b in blobs])
+    h = P()
+    _check(lib().mc_blob_concat(arr, len(blobs), C.byref(h)), "mc_blob_concat")
+    return Blob(h)
+
+
+# ----------------------------------------------------------------- device
+class DeviceBatch:
+    """A blob copied into device memory (torch uint8 tensors) plus the
+    ``mc_device_batch`` that points at it."""
+
+    def __init__(self, blob: Blob, device="cuda"):
+        a = blob.arrays()
+        self._init(a["desc"], a["payload"], a["grids"], blob.stats(), device)
+        self.meshes = a["meshes"]
+
+    @classmethod
+    def from_arrays(cls, desc, payload, grids, total_tris, total_verts, max_block_words,
+                    device="cuda"):
+        """Wrap blob arrays that did not come from ``mc_encode`` (e.g. a
+        hand-packed stream); sizes are the caller's."""
+        self = cls.__new__(cls)
+        stats = {"n_meshlets": desc.shape[0], "n_grids": grids.shape[0],
+                 "payload_bytes": payload.size, "total_tris": total_tris,
+                 "total_verts": total_verts, "max_block_words": max_block_words}
+        self._init(np.asarray(desc, np.uint8), np.asarray(payload, np.uint8),
+                   np.asarray(grids, np.uint8), stats, device)
+        self.meshes = []
+        return self
+
+    def _init(self, desc, payload, grids, stats, device):
+        import torch
+        self.stats = stats
+        self.desc = torch.from_numpy(np.ascontiguousarray(desc).reshape(-1)).to(device)
+        self.payload = torch.from_numpy(np.ascontiguousarray(payload) if payload.size
+                                        else np.zeros(16, np.uint8)).to(device)
+        self.grids = torch.from_numpy(np.ascontiguousarray(grids).reshape(-1)).to(device)
+        s = self.stats
+        self.c = mc_device_batch(self.desc.data_ptr(), self.payload.data_ptr(), self.grids.data_ptr(),
+                                 s["n_meshlets"], s["n_grids"], s["payload_bytes"], s["total_tris"],
+                                 s["total_verts"], max(1, s["max_block_words"]))
+
+    def outputs(self, local=True, global_=True, device="cuda"):
+        import torch
+        T, V = self.stats["total_tris"], self.stats["total_verts"]
+        return {
+            "local": torch.empty(3 * T, dtype=torch.uint8, device=device) if local else None,
+            "global": torch.empty(3 * T, dtype=torch.int32, device=device) if global_ else None,
+            "pos": torch.empty(3 * V, dtype=torch.float32, device=device),
+            "status": torch.zeros(1, dtype=torch.int32, device=device),
+        }
+
+
+def new_scratch(device="cuda"):
+    import torch
+    return torch.zeros(mc_scratch_bytes() // 4, dtype=torch.int32, device=device)
+
+
+def mc_decode_plain(db: DeviceBatch, first, count, d_local, d_global, d_pos, d_status,
+                    tuning=None, stream=None):
+    _check(lib().mc_decode_plain(C.byref(db.c), first, count, _tptr(d_local), _tptr(d_global),
+                                 _tptr(d_pos), _tptr(d_status), _tuning(tuning), _stream(stream)),
+           "mc_decode_plain")
+
+
+def mc_decode_batch(db: DeviceBatch, d_local, d_global, d_pos, d_status, d_scratch, tuning=None,
+                    stream=None):
+    _check(lib().mc_decode_batch(C.byref(db.c), _tptr(d_local), _tptr(d_global), _tptr(d_pos),
+                                 _tptr(d_status), _tptr(d_scratch), _tuning(tuning), _stream(stream)),
+           "mc_decode_batch")
+
+
+def mc_decode_cull(db: DeviceBatch, d_view_proj, d_tri_out, d_tri_count, d_pos, d_status, d_scratch,
+                   tuning=None, stream=None):
+    _check(lib().mc_decode_cull(C.byref(db.c), _tptr(d_view_proj), _tptr(d_tri_out),
+                                _tptr(d_tri_count), _tptr(d_pos), _tptr(d_status), _tptr(d_scratch),
+                                _tuning(tuning), _stream(stream)), "mc_decode_cull")
+
+
+def mc_autotune(db: DeviceBatch, d_local, d_global, d_pos, d_status, d_scratch, stream=None):
+    best = mc_tuning()
+    ms = C.c_float()
+    _check(lib().mc_autotune(C.byref(db.c), _tptr(d_local), _tptr(d_global), _tptr(d_pos),
+                             _tptr(d_status), _tptr(d_scratch), _stream(stream), C.byref(best),
+                             C.byref(ms)), "mc_autotune")
+    return best, float(ms.value)
+
+
+class Graph:
+    def __init__(self, h):
+        self._h = h
+
+    def launch(self, stream=None):
+        mc_graph_launch(self, stream)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().mc_graph_free(self._h)
+            self._h = None
+
+
+def mc_graph_capture_batch(db: DeviceBatch, d_local, d_global, d_pos, d_status, d_scratch,
+                           tuning=None, stream=None) -> Graph:
+    h = P()
+    _check(lib().mc_graph_capture_batch(C.byref(db.c), _tptr(d_local), _tptr(d_global), _tptr(d_pos),
+                                        _tptr(d_status), _tptr(d_scratch), _tuning(tuning),
+                                        _stream(stream), C.byref(h)), "mc_graph_capture_batch")
+    return Graph(h)
+
+
+def mc_graph_capture_cull(db: DeviceBatch, d_view_projs, n_views, d_tri_out, d_tri_count, d_pos,
+                          d_status, d_scratch, tuning=None, stream=None) -> Graph:
+    h = P()
+    _check(lib().mc_graph_capture_cull(C.byref(db.c), _tptr(d_view_projs), n_views, _tptr(d_tri_out),
+                                       _tptr(d_tri_count), _tptr(d_pos), _tptr(d_status),
+                                       _tptr(d_scratch), _tuning(tuning), _stream(stream), C.byref(h)),
+           "mc_graph_capture_cull")
+    return Graph(h)
+
+
+def mc_graph_launch(g: Graph, stream=None):
+    _check(lib().mc_graph_launch(g._h, _stream(stream)), "mc_graph_launch")
+
+
+def mc_decode_batch_host(blob: Blob, d_desc, d_payload, d_grids, d_local, d_global, d_pos, d_status,
+                         d_scratch, h_local, h_global, h_pos, tuning=None, stream=None):
+    v = blob.view()
+    _check(lib().mc_decode_batch_host(C.byref(v), _tptr(d_desc), _tptr(d_payload), _tptr(d_grids),
+                                      _tptr(d_local), _tptr(d_global), _tptr(d_pos), _tptr(d_status),
+                                      _tptr(d_scratch), _tptr(h_local), _tptr(h_global), _tptr(h_pos),
+                                      _tuning(tuning), _stream(stream)), "mc_decode_batch_host")

@@ -1,0 +1,366 @@
+// C ABI of the device side: argument checks, launch shapes, the autotuner,
+// CUDA-graph capture and the host-buffer (end-to-end) decode.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "kernels.h"
+#include "meshlet_codec.h"
+
+using namespace mcdev;
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+constexpr uint32_t kScratchBytes = 256;
+
+struct Key {
+  int device;
+  uint32_t n_meshlets, max_block_words;
+  uint64_t payload_bytes;
+  bool operator<(const Key &o) const {
+    return std::tie(device, n_meshlets, max_block_words, payload_bytes) <
+           std::tie(o.device, o.n_meshlets, o.max_block_words, o.payload_bytes);
+  }
+};
+std::mutex g_tune_mu;
+std::map<Key, mc_tuning> g_tuned;
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return n;
+}
+
+Key key_of(const mc_device_batch *b) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return Key{dev, b->n_meshlets, b->max_block_words, b->payload_bytes};
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+mc_status check_batch(const mc_device_batch *b) {
+  if (!b || !b->desc || !b->payload || !b->grids) return MC_ERR_INVALID_ARG;
+  if (!aligned(b->desc, 16) || !aligned(b->payload, 16) || !aligned(b->grids, 16))
+    return MC_ERR_INVALID_ARG;
+  if (b->n_grids == 0 || b->n_grids > 65536) return MC_ERR_INVALID_ARG;
+  if (b->max_block_words == 0 || b->max_block_words > 2 * 8 + 64 + 768 + 4) return MC_ERR_INVALID_ARG;
+  if (b->payload_bytes % 16) return MC_ERR_INVALID_ARG;
+  return MC_OK;
+}
+
+BatchArgs args_of(const mc_device_batch *b) {
+  BatchArgs a;
+  a.desc = b->desc;
+  a.payload = b->payload;
+  a.grids = b->grids;
+  a.n_meshlets = b->n_meshlets;
+  a.n_grids = b->n_grids;
+  a.payload_bytes = b->payload_bytes;
+  a.total_tris = b->total_tris;
+  a.total_verts = b->total_verts;
+  a.max_block_words = b->max_block_words;
+  return a;
+}
+
+mc_status from_cuda(cudaError_t e) { return e == cudaSuccess ? MC_OK : MC_ERR_CUDA; }
+
+// Resolves a launch shape for the persistent batch kernel.
+mc_tuning resolve_batch(const mc_device_batch *b, const mc_tuning *t) {
+  mc_tuning r{};
+  if (t) r = *t;
+  if (!t || (!r.warps_per_cta && !r.ctas_per_sm && !r.meshlets_per_grab)) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key_of(b));
+    if (it != g_tuned.end()) {
+      uint32_t checked = r.checked;
+      r = it->second;
+      r.checked = checked;
+    }
+  }
+  if (!r.warps_per_cta) r.warps_per_cta = 8;
+  if (!r.meshlets_per_grab) r.meshlets_per_grab = 2;
+  if (!r.ctas_per_sm) {
+    int occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words);
+    r.ctas_per_sm = occ > 0 ? (uint32_t)occ : 1;
+  }
+  return r;
+}
+
+mc_status launch_batch_checked(const mc_device_batch *b, uint8_t *d_local, uint32_t *d_global,
+                               float *d_pos, uint32_t *d_status, void *d_scratch,
+                               const mc_tuning &r, cudaStream_t s) {
+  if (r.warps_per_cta < 1 || r.warps_per_cta > 32 || r.meshlets_per_grab < 1) return MC_ERR_INVALID_ARG;
+  int occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words);
+  if (occ <= 0) return MC_ERR_INVALID_ARG;
+  uint32_t per_sm = std::min<uint32_t>(r.ctas_per_sm, (uint32_t)occ);
+  uint32_t ctas = per_sm * (uint32_t)sm_count();
+  if (ctas == 0) return MC_ERR_CUDA;
+  cudaError_t e = launch_batch(args_of(b), ctas, r.warps_per_cta, r.meshlets_per_grab,
+                               b->max_block_words, r.checked != 0, d_local, d_global, d_pos,
+                               d_status, static_cast<uint32_t *>(d_scratch), s);
+  if (e == cudaSuccess) g_launches++;
+  return from_cuda(e);
+}
+
+}  // namespace
+
+extern "C" size_t mc_scratch_bytes(void) { return kScratchBytes; }
+
+extern "C" uint64_t mc_launch_count(void) { return g_launches.load(); }
+
+extern "C" mc_status mc_decode_plain(const mc_device_batch *b, uint32_t first, uint32_t count,
+                                     uint8_t *d_local, uint32_t *d_global, float *d_pos,
+                                     uint32_t *d_status, const mc_tuning *t, void *stream) {
+  if (!b) return MC_ERR_INVALID_ARG;
+  if (count == 0 && first <= b->n_meshlets) return MC_OK;
+  mc_status st = check_batch(b);
+  if (st != MC_OK) return st;
+  if (!d_pos || (uint64_t)first + count > b->n_meshlets) return MC_ERR_INVALID_ARG;
+  uint32_t warps = (t && t->warps_per_cta) ? t->warps_per_cta : 8;
+  if (warps > 32) return MC_ERR_INVALID_ARG;
+  if (count == 0) return MC_OK;
+  cudaError_t e = launch_plain(args_of(b), first, count, warps, b->max_block_words,
+                               t && t->checked, d_local, d_global, d_pos, d_status,
+                               static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) g_launches++;
+  return from_cuda(e);
+}
+
+extern "C" mc_status mc_decode_batch(const mc_device_batch *b, uint8_t *d_local, uint32_t *d_global,
+                                     float *d_pos, uint32_t *d_status, void *d_scratch,
+                                     const mc_tuning *t, void *stream) {
+  if (!b) return MC_ERR_INVALID_ARG;
+  if (b->n_meshlets == 0) return MC_OK;
+  mc_status st = check_batch(b);
+  if (st != MC_OK) return st;
+  if (!d_pos || !d_scratch || !aligned(d_scratch, 16)) return MC_ERR_INVALID_ARG;
+  mc_tuning r = resolve_batch(b, t);
+  return launch_batch_checked(b, d_local, d_global, d_pos, d_status, d_scratch, r,
+                              static_cast<cudaStream_t>(stream));
+}
+
+namespace {
+mc_status launch_cull_checked(const mc_device_batch *b, const float *d_vp, uint32_t *d_tri_out,
+                              uint32_t *d_tri_count, float *d_pos, uint32_t *d_status,
+                              void *d_scratch, const mc_tuning *t, cudaStream_t s) {
+  uint32_t warps = (t && t->warps_per_cta) ? t->warps_per_cta : 8;
+  if (warps < 1 || warps > 32) return MC_ERR_INVALID_ARG;
+  int occ = max_ctas_per_sm_cull(warps, b->max_block_words);
+  if (occ <= 0) return MC_ERR_INVALID_ARG;
+  uint32_t per_sm = (t && t->ctas_per_sm) ? std::min<uint32_t>(t->ctas_per_sm, occ) : (uint32_t)occ;
+  uint32_t ctas = per_sm * (uint32_t)sm_count();
+  if (ctas == 0) return MC_ERR_CUDA;
+  cudaError_t e = launch_cull(args_of(b), d_vp, ctas, warps, b->max_block_words, t && t->checked,
+                              d_tri_out, d_tri_count, d_pos, d_status,
+                              static_cast<uint32_t *>(d_scratch), s);
+  if (e == cudaSuccess) g_launches++;
+  return from_cuda(e);
+}
+}  // namespace
+
+extern "C" mc_status mc_decode_cull(const mc_device_batch *b, const float *d_view_proj,
+                                    uint32_t *d_tri_out, uint32_t *d_tri_count, float *d_pos,
+                                    uint32_t *d_status, void *d_scratch, const mc_tuning *t,
+                                    void *stream) {
+  if (!b || !d_tri_count) return MC_ERR_INVALID_ARG;
+  if (b->n_meshlets == 0)
+    return from_cuda(cudaMemsetAsync(d_tri_count, 0, 4, static_cast<cudaStream_t>(stream)));
+  mc_status st = check_batch(b);
+  if (st != MC_OK) return st;
+  if (!d_view_proj || !d_tri_out || !d_pos || !d_scratch || !aligned(d_scratch, 16))
+    return MC_ERR_INVALID_ARG;
+  return launch_cull_checked(b, d_view_proj, d_tri_out, d_tri_count, d_pos, d_status, d_scratch, t,
+                             static_cast<cudaStream_t>(stream));
+}
+
+extern "C" mc_status mc_autotune(const mc_device_batch *b, uint8_t *d_local, uint32_t *d_global,
+                                 float *d_pos, uint32_t *d_status, void *d_scratch, void *stream,
+                                 mc_tuning *best, float *best_ms) {
+  mc_status st = check_batch(b);
+  if (st != MC_OK) return st;
+  if (!d_pos || !d_scratch) return MC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MC_ERR_CUDA;
+  mc_tuning bt{};
+  float bms = 1e30f;
+  const uint32_t warps_c[] = {4, 8, 16};
+  const uint32_t grab_c[] = {1, 2, 4, 8};
+  st = MC_OK;
+  for (uint32_t w : warps_c) {
+    int occ = max_ctas_per_sm_batch(w, b->max_block_words);
+    if (occ <= 0) continue;
+    for (uint32_t g : grab_c) {
+      for (uint32_t frac = 0; frac < 2; frac++) {
+        mc_tuning c{};
+        c.warps_per_cta = w;
+        c.meshlets_per_grab = g;
+        c.ctas_per_sm = frac == 0 ? (uint32_t)occ : std::max(1u, (uint32_t)occ / 2);
+        if (frac == 1 && c.ctas_per_sm == (uint32_t)occ) continue;
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 4 && st == MC_OK; rep++) {
+          cudaEventRecord(e0, s);
+          st = launch_batch_checked(b, d_local, d_global, d_pos, d_status, d_scratch, c, s);
+          cudaEventRecord(e1, s);
+          if (cudaEventSynchronize(e1) != cudaSuccess) st = MC_ERR_CUDA;
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) ms_min = std::min(ms_min, ms);
+        }
+        if (st != MC_OK) break;
+        if (ms_min < bms) {
+          bms = ms_min;
+          bt = c;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != MC_OK) return st;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key_of(b)] = bt;
+  }
+  if (best) *best = bt;
+  if (best_ms) *best_ms = bms;
+  return MC_OK;
+}
+
+struct mc_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t launches = 0;
+};
+
+namespace {
+template <class F>
+mc_status capture(F &&body, mc_graph **out) {
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return MC_ERR_CUDA;
+  mc_graph *g = new mc_graph();
+  mc_status st = MC_OK;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = MC_ERR_CUDA;
+  uint64_t before = g_launches.load();
+  if (st == MC_OK) st = body(cs);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  if (st == MC_OK && e != cudaSuccess) st = MC_ERR_CUDA;
+  if (st == MC_OK && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) st = MC_ERR_CUDA;
+  g->graph = graph;
+  g->launches = g_launches.load() - before;
+  g_launches.store(before);  // captured, not yet launched
+  cudaStreamDestroy(cs);
+  if (st != MC_OK) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return st;
+  }
+  *out = g;
+  return MC_OK;
+}
+}  // namespace
+
+extern "C" mc_status mc_graph_capture_batch(const mc_device_batch *b, uint8_t *d_local,
+                                            uint32_t *d_global, float *d_pos, uint32_t *d_status,
+                                            void *d_scratch, const mc_tuning *t, void *stream,
+                                            mc_graph **out) {
+  if (!out) return MC_ERR_INVALID_ARG;
+  *out = nullptr;
+  mc_status st = check_batch(b);
+  if (st != MC_OK) return st;
+  if (!d_pos || !d_scratch || b->n_meshlets == 0) return MC_ERR_INVALID_ARG;
+  (void)stream;
+  mc_tuning r = resolve_batch(b, t);  // resolved before capture (no device queries inside)
+  return capture(
+      [&](cudaStream_t cs) {
+        return launch_batch_checked(b, d_local, d_global, d_pos, d_status, d_scratch, r, cs);
+      },
+      out);
+}
+
+extern "C" mc_status mc_graph_capture_cull(const mc_device_batch *b, const float *d_view_projs,
+                                           uint32_t n_views, uint32_t *d_tri_out,
+                                           uint32_t *d_tri_count, float *d_pos, uint32_t *d_status,
+                                           void *d_scratch, const mc_tuning *t, void *stream,
+                                           mc_graph **out) {
+  if (!out) return MC_ERR_INVALID_ARG;
+  *out = nullptr;
+  mc_status st = check_batch(b);
+  if (st != MC_OK) return st;
+  if (!d_view_projs || n_views == 0 || !d_tri_out || !d_tri_count || !d_pos || !d_scratch ||
+      b->n_meshlets == 0)
+    return MC_ERR_INVALID_ARG;
+  (void)stream;
+  return capture(
+      [&](cudaStream_t cs) {
+        for (uint32_t i = 0; i < n_views; i++) {
+          mc_status s2 = launch_cull_checked(b, d_view_projs + 16 * (size_t)i, d_tri_out,
+                                             d_tri_count + i, d_pos, d_status, d_scratch, t, cs);
+          if (s2 != MC_OK) return s2;
+        }
+        return MC_OK;
+      },
+      out);
+}
+
+extern "C" mc_status mc_graph_launch(mc_graph *g, void *stream) {
+  if (!g || !g->exec) return MC_ERR_INVALID_ARG;
+  cudaError_t e = cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) g_launches += g->launches;
+  return from_cuda(e);
+}
+
+extern "C" void mc_graph_free(mc_graph *g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+}
+
+extern "C" mc_status mc_decode_batch_host(const mc_blob_view_t *v, mc_desc *d_desc,
+                                          uint8_t *d_payload, mc_grid *d_grids, uint8_t *d_local,
+                                          uint32_t *d_global, float *d_pos, uint32_t *d_status,
+                                          void *d_scratch, uint8_t *h_local, uint32_t *h_global,
+                                          float *h_pos, const mc_tuning *t, void *stream) {
+  if (!v || !d_desc || !d_payload || !d_grids || !d_pos) return MC_ERR_INVALID_ARG;
+  if ((h_local && !d_local) || (h_global && !d_global)) return MC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(d_desc, v->desc, sizeof(mc_desc) * (size_t)v->n_meshlets,
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_payload, v->payload, v->payload_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_grids, v->grids, sizeof(mc_grid) * (size_t)v->n_grids,
+                        cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return MC_ERR_CUDA;
+  mc_device_batch b{};
+  b.desc = d_desc;
+  b.payload = d_payload;
+  b.grids = d_grids;
+  b.n_meshlets = v->n_meshlets;
+  b.n_grids = v->n_grids;
+  b.payload_bytes = v->payload_bytes;
+  b.total_tris = v->total_tris;
+  b.total_verts = v->total_verts;
+  b.max_block_words = v->max_block_words;
+  mc_status st = mc_decode_batch(&b, d_local, d_global, d_pos, d_status, d_scratch, t, stream);
+  if (st != MC_OK) return st;
+  if (h_local) e = cudaMemcpyAsync(h_local, d_local, 3 * v->total_tris, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && h_global)
+    e = cudaMemcpyAsync(h_global, d_global, 12 * v->total_tris, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && h_pos)
+    e = cudaMemcpyAsync(h_pos, d_pos, 12 * v->total_verts, cudaMemcpyDeviceToHost, s);
+  return from_cuda(e);
+}

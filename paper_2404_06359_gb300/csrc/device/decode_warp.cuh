@@ -1,0 +1,195 @@
+// Warp-level GTS-Reuse meshlet decode (device side).
+//
+// One warp decodes one meshlet; lane l owns triangles k = l, l+32, ... and
+// vertices v = l, l+32, ...  Everything follows the parallel formulation:
+//
+//   stream entry of triangle k (Sec. 4.3): with s_k = 2 + (number of
+//     increment flags set among triangles 1..k) -- an inclusive add-scan,
+//     done per 32-triangle word with __popc on the increment word itself --
+//     the entry is s_k if the flag is set, else reuse[k + 1 - s_k]
+//     (unpacked from w bits with a funnel shift).  I[0..2] = 0,1,2.
+//   third vertex (Sec. 4.2): the last triangle j < k whose L/R flag differs
+//     from flag k, found by masking the flag word (inverted when flag k is
+//     set) below bit k and taking 31 - __clz, walking back word by word
+//     when a fan spans more than 32 triangles; old = I[j + 1] (I[0] if none).
+//   triangle (Sec. 4.2, orientation by the flag): R -> (I[k+1], old, I[k+2]),
+//     L -> (old, I[k+1], I[k+2]).
+//   position (Sec. 4.4): g = L_c + q (q = b bits at (3v+c) b), then
+//     x = fma((float)(g & 0xFFF), D, fma((float)(g >> 12), 4096 D, G)).
+#pragma once
+
+#include <cstdint>
+
+#include "meshlet_codec.h"
+
+namespace mcdev {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+struct Desc {
+  uint32_t off16, vbase, tbase, V, T, w, b, grid, L[3];
+};
+
+__device__ __forceinline__ Desc load_desc(const mc_desc *d) {
+  const uint4 *p = reinterpret_cast<const uint4 *>(d);
+  uint4 a = __ldg(p), c = __ldg(p + 1);
+  Desc r;
+  r.off16 = a.x;
+  r.vbase = a.y;
+  r.tbase = a.z;
+  r.V = a.w & 0xFFFFu;
+  r.T = a.w >> 16;
+  r.w = c.x & 0xFFu;
+  r.b = (c.x >> 8) & 0xFFu;
+  r.grid = c.x >> 16;
+  r.L[0] = c.y;
+  r.L[1] = c.z;
+  r.L[2] = c.w;
+  return r;
+}
+
+struct Grid {
+  float G[3], D[3];
+  uint32_t b;
+};
+
+__device__ __forceinline__ Grid load_grid(const mc_grid *g) {
+  const uint4 *p = reinterpret_cast<const uint4 *>(g);
+  uint4 a = __ldg(p), c = __ldg(p + 1);
+  Grid r;
+  r.G[0] = __uint_as_float(a.x);
+  r.G[1] = __uint_as_float(a.y);
+  r.G[2] = __uint_as_float(a.z);
+  r.b = a.w;
+  r.D[0] = __uint_as_float(c.x);
+  r.D[1] = __uint_as_float(c.y);
+  r.D[2] = __uint_as_float(c.z);
+  return r;
+}
+
+// Payload block size in u32 words (unpadded) of a meshlet.
+__device__ __forceinline__ uint32_t block_words(const Desc &d) {
+  uint32_t nw = (d.T + 31) >> 5;
+  uint32_t R = d.T + 2 - d.V;
+  return 2 * nw + (R * d.w + 31) / 32 + (3 * d.V * d.b + 31) / 32;
+}
+
+struct BatchArgs {
+  const mc_desc *desc;
+  const uint8_t *payload;
+  const mc_grid *grids;
+  uint32_t n_meshlets, n_grids;
+  uint64_t payload_bytes, total_tris, total_verts;
+  uint32_t max_block_words;  // capacity of the per-warp shared-memory slot
+};
+
+// Header sanity (all builds): a descriptor that passes cannot make the decode
+// read or write outside its buffers.
+__device__ __forceinline__ bool header_ok(const Desc &d, const BatchArgs &a) {
+  if (d.V < 3 || d.V > 256 || d.T < 1 || d.T > 256 || d.V > d.T + 2) return false;
+  if (d.w < 1 || d.w > 8 || d.b < 1 || d.b > 32 || d.grid >= a.n_grids) return false;
+  const uint32_t padded = (block_words(d) + 3) & ~3u;
+  if (padded > a.max_block_words) return false;
+  uint64_t end = 16ull * d.off16 + 4ull * padded;
+  if (end > a.payload_bytes) return false;
+  if ((uint64_t)d.tbase + d.T > a.total_tris || (uint64_t)d.vbase + d.V > a.total_verts)
+    return false;
+  return true;
+}
+
+__device__ __forceinline__ uint32_t extract(const uint32_t *w, uint32_t bit, uint32_t nbits) {
+  uint32_t i = bit >> 5;
+  uint32_t v = __funnelshift_r(w[i], w[i + 1], bit & 31u);
+  return nbits >= 32 ? v : (v & ((1u << nbits) - 1u));
+}
+
+__device__ __forceinline__ float dequant(uint32_t g, float G, float D) {
+  float hi = __uint2float_rn(g >> 12);
+  float lo = __uint2float_rn(g & 0xFFFu);
+  float D4096 = __fmul_rn(D, 4096.0f);
+  return __fmaf_rn(lo, D, __fmaf_rn(hi, D4096, G));
+}
+
+__device__ __forceinline__ void set_status(uint32_t *st, uint32_t code) {
+  if (st) atomicOr(st, 1u << code);
+}
+
+// Copies the meshlet's payload block into shared memory (16-byte vectors).
+__device__ __forceinline__ void stage_payload(const Desc &d, const uint8_t *payload,
+                                              uint32_t *sw, uint32_t lane) {
+  const uint4 *src = reinterpret_cast<const uint4 *>(payload) + d.off16;
+  uint4 *dst = reinterpret_cast<uint4 *>(sw);
+  uint32_t n4 = (block_words(d) + 3) >> 2;
+  for (uint32_t i = lane; i < n4; i += 32) dst[i] = __ldg(src + i);
+}
+
+// Builds the strip stream I[0..T+1] in shared memory (sI).  CHECKED: returns
+// false (warp-uniform) when the stream contradicts V, R or reuse bounds.
+template <bool CHECKED>
+__device__ __forceinline__ bool build_stream(const Desc &d, const uint32_t *sw, uint8_t *sI,
+                                             uint32_t lane) {
+  const uint32_t nw = (d.T + 31) >> 5;
+  const uint32_t ro = 2 * nw;  // reuse section (words)
+  if (lane < 3) sI[lane] = (uint8_t)lane;
+  uint32_t base = 0;
+  bool bad = false;
+  const uint32_t le = (2u << lane) - 1u;  // bits 0..lane
+  for (uint32_t i = 0; i < nw; i++) {
+    uint32_t inc = sw[nw + i];
+    uint32_t k = 32 * i + lane;
+    uint32_t s = 2 + base + __popc(inc & le);
+    if (k >= 1 && k < d.T) {
+      uint32_t n;
+      if ((inc >> lane) & 1u) {
+        n = s;
+      } else {
+        uint32_t slot = k + 1 - s;
+        n = extract(sw + ro, slot * d.w, d.w);
+        if (CHECKED && n > s) bad = true;  // entries seen so far: 0..s
+      }
+      if (CHECKED && n > 255) bad = true;
+      sI[k + 2] = (uint8_t)n;
+    }
+    base += __popc(inc);
+  }
+  if (CHECKED) {
+    if (base + 3 != d.V) bad = true;
+    if ((sw[0] & 1u) || (sw[nw] & 1u)) bad = true;
+    // bits past T' in the last flag words must be clear
+    uint32_t tail = d.T & 31u;
+    if (tail && ((sw[nw - 1] >> tail) | (sw[2 * nw - 1] >> tail))) bad = true;
+    bad = __any_sync(kFull, bad);
+  }
+  __syncwarp();
+  return !bad;
+}
+
+// Triangle k of the meshlet (sI built, flags in sw[0..nw)).
+__device__ __forceinline__ void triangle(const uint32_t *sw, const uint8_t *sI, uint32_t k,
+                                         uint32_t &a, uint32_t &b, uint32_t &c) {
+  const uint32_t wi = k >> 5, bit = k & 31u;
+  const uint32_t f = sw[wi];
+  const uint32_t fk = (f >> bit) & 1u;
+  const uint32_t inv = 0u - fk;  // all ones when flag k is set
+  uint32_t x = (f ^ inv) & ((1u << bit) - 1u);
+  int j = -1;
+  if (x) {
+    j = (int)(32 * wi + 31 - __clz(x));
+  } else {
+    for (int w = (int)wi - 1; w >= 0; w--) {
+      uint32_t y = sw[w] ^ inv;
+      if (y) {
+        j = 32 * w + 31 - __clz(y);
+        break;
+      }
+    }
+  }
+  const uint32_t old = sI[j + 1];
+  const uint32_t prev = sI[k + 1];
+  const uint32_t cur = sI[k + 2];
+  a = fk ? prev : old;
+  b = fk ? old : prev;
+  c = cur;
+}
+
+}  // namespace mcdev

@@ -1,0 +1,353 @@
+// Decode kernels for sm_103a: plain (one warp per meshlet, grid over a
+// meshlet range), batched (persistent CTAs pulling meshlets from a device work
+// queue) and fused decode + cull + compaction.
+#include <cuda_runtime.h>
+
+#include "decode_warp.cuh"
+#include "kernels.h"
+
+namespace mcdev {
+
+// Per-warp shared memory: payload words, then the strip stream (260 bytes).
+__host__ __device__ inline uint32_t warp_words(uint32_t max_block_words) {
+  uint32_t w = max_block_words < 80 ? 80 : max_block_words;
+  return (w + 8 + 3) & ~3u;
+}
+__host__ __device__ inline uint32_t warp_smem_bytes(uint32_t max_block_words) {
+  return 4 * warp_words(max_block_words) + 272;
+}
+uint32_t decode_smem_per_warp(uint32_t max_block_words) { return warp_smem_bytes(max_block_words); }
+uint32_t cull_smem_per_warp(uint32_t max_block_words) {
+  // + clip (x, y, w) per vertex + survivor triples
+  return warp_smem_bytes(max_block_words) + 3 * 4 * 256 + 3 * 4 * 256;
+}
+
+template <bool CHECKED>
+__device__ __forceinline__ void decode_one(const BatchArgs &a, uint32_t m, uint32_t *sw,
+                                           uint8_t *sI, uint32_t lane, uint8_t *out_local,
+                                           uint32_t *out_global, float *out_pos,
+                                           uint32_t *status) {
+  const Desc d = load_desc(a.desc + m);
+  if (!header_ok(d, a)) {
+    if (lane == 0) set_status(status, MC_ERR_CORRUPT);
+    return;
+  }
+  __syncwarp();
+  stage_payload(d, a.payload, sw, lane);
+  __syncwarp();
+  if (!build_stream<CHECKED>(d, sw, sI, lane)) {
+    if (lane == 0) set_status(status, MC_ERR_CORRUPT);
+    return;
+  }
+  // triangles
+  for (uint32_t k = lane; k < d.T; k += 32) {
+    uint32_t x, y, z;
+    triangle(sw, sI, k, x, y, z);
+    const uint64_t o = 3ull * (d.tbase + k);
+    if (out_local) {
+      out_local[o] = (uint8_t)x;
+      out_local[o + 1] = (uint8_t)y;
+      out_local[o + 2] = (uint8_t)z;
+    }
+    if (out_global) {
+      out_global[o] = d.vbase + x;
+      out_global[o + 1] = d.vbase + y;
+      out_global[o + 2] = d.vbase + z;
+    }
+  }
+  // vertices
+  const Grid g = load_grid(a.grids + d.grid);
+  const uint32_t *pw = sw + 2 * ((d.T + 31) >> 5) + ((d.T + 2 - d.V) * d.w + 31) / 32;
+  for (uint32_t v = lane; v < d.V; v += 32) {
+    const uint64_t o = 3ull * (d.vbase + v);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      uint32_t q = extract(pw, (3 * v + c) * d.b, d.b);
+      out_pos[o + c] = dequant(d.L[c] + q, g.G[c], g.D[c]);
+    }
+  }
+  __syncwarp();
+}
+
+template <bool CHECKED>
+__global__ void decode_plain_kernel(BatchArgs a, uint32_t first, uint32_t count,
+                                    uint32_t smem_per_warp, uint8_t *out_local,
+                                    uint32_t *out_global, float *out_pos, uint32_t *status) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  uint8_t *base = smem + warp * smem_per_warp;
+  uint32_t *sw = reinterpret_cast<uint32_t *>(base);
+  uint8_t *sI = base + smem_per_warp - 272;
+  const uint32_t i = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (i >= count) return;
+  decode_one<CHECKED>(a, first + i, sw, sI, lane, out_local, out_global, out_pos, status);
+}
+
+// Scratch words used by the persistent kernels.
+enum { kQueue = 0, kDone = 1, kCount = 2 };
+
+template <bool CHECKED>
+__global__ void decode_batch_kernel(BatchArgs a, uint32_t per_grab, uint32_t smem_per_warp,
+                                    uint8_t *out_local, uint32_t *out_global, float *out_pos,
+                                    uint32_t *status, uint32_t *scratch) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  uint8_t *base = smem + warp * smem_per_warp;
+  uint32_t *sw = reinterpret_cast<uint32_t *>(base);
+  uint8_t *sI = base + smem_per_warp - 272;
+  for (;;) {
+    uint32_t m0 = 0;
+    if (lane == 0) m0 = atomicAdd(scratch + kQueue, per_grab);
+    m0 = __shfl_sync(kFull, m0, 0);
+    if (m0 >= a.n_meshlets) break;
+    uint32_t m1 = min(a.n_meshlets, m0 + per_grab);
+    for (uint32_t m = m0; m < m1; m++)
+      decode_one<CHECKED>(a, m, sw, sI, lane, out_local, out_global, out_pos, status);
+  }
+  // the last CTA to finish leaves the queue reset for the next launch
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(scratch + kDone, 1u) == gridDim.x - 1) {
+      atomicExch(scratch + kQueue, 0u);
+      atomicExch(scratch + kDone, 0u);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- culling
+__device__ __forceinline__ float clip_row(const float *M, int r, float x, float y, float z) {
+  return __fmaf_rn(M[4 * r + 2], z, __fmaf_rn(M[4 * r + 1], y, __fmaf_rn(M[4 * r + 0], x, M[4 * r + 3])));
+}
+
+// true when all 8 corners of the meshlet's quantisation box are outside one
+// clip plane
+__device__ __forceinline__ bool box_outside(const Desc &d, const Grid &g, const float *M) {
+  float lo[3], hi[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    uint32_t top = d.L[c] + (d.b >= 32 ? 0xFFFFFFFFu : ((1u << d.b) - 1u));
+    lo[c] = dequant(d.L[c], g.G[c], g.D[c]);
+    hi[c] = dequant(top, g.G[c], g.D[c]);
+  }
+  bool any = false;
+#pragma unroll
+  for (int plane = 0; plane < 6; plane++) {
+    bool all_out = true;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      float x = (k & 1) ? hi[0] : lo[0];
+      float y = (k & 2) ? hi[1] : lo[1];
+      float z = (k & 4) ? hi[2] : lo[2];
+      float comp = clip_row(M, plane >> 1, x, y, z);
+      float w = clip_row(M, 3, x, y, z);
+      float dist = (plane & 1) ? __fsub_rn(w, comp) : __fadd_rn(w, comp);
+      all_out = all_out && (dist < 0.0f);
+    }
+    any = any || all_out;
+  }
+  return any;
+}
+
+template <bool CHECKED>
+__global__ void decode_cull_kernel(BatchArgs a, const float *view_proj, uint32_t smem_per_warp,
+                                   uint32_t *tri_out, uint32_t *tri_count, float *out_pos,
+                                   uint32_t *status, uint32_t *scratch) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ uint32_t s_meshlet[32];
+  __shared__ uint32_t s_cnt[32];
+  __shared__ uint32_t s_base;
+  __shared__ float s_M[16];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const uint32_t nwarps = blockDim.x >> 5;
+  uint8_t *base = smem + warp * smem_per_warp;
+  uint32_t *sw = reinterpret_cast<uint32_t *>(base);
+  const uint32_t ws = smem_per_warp - (3 * 4 * 256 + 3 * 4 * 256);  // decode part
+  uint8_t *sI = base + ws - 272;
+  float *cx = reinterpret_cast<float *>(base + ws);
+  float *cy = cx + 256;
+  float *cw = cy + 256;
+  uint32_t *surv = reinterpret_cast<uint32_t *>(cw + 256);
+  if (threadIdx.x < 16) s_M[threadIdx.x] = view_proj[threadIdx.x];
+  __syncthreads();
+  for (;;) {
+    // one round: every warp takes one meshlet of a chunk grabbed by the CTA
+    if (threadIdx.x == 0) s_base = atomicAdd(scratch + kQueue, nwarps);
+    __syncthreads();
+    const uint32_t m = s_base + warp;
+    const bool round_live = s_base < a.n_meshlets;
+    uint32_t n_keep = 0;
+    if (round_live && m < a.n_meshlets) {
+      const Desc d = load_desc(a.desc + m);
+      bool ok = header_ok(d, a);
+      if (!ok && lane == 0) set_status(status, MC_ERR_CORRUPT);
+      if (ok) {
+        const Grid g = load_grid(a.grids + d.grid);
+        if (!box_outside(d, g, s_M)) {
+          stage_payload(d, a.payload, sw, lane);
+          __syncwarp();
+          if (!build_stream<CHECKED>(d, sw, sI, lane)) {
+            if (lane == 0) set_status(status, MC_ERR_CORRUPT);
+          } else {
+            const uint32_t *pw = sw + 2 * ((d.T + 31) >> 5) + ((d.T + 2 - d.V) * d.w + 31) / 32;
+            for (uint32_t v = lane; v < d.V; v += 32) {
+              float p[3];
+#pragma unroll
+              for (int c = 0; c < 3; c++) {
+                uint32_t q = extract(pw, (3 * v + c) * d.b, d.b);
+                p[c] = dequant(d.L[c] + q, g.G[c], g.D[c]);
+              }
+              const uint64_t o = 3ull * (d.vbase + v);
+              out_pos[o] = p[0];
+              out_pos[o + 1] = p[1];
+              out_pos[o + 2] = p[2];
+              cx[v] = clip_row(s_M, 0, p[0], p[1], p[2]);
+              cy[v] = clip_row(s_M, 1, p[0], p[1], p[2]);
+              cw[v] = clip_row(s_M, 3, p[0], p[1], p[2]);
+            }
+            __syncwarp();
+            for (uint32_t k0 = 0; k0 < d.T; k0 += 32) {
+              const uint32_t k = k0 + lane;
+              bool keep = false;
+              uint32_t x = 0, y = 0, z = 0;
+              if (k < d.T) {
+                triangle(sw, sI, k, x, y, z);
+                if (x != y && y != z && x != z) {
+                  const float w0 = cw[x], w1 = cw[y], w2 = cw[z];
+                  if (w0 <= 0.0f || w1 <= 0.0f || w2 <= 0.0f) {
+                    keep = true;
+                  } else {
+                    const float x0 = cx[x], y0 = cy[x], x1 = cx[y], y1 = cy[y];
+                    const float x2 = cx[z], y2 = cy[z];
+                    const float c0 = __fmaf_rn(y1, w2, -__fmul_rn(w1, y2));
+                    const float c1 = __fmaf_rn(x1, w2, -__fmul_rn(w1, x2));
+                    const float c2 = __fmaf_rn(x1, y2, -__fmul_rn(y1, x2));
+                    const float det = __fmaf_rn(w0, c2, __fmaf_rn(-y0, c1, __fmul_rn(x0, c0)));
+                    keep = det > 0.0f;
+                  }
+                }
+              }
+              const uint32_t bal = __ballot_sync(kFull, keep);
+              if (keep) {
+                const uint32_t o = n_keep + __popc(bal & ((1u << lane) - 1u));
+                surv[3 * o] = d.vbase + x;
+                surv[3 * o + 1] = d.vbase + y;
+                surv[3 * o + 2] = d.vbase + z;
+              }
+              n_keep += __popc(bal);
+            }
+          }
+        }
+      }
+    }
+    if (lane == 0) s_cnt[warp] = n_keep;
+    __syncthreads();
+    if (!round_live) break;
+    if (threadIdx.x == 0) {
+      uint32_t tot = 0;
+      for (uint32_t w = 0; w < nwarps; w++) {
+        uint32_t c = s_cnt[w];
+        s_cnt[w] = tot;
+        tot += c;
+      }
+      s_meshlet[0] = tot ? atomicAdd(scratch + kCount, tot) : 0;
+    }
+    __syncthreads();
+    {
+      const uint32_t dst = s_meshlet[0] + s_cnt[warp];
+      __syncwarp();
+      for (uint32_t i = lane; i < 3 * n_keep; i += 32) tri_out[3ull * dst + i] = surv[i];
+    }
+    __syncthreads();
+  }
+  // the last CTA publishes the count and resets the scratch
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(scratch + kDone, 1u) == gridDim.x - 1) {
+      __threadfence();
+      *tri_count = atomicAdd(scratch + kCount, 0u);
+      atomicExch(scratch + kCount, 0u);
+      atomicExch(scratch + kQueue, 0u);
+      atomicExch(scratch + kDone, 0u);
+    }
+  }
+}
+
+// ------------------------------------------------------------- launchers
+cudaError_t launch_plain(const BatchArgs &a, uint32_t first, uint32_t count, uint32_t warps,
+                         uint32_t max_block_words, bool checked, uint8_t *out_local,
+                         uint32_t *out_global, float *out_pos, uint32_t *status,
+                         cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const uint32_t spw = warp_smem_bytes(max_block_words);
+  const uint32_t smem = spw * warps;
+  const uint32_t grid = (count + warps - 1) / warps;
+  if (checked) {
+    cudaFuncSetAttribute(decode_plain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    decode_plain_kernel<true><<<grid, warps * 32, smem, s>>>(a, first, count, spw, out_local,
+                                                             out_global, out_pos, status);
+  } else {
+    cudaFuncSetAttribute(decode_plain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    decode_plain_kernel<false><<<grid, warps * 32, smem, s>>>(a, first, count, spw, out_local,
+                                                              out_global, out_pos, status);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchArgs &a, uint32_t ctas, uint32_t warps, uint32_t per_grab,
+                         uint32_t max_block_words, bool checked, uint8_t *out_local,
+                         uint32_t *out_global, float *out_pos, uint32_t *status,
+                         uint32_t *scratch, cudaStream_t s) {
+  const uint32_t spw = warp_smem_bytes(max_block_words);
+  const uint32_t smem = spw * warps;
+  if (checked) {
+    cudaFuncSetAttribute(decode_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    decode_batch_kernel<true><<<ctas, warps * 32, smem, s>>>(a, per_grab, spw, out_local,
+                                                             out_global, out_pos, status, scratch);
+  } else {
+    cudaFuncSetAttribute(decode_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    decode_batch_kernel<false><<<ctas, warps * 32, smem, s>>>(a, per_grab, spw, out_local,
+                                                              out_global, out_pos, status, scratch);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cull(const BatchArgs &a, const float *view_proj, uint32_t ctas, uint32_t warps,
+                        uint32_t max_block_words, bool checked, uint32_t *tri_out,
+                        uint32_t *tri_count, float *out_pos, uint32_t *status, uint32_t *scratch,
+                        cudaStream_t s) {
+  const uint32_t spw = cull_smem_per_warp(max_block_words);
+  const uint32_t smem = spw * warps;
+  if (checked) {
+    cudaFuncSetAttribute(decode_cull_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    decode_cull_kernel<true><<<ctas, warps * 32, smem, s>>>(a, view_proj, spw, tri_out, tri_count,
+                                                            out_pos, status, scratch);
+  } else {
+    cudaFuncSetAttribute(decode_cull_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    decode_cull_kernel<false><<<ctas, warps * 32, smem, s>>>(a, view_proj, spw, tri_out, tri_count,
+                                                             out_pos, status, scratch);
+  }
+  return cudaGetLastError();
+}
+
+int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words) {
+  int n = 0;
+  const int smem = (int)(warp_smem_bytes(max_block_words) * warps);
+  cudaFuncSetAttribute(decode_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(decode_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_batch_kernel<false>, warps * 32,
+                                                warp_smem_bytes(max_block_words) * warps);
+  return n;
+}
+
+int max_ctas_per_sm_cull(uint32_t warps, uint32_t max_block_words) {
+  int n = 0;
+  const int smem = (int)(cull_smem_per_warp(max_block_words) * warps);
+  cudaFuncSetAttribute(decode_cull_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(decode_cull_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_cull_kernel<false>, warps * 32,
+                                                cull_smem_per_warp(max_block_words) * warps);
+  return n;
+}
+
+}  // namespace mcdev

@@ -1,0 +1,64 @@
+// Internal declarations of the host-side encoder (meshletize / stripify /
+// encode).  Not part of the C ABI.
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <functional>
+#include <thread>
+#include <vector>
+
+#include "meshlet_codec.h"
+
+namespace mc {
+
+// Runs fn(i) for i in [0, n) on up to `threads` workers, dynamic chunks.
+void parallel_for(uint64_t n, uint32_t threads, const std::function<void(uint64_t)> &fn,
+                  uint64_t chunk = 1);
+uint32_t default_threads(uint32_t requested);
+
+// One meshlet's generalized triangle strip (Sec. 2, 4.2).
+struct StripOut {
+  uint32_t tp = 0;      // T' (triangles incl. restart degenerates)
+  uint32_t strips = 0;  // number of strips (restarts + 1)
+  std::vector<uint32_t> stream;  // T'+2 global vertex ids
+  std::vector<uint8_t> flags;    // T' flags, 1 = right
+  std::vector<uint32_t> order;   // list positions in strip order
+};
+
+// Per-thread scratch of the strip builder.
+struct StripScratch {
+  std::vector<uint64_t> keys;
+  std::vector<int32_t> nb;
+  std::vector<uint8_t> visited;
+};
+
+// Greedy strip over the triangles tri[ids[i]], i = list position.
+void build_strip(const uint32_t *tri, const uint32_t *ids, uint32_t T, StripScratch &s,
+                 StripOut &out);
+
+}  // namespace mc
+
+// Final meshlets of one mesh: triangle grouping plus the strip of each.
+struct mc_meshlets {
+  uint32_t n_tris = 0, n_verts = 0;
+  uint32_t n_grown = 0;
+  std::vector<uint32_t> tri;          // triangle ids grouped by meshlet
+  std::vector<uint32_t> start;        // meshlet offsets into tri (count + 1)
+  std::vector<uint64_t> stream_start; // meshlet offsets into stream (count + 1)
+  std::vector<uint32_t> stream;       // strip entries (global vertex ids)
+  std::vector<uint8_t> flags;         // one per strip triangle, same offsets - 2*m
+  std::vector<uint16_t> tp;           // T' per meshlet
+  std::vector<uint16_t> strips;       // strips per meshlet
+};
+
+struct mc_blob {
+  std::vector<mc_desc> desc;
+  std::vector<uint8_t> payload;
+  std::vector<mc_grid> grids;
+  std::vector<mc_mesh_info> meshes;
+  std::vector<uint32_t> vmap;
+  uint64_t total_tris = 0, total_verts = 0, input_tris = 0;
+  uint64_t restarts = 0, split_meshlets = 0, conn_bits = 0, pos_bits_total = 0;
+  uint32_t max_block_words = 0, max_tris = 0;
+};

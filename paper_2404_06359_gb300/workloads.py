@@ -1,0 +1,91 @@
+"""The benchmark workloads, built through the library's own host encoder.
+
+  cfg1  64x64-quad jittered grid, 8,192 triangles; meshlets 64/126; b = 16,
+        w = 8; u8 local indices + FP32 positions; plain one-launch decode.
+  cfg2  256 UV-spheres / tori, triangles log-uniform in [10k, 200k]
+        (~16 M total), 1% normal noise; meshlets 64/126; b = 16, w = 8;
+        u8 + u32 + FP32; one persistent launch.
+  cfg3  disc height field of ~50 M triangles (4-octave value noise), three
+        120-degree sectors meshletized at 64/126, 128/128 and 256/256;
+        w = ceil(log2 V); b drawn from {12, 16, 20} per meshlet; meshlets
+        shuffled; one persistent launch.
+  cfg4  cfg2's generator grown to >= 50 M triangles on a 3-D lattice, fused
+        decode + frustum/back-face cull + compaction under 64 camera poses
+        (60 degree FOV), one CUDA graph.
+All inputs are seeded; see meshgen for the recipes.
+"""
+from __future__ import annotations
+
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+from . import codec as mc
+from . import meshgen as G
+
+SEEDS = {1: G.SEED_BASE + 1, 2: G.SEED_BASE + 2, 3: G.SEED_BASE + 3, 4: G.SEED_BASE + 4}
+
+
+def _threads():
+    return os.cpu_count() or 4
+
+
+def encode_meshes(meshes, limits=((64, 126),), pos_bits=16, reuse_mode=0):
+    """Encode each mesh (in parallel, one thread per mesh) and concatenate."""
+    def enc(i):
+        m = meshes[i]
+        ml = mc.mc_meshletize(m.tris, m.n_verts, limits, m.tri_class, n_threads=1)
+        return mc.mc_encode(ml, m.pos, pos_bits, reuse_mode, mesh_id=i, n_threads=1)
+    with ThreadPoolExecutor(_threads()) as ex:
+        blobs = list(ex.map(enc, range(len(meshes))))
+    return mc.mc_blob_concat(blobs)
+
+
+def cfg1():
+    mesh = G.grid_mesh(64, 0.25, SEEDS[1])
+    ml = mc.mc_meshletize(mesh.tris, mesh.n_verts, [(64, 126)])
+    return mc.mc_encode(ml, mesh.pos, 16, 0), [mesh]
+
+
+def cfg2(rank: int = 0):
+    meshes = G.surface_batch(256, 10_000, 200_000, SEEDS[2] + 1000 * rank)
+    return encode_meshes(meshes), meshes
+
+
+def cfg3(rank: int = 0, total_tris: int = 50_000_000):
+    seed = SEEDS[3] + 1000 * rank
+    mesh = G.height_field_disc(total_tris, seed)
+    ml = mc.mc_meshletize(mesh.tris, mesh.n_verts, list(G.SECTOR_LIMITS), mesh.tri_class)
+    n = ml.count
+    bits = G.meshlet_bits(n, seed + 1)
+    order = G.meshlet_permutation(n, seed + 2)
+    return mc.mc_encode(ml, mesh.pos, bits, 1, order), [mesh]
+
+
+def cfg4(rank: int = 0, min_tris: int = 50_000_000, n_views: int = 64):
+    meshes = G.surface_batch(256, 10_000, 200_000, SEEDS[2] + 1000 * rank, min_total_tris=min_tris)
+    blob = encode_meshes(meshes)
+    lo = np.min([m.pos.min(0) for m in meshes], 0).astype(np.float64)
+    hi = np.max([m.pos.max(0) for m in meshes], 0).astype(np.float64)
+    center = 0.5 * (lo + hi)
+    radius = float(np.linalg.norm(hi - lo) / 2)
+    vps = G.camera_poses(n_views, center, radius, SEEDS[4] + rank)
+    return blob, meshes, vps
+
+
+def algorithmic_bytes(stats: dict, desc: np.ndarray, local=True, global_=True) -> dict:
+    """Bytes one decode must move: compressed input read (descriptors, payload
+    without block padding, grids) and decoded output written."""
+    w = desc.view(np.uint32).reshape(-1, 8)
+    V = (w[:, 3] & 0xFFFF).astype(np.int64)
+    T = (w[:, 3] >> 16).astype(np.int64)
+    rw = (w[:, 4] & 0xFF).astype(np.int64)
+    b = ((w[:, 4] >> 8) & 0xFF).astype(np.int64)
+    R = T + 2 - V
+    words = 2 * ((T + 31) // 32) + (R * rw + 31) // 32 + (3 * V * b + 31) // 32
+    read = 32 * w.shape[0] + 4 * int(words.sum()) + 32 * stats["n_grids"]
+    Tt, Vt = int(T.sum()), int(V.sum())
+    write = (3 * Tt if local else 0) + (12 * Tt if global_ else 0) + 12 * Vt
+    return {"read": read, "write": write, "total": read + write,
+            "padding": 4 * int(((words + 3) // 4 * 4 - words).sum())}
