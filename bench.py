@@ -235,6 +235,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--tuning", default="", help="warps,ctas_per_sm,meshlets_per_grab (skips the autotuner)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
@@ -280,10 +281,14 @@ def main():
             launches_per_step = 1
             tune = {"warps_per_cta": 4}
         else:
-            tune, tune_ms = mc.mc_autotune(db, out["local"], out["global"], out["pos"], out["status"],
-                                           scratch, stream)
+            if args.tuning:
+                w_, c_, g_ = (int(x) for x in args.tuning.split(","))
+                tune = mc.mc_tuning(w_, c_, g_, 0)
+            else:
+                tune, tune_ms = mc.mc_autotune(db, out["local"], out["global"], out["pos"],
+                                               out["status"], scratch, stream)
             graph = mc.mc_graph_capture_batch(db, out["local"], out["global"], out["pos"],
-                                              out["status"], scratch, None, stream)
+                                              out["status"], scratch, tune, stream)
             launches_per_step = 1
             extra["tuning"] = {"warps_per_cta": tune.warps_per_cta, "ctas_per_sm": tune.ctas_per_sm,
                                "meshlets_per_grab": tune.meshlets_per_grab}

@@ -28,6 +28,8 @@ planar meshes).
 from __future__ import annotations
 
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -208,7 +210,24 @@ def _hash32(ix: np.ndarray, iy: np.ndarray, octave: int, seed: int) -> np.ndarra
 def value_noise(x: np.ndarray, y: np.ndarray, seed: int, octaves: int = 4,
                 base_period: float = 512.0, amplitude: float = 64.0) -> np.ndarray:
     """Sum of ``octaves`` layers of lattice value noise with smoothstep
-    interpolation; each octave doubles the frequency and halves the amplitude."""
+    interpolation; each octave doubles the frequency and halves the amplitude.
+    Evaluated in parallel chunks (pointwise, so the result does not depend on
+    the chunking)."""
+    n = x.shape[0]
+    chunk = 1 << 20
+    if n <= chunk:
+        return _value_noise(x, y, seed, octaves, base_period, amplitude)
+    out = np.empty(n, np.float64)
+
+    def run(i):
+        sl = slice(i, min(n, i + chunk))
+        out[sl] = _value_noise(x[sl], y[sl], seed, octaves, base_period, amplitude)
+    with ThreadPoolExecutor(os.cpu_count() or 4) as ex:
+        list(ex.map(run, range(0, n, chunk)))
+    return out
+
+
+def _value_noise(x, y, seed, octaves, base_period, amplitude):
     out = np.zeros(x.shape, np.float64)
     freq, amp = 1.0 / base_period, amplitude
     with np.errstate(over="ignore"):
