@@ -84,7 +84,9 @@ typedef struct {
 } mc_desc;
 
 /* Global quantisation grid (Sec. 4.4): x = G + g * Delta for grid coordinate
- * g = L + q.  One entry per mesh and position bit width. */
+ * g = L + q, evaluated in FP32 as fmaf((float)g, Delta, G) when g < 2^24 and
+ * as fmaf((float)(g & 0xFFF), Delta, fmaf((float)(g >> 12), 4096 Delta, G))
+ * otherwise.  One entry per mesh and position bit width. */
 typedef struct {
   float G[3];
   uint32_t pos_bits;

@@ -14,8 +14,11 @@
  * Dequantisation (Sec. 4.4): integer add g = L_c + q, then the grid
  * coordinate maps back to float as G_c + g * Delta_c.  In FP32 this oracle
  * fixes the evaluation order
- *     x = fmaf((float)(g & 0xFFF), Delta, fmaf((float)(g >> 12), Delta * 4096, G))
- * (both integer-to-float conversions and the power-of-two scale are exact);
+ *     g < 2^24:  x = fmaf((float)g, Delta, G)           (one rounding)
+ *     otherwise: x = fmaf((float)(g & 0xFFF), Delta,
+ *                         fmaf((float)(g >> 12), Delta * 4096, G))
+ * (every integer-to-float conversion and the power-of-two scale are exact,
+ * and x depends on g alone, so shared boundary vertices stay crack-free);
  * the FP64 reference is G + g * Delta in double.
  *
  * Culling: a meshlet is dropped when all 8 corners of its quantisation box
@@ -53,6 +56,7 @@ static uint32_t get_bits(const uint8_t *words, uint64_t bit, uint32_t nbits) {
 }
 
 float orc_dequant32(uint32_t g, float G, float D) {
+  if (g < (1u << 24)) return fmaf((float)g, D, G); /* (float)g is exact */
   float hi = (float)(g >> 12);
   float lo = (float)(g & 0xFFFu);
   float D4096 = D * 4096.0f;

@@ -96,7 +96,8 @@ int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
 void orc_blob_free(orc_blob *b);
 
 /* FP32 dequantisation of a grid coordinate g (Sec. 4.4):
- *   x = fmaf((float)(g & 0xFFF), D, fmaf((float)(g >> 12), D * 4096, G)). */
+ *   g < 2^24:  x = fmaf((float)g, D, G)
+ *   otherwise: x = fmaf((float)(g & 0xFFF), D, fmaf((float)(g >> 12), D * 4096, G)). */
 float orc_dequant32(uint32_t g, float G, float D);
 
 /* Sequential decode of one meshlet (descriptor desc32) into

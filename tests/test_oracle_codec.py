@@ -251,15 +251,19 @@ def _ulp(x: float) -> Fraction:
 
 
 def test_dequant32_against_exact_rationals():
-    """x32 = fma(lo, D, fma(hi, 4096 D, G)) has two roundings, so
-    |x32 - (G + g D)| <= ulp(inner)/2 + ulp(x32)/2 in exact arithmetic."""
+    """g < 2^24: one correctly rounded fma, |x32 - (G + g D)| <= ulp(x32)/2.
+    Larger g: x32 = fma(lo, D, fma(hi, 4096 D, G)) has two roundings, so
+    |x32 - (G + g D)| <= ulp(inner)/2 + ulp(x32)/2, in exact arithmetic."""
     rng = np.random.Generator(np.random.PCG64(9))
-    for _ in range(4000):
-        g = int(rng.integers(0, 2 ** 32))
+    for i in range(6000):
+        g = int(rng.integers(0, 2 ** 32)) if i % 2 else int(rng.integers(0, 2 ** 24))
         Gf = np.float32(rng.normal() * 10.0 ** int(rng.integers(-3, 4)))
         Df = np.float32(abs(rng.normal()) * 10.0 ** int(rng.integers(-9, -1)))
         x = O.dequant32(g, float(Gf), float(Df))
         exact = Fraction(float(Gf)) + g * Fraction(float(Df))
+        if g < 2 ** 24:
+            assert abs(Fraction(x) - exact) <= _ulp(x) / 2, (g, Gf, Df)
+            continue
         inner = float(np.float32(Fraction(float(Gf)) + (g >> 12) * 4096 * Fraction(float(Df))))
         assert abs(Fraction(x) - exact) <= (_ulp(inner) + _ulp(x)) / 2, (g, Gf, Df)
     # exact when everything is representable: G + g D with small g, D = 2^-k
