@@ -89,8 +89,9 @@ mc_tuning resolve_batch(const mc_device_batch *b, const mc_tuning *t) {
   }
   if (!r.warps_per_cta) r.warps_per_cta = 8;
   if (!r.meshlets_per_grab) r.meshlets_per_grab = 2;
+  if (r.meshlets_per_grab > 16) r.meshlets_per_grab = 16;
   if (!r.ctas_per_sm) {
-    int occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words);
+    int occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, r.meshlets_per_grab);
     r.ctas_per_sm = occ > 0 ? (uint32_t)occ : 1;
   }
   return r;
@@ -99,8 +100,10 @@ mc_tuning resolve_batch(const mc_device_batch *b, const mc_tuning *t) {
 mc_status launch_batch_checked(const mc_device_batch *b, uint8_t *d_local, uint32_t *d_global,
                                float *d_pos, uint32_t *d_status, void *d_scratch,
                                const mc_tuning &r, cudaStream_t s) {
-  if (r.warps_per_cta < 1 || r.warps_per_cta > 32 || r.meshlets_per_grab < 1) return MC_ERR_INVALID_ARG;
-  int occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words);
+  if (r.warps_per_cta < 1 || r.warps_per_cta > 32 || r.meshlets_per_grab < 1 ||
+      r.meshlets_per_grab > 16)
+    return MC_ERR_INVALID_ARG;
+  int occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, r.meshlets_per_grab);
   if (occ <= 0) return MC_ERR_INVALID_ARG;
   uint32_t per_sm = std::min<uint32_t>(r.ctas_per_sm, (uint32_t)occ);
   uint32_t ctas = per_sm * (uint32_t)sm_count();
@@ -195,12 +198,12 @@ extern "C" mc_status mc_autotune(const mc_device_batch *b, uint8_t *d_local, uin
   mc_tuning bt{};
   float bms = 1e30f;
   const uint32_t warps_c[] = {4, 8, 16};
-  const uint32_t grab_c[] = {1, 2, 4, 8};
+  const uint32_t grab_c[] = {1, 2, 4, 8, 16};
   st = MC_OK;
   for (uint32_t w : warps_c) {
-    int occ = max_ctas_per_sm_batch(w, b->max_block_words);
-    if (occ <= 0) continue;
     for (uint32_t g : grab_c) {
+      int occ = max_ctas_per_sm_batch(w, b->max_block_words, g);
+      if (occ <= 0) continue;
       for (uint32_t frac = 0; frac < 2; frac++) {
         mc_tuning c{};
         c.warps_per_cta = w;

@@ -15,7 +15,10 @@
 //   triangle (Sec. 4.2, orientation by the flag): R -> (I[k+1], old, I[k+2]),
 //     L -> (old, I[k+1], I[k+2]).
 //   position (Sec. 4.4): g = L_c + q (q = b bits at (3v+c) b), then
+//     x = fma((float)g, D, G) for g < 2^24, else
 //     x = fma((float)(g & 0xFFF), D, fma((float)(g >> 12), 4096 D, G)).
+// The common widths -- 8-bit reuse entries and 16-bit position fields -- are
+// read with byte / halfword shared-memory loads instead of funnel shifts.
 #pragma once
 
 #include <cstdint>
@@ -25,14 +28,14 @@
 namespace mcdev {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kSlackWords = 88;  // over-read margin after a staged payload
+constexpr uint32_t kStreamBytes = 272;
 
 struct Desc {
   uint32_t off16, vbase, tbase, V, T, w, b, grid, L[3];
 };
 
-__device__ __forceinline__ Desc load_desc(const mc_desc *d) {
-  const uint4 *p = reinterpret_cast<const uint4 *>(d);
-  uint4 a = __ldg(p), c = __ldg(p + 1);
+__device__ __forceinline__ Desc unpack_desc(uint4 a, uint4 c) {
   Desc r;
   r.off16 = a.x;
   r.vbase = a.y;
@@ -48,9 +51,13 @@ __device__ __forceinline__ Desc load_desc(const mc_desc *d) {
   return r;
 }
 
+__device__ __forceinline__ Desc load_desc(const mc_desc *d) {
+  const uint4 *p = reinterpret_cast<const uint4 *>(d);
+  return unpack_desc(__ldg(p), __ldg(p + 1));
+}
+
 struct Grid {
   float G[3], D[3];
-  uint32_t b;
 };
 
 __device__ __forceinline__ Grid load_grid(const mc_grid *g) {
@@ -60,7 +67,6 @@ __device__ __forceinline__ Grid load_grid(const mc_grid *g) {
   r.G[0] = __uint_as_float(a.x);
   r.G[1] = __uint_as_float(a.y);
   r.G[2] = __uint_as_float(a.z);
-  r.b = a.w;
   r.D[0] = __uint_as_float(c.x);
   r.D[1] = __uint_as_float(c.y);
   r.D[2] = __uint_as_float(c.z);
@@ -80,21 +86,19 @@ struct BatchArgs {
   const mc_grid *grids;
   uint32_t n_meshlets, n_grids;
   uint64_t payload_bytes, total_tris, total_verts;
-  uint32_t max_block_words;  // capacity of the per-warp shared-memory slot
+  uint32_t max_block_words;  // capacity of one meshlet's shared-memory slot
 };
 
 // Header sanity (all builds): a descriptor that passes cannot make the decode
 // read or write outside its buffers.
 __device__ __forceinline__ bool header_ok(const Desc &d, const BatchArgs &a) {
-  if (d.V < 3 || d.V > 256 || d.T < 1 || d.T > 256 || d.V > d.T + 2) return false;
-  if (d.w < 1 || d.w > 8 || d.b < 1 || d.b > 32 || d.grid >= a.n_grids) return false;
+  bool ok = d.V >= 3 && d.V <= 256 && d.T >= 1 && d.T <= 256 && d.V <= d.T + 2 && d.w >= 1 &&
+            d.w <= 8 && d.b >= 1 && d.b <= 32 && d.grid < a.n_grids;
+  if (!ok) return false;
   const uint32_t padded = (block_words(d) + 3) & ~3u;
-  if (padded > a.max_block_words) return false;
-  uint64_t end = 16ull * d.off16 + 4ull * padded;
-  if (end > a.payload_bytes) return false;
-  if ((uint64_t)d.tbase + d.T > a.total_tris || (uint64_t)d.vbase + d.V > a.total_verts)
-    return false;
-  return true;
+  return padded <= a.max_block_words &&
+         16ull * d.off16 + 4ull * padded <= a.payload_bytes &&
+         (uint64_t)d.tbase + d.T <= a.total_tris && (uint64_t)d.vbase + d.V <= a.total_verts;
 }
 
 __device__ __forceinline__ uint32_t extract(const uint32_t *w, uint32_t bit, uint32_t nbits) {
@@ -103,18 +107,22 @@ __device__ __forceinline__ uint32_t extract(const uint32_t *w, uint32_t bit, uin
   return nbits >= 32 ? v : (v & ((1u << nbits) - 1u));
 }
 
+// Grid coordinate -> FP32 (the evaluation order of Sec. 4.4 fixed above).
+__device__ __forceinline__ float dequant_small(uint32_t g, float G, float D) {
+  return __fmaf_rn(__uint2float_rn(g), D, G);
+}
 __device__ __forceinline__ float dequant(uint32_t g, float G, float D) {
+  if (g < (1u << 24)) return dequant_small(g, G, D);
   float hi = __uint2float_rn(g >> 12);
   float lo = __uint2float_rn(g & 0xFFFu);
-  float D4096 = __fmul_rn(D, 4096.0f);
-  return __fmaf_rn(lo, D, __fmaf_rn(hi, D4096, G));
+  return __fmaf_rn(lo, D, __fmaf_rn(hi, __fmul_rn(D, 4096.0f), G));
 }
 
 __device__ __forceinline__ void set_status(uint32_t *st, uint32_t code) {
   if (st) atomicOr(st, 1u << code);
 }
 
-// Copies the meshlet's payload block into shared memory (16-byte vectors).
+// Copies one meshlet's payload block into shared memory (16-byte vectors).
 __device__ __forceinline__ void stage_payload(const Desc &d, const uint8_t *payload,
                                               uint32_t *sw, uint32_t lane) {
   const uint4 *src = reinterpret_cast<const uint4 *>(payload) + d.off16;
@@ -125,26 +133,27 @@ __device__ __forceinline__ void stage_payload(const Desc &d, const uint8_t *payl
 
 // Builds the strip stream I[0..T+1] in shared memory (sI).  CHECKED: returns
 // false (warp-uniform) when the stream contradicts V, R or reuse bounds.
-template <bool CHECKED>
+template <bool CHECKED, bool W8>
 __device__ __forceinline__ bool build_stream(const Desc &d, const uint32_t *sw, uint8_t *sI,
                                              uint32_t lane) {
   const uint32_t nw = (d.T + 31) >> 5;
-  const uint32_t ro = 2 * nw;  // reuse section (words)
+  const uint32_t *rw = sw + 2 * nw;  // reuse section
+  const uint8_t *rb = reinterpret_cast<const uint8_t *>(rw);
   if (lane < 3) sI[lane] = (uint8_t)lane;
-  uint32_t base = 0;
+  uint32_t base = 2;
   bool bad = false;
   const uint32_t le = (2u << lane) - 1u;  // bits 0..lane
   for (uint32_t i = 0; i < nw; i++) {
-    uint32_t inc = sw[nw + i];
-    uint32_t k = 32 * i + lane;
-    uint32_t s = 2 + base + __popc(inc & le);
+    const uint32_t inc = sw[nw + i];
+    const uint32_t k = 32 * i + lane;
+    const uint32_t s = base + __popc(inc & le);
     if (k >= 1 && k < d.T) {
       uint32_t n;
       if ((inc >> lane) & 1u) {
         n = s;
       } else {
-        uint32_t slot = k + 1 - s;
-        n = extract(sw + ro, slot * d.w, d.w);
+        const uint32_t slot = k + 1 - s;
+        n = W8 ? rb[slot] : extract(rw, slot * d.w, d.w);
         if (CHECKED && n > s) bad = true;  // entries seen so far: 0..s
       }
       if (CHECKED && n > 255) bad = true;
@@ -153,10 +162,10 @@ __device__ __forceinline__ bool build_stream(const Desc &d, const uint32_t *sw, 
     base += __popc(inc);
   }
   if (CHECKED) {
-    if (base + 3 != d.V) bad = true;
+    if (base + 1 != d.V) bad = true;
     if ((sw[0] & 1u) || (sw[nw] & 1u)) bad = true;
     // bits past T' in the last flag words must be clear
-    uint32_t tail = d.T & 31u;
+    const uint32_t tail = d.T & 31u;
     if (tail && ((sw[nw - 1] >> tail) | (sw[2 * nw - 1] >> tail))) bad = true;
     bad = __any_sync(kFull, bad);
   }
@@ -171,13 +180,13 @@ __device__ __forceinline__ void triangle(const uint32_t *sw, const uint8_t *sI, 
   const uint32_t f = sw[wi];
   const uint32_t fk = (f >> bit) & 1u;
   const uint32_t inv = 0u - fk;  // all ones when flag k is set
-  uint32_t x = (f ^ inv) & ((1u << bit) - 1u);
+  const uint32_t x = (f ^ inv) & ((1u << bit) - 1u);
   int j = -1;
   if (x) {
     j = (int)(32 * wi + 31 - __clz(x));
   } else {
     for (int w = (int)wi - 1; w >= 0; w--) {
-      uint32_t y = sw[w] ^ inv;
+      const uint32_t y = sw[w] ^ inv;
       if (y) {
         j = 32 * w + 31 - __clz(y);
         break;
@@ -190,6 +199,85 @@ __device__ __forceinline__ void triangle(const uint32_t *sw, const uint8_t *sI, 
   a = fk ? prev : old;
   b = fk ? old : prev;
   c = cur;
+}
+
+// Position fields of vertex v (q for x, y, z).
+template <bool B16>
+__device__ __forceinline__ void vertex_q(const uint32_t *pw, uint32_t v, uint32_t b, uint32_t q[3]) {
+  if (B16) {
+    const uint16_t *p = reinterpret_cast<const uint16_t *>(pw) + 3 * v;
+    q[0] = p[0];
+    q[1] = p[1];
+    q[2] = p[2];
+  } else {
+    const uint32_t bit = 3 * v * b;
+    q[0] = extract(pw, bit, b);
+    q[1] = extract(pw, bit + b, b);
+    q[2] = extract(pw, bit + 2 * b, b);
+  }
+}
+
+// true when every grid coordinate of the meshlet is below 2^24
+__device__ __forceinline__ bool small_coords(const Desc &d) {
+  if (d.b > 24) return false;
+  const uint32_t lim = (1u << 24) - (1u << d.b);  // L + 2^b - 1 < 2^24
+  return d.L[0] <= lim && d.L[1] <= lim && d.L[2] <= lim;
+}
+
+// Full decode of one staged meshlet into the batch outputs.
+template <bool CHECKED, bool B16, bool W8>
+__device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, const uint32_t *sw,
+                                              uint8_t *sI, uint32_t lane, uint8_t *out_local,
+                                              uint32_t *out_global, float *out_pos) {
+  if (!build_stream<CHECKED, W8>(d, sw, sI, lane)) return false;
+  const uint32_t nw = (d.T + 31) >> 5;
+  uint8_t *ol = out_local ? out_local + 3ull * d.tbase : nullptr;
+  uint32_t *og = out_global ? out_global + 3ull * d.tbase : nullptr;
+  for (uint32_t k = lane; k < d.T; k += 32) {
+    uint32_t x, y, z;
+    triangle(sw, sI, k, x, y, z);
+    if (ol) {
+      ol[3 * k] = (uint8_t)x;
+      ol[3 * k + 1] = (uint8_t)y;
+      ol[3 * k + 2] = (uint8_t)z;
+    }
+    if (og) {
+      og[3 * k] = d.vbase + x;
+      og[3 * k + 1] = d.vbase + y;
+      og[3 * k + 2] = d.vbase + z;
+    }
+  }
+  const uint32_t *pw = sw + 2 * nw + ((d.T + 2 - d.V) * d.w + 31) / 32;
+  float *op = out_pos + 3ull * d.vbase;
+  if (small_coords(d)) {
+    for (uint32_t v = lane; v < d.V; v += 32) {
+      uint32_t q[3];
+      vertex_q<B16>(pw, v, d.b, q);
+#pragma unroll
+      for (int c = 0; c < 3; c++) op[3 * v + c] = dequant_small(d.L[c] + q[c], g.G[c], g.D[c]);
+    }
+  } else {
+    for (uint32_t v = lane; v < d.V; v += 32) {
+      uint32_t q[3];
+      vertex_q<B16>(pw, v, d.b, q);
+#pragma unroll
+      for (int c = 0; c < 3; c++) op[3 * v + c] = dequant(d.L[c] + q[c], g.G[c], g.D[c]);
+    }
+  }
+  __syncwarp();
+  return true;
+}
+
+template <bool CHECKED>
+__device__ __forceinline__ bool decode_dispatch(const Desc &d, const Grid &g, const uint32_t *sw,
+                                                uint8_t *sI, uint32_t lane, uint8_t *out_local,
+                                                uint32_t *out_global, float *out_pos) {
+  if (d.b == 16) {
+    if (d.w == 8) return decode_staged<CHECKED, true, true>(d, g, sw, sI, lane, out_local, out_global, out_pos);
+    return decode_staged<CHECKED, true, false>(d, g, sw, sI, lane, out_local, out_global, out_pos);
+  }
+  if (d.w == 8) return decode_staged<CHECKED, false, true>(d, g, sw, sI, lane, out_local, out_global, out_pos);
+  return decode_staged<CHECKED, false, false>(d, g, sw, sI, lane, out_local, out_global, out_pos);
 }
 
 }  // namespace mcdev

@@ -8,15 +8,22 @@
 
 namespace mcdev {
 
-// Per-warp shared memory: payload words, then the strip stream (260 bytes).
+// Per-warp shared memory of the single-meshlet kernels: payload words (plus
+// over-read slack), then the strip stream.
 __host__ __device__ inline uint32_t warp_words(uint32_t max_block_words) {
-  uint32_t w = max_block_words < 80 ? 80 : max_block_words;
-  return (w + 8 + 3) & ~3u;
+  return ((max_block_words + 3) & ~3u) + kSlackWords;
 }
 __host__ __device__ inline uint32_t warp_smem_bytes(uint32_t max_block_words) {
-  return 4 * warp_words(max_block_words) + 272;
+  return 4 * warp_words(max_block_words) + kStreamBytes;
+}
+// Batched kernel: descriptors of one grab, the grab's payload blocks, stream.
+__host__ __device__ inline uint32_t grab_words(uint32_t max_block_words, uint32_t per_grab) {
+  return 8 * per_grab + per_grab * ((max_block_words + 3) & ~3u) + kSlackWords;
 }
 uint32_t decode_smem_per_warp(uint32_t max_block_words) { return warp_smem_bytes(max_block_words); }
+uint32_t batch_smem_per_warp(uint32_t max_block_words, uint32_t per_grab) {
+  return 4 * grab_words(max_block_words, per_grab) + kStreamBytes;
+}
 uint32_t cull_smem_per_warp(uint32_t max_block_words) {
   // + clip (x, y, w) per vertex + survivor triples
   return warp_smem_bytes(max_block_words) + 3 * 4 * 256 + 3 * 4 * 256;
@@ -32,40 +39,11 @@ __device__ __forceinline__ void decode_one(const BatchArgs &a, uint32_t m, uint3
     if (lane == 0) set_status(status, MC_ERR_CORRUPT);
     return;
   }
-  __syncwarp();
+  const Grid g = load_grid(a.grids + d.grid);
   stage_payload(d, a.payload, sw, lane);
   __syncwarp();
-  if (!build_stream<CHECKED>(d, sw, sI, lane)) {
-    if (lane == 0) set_status(status, MC_ERR_CORRUPT);
-    return;
-  }
-  // triangles
-  for (uint32_t k = lane; k < d.T; k += 32) {
-    uint32_t x, y, z;
-    triangle(sw, sI, k, x, y, z);
-    const uint64_t o = 3ull * (d.tbase + k);
-    if (out_local) {
-      out_local[o] = (uint8_t)x;
-      out_local[o + 1] = (uint8_t)y;
-      out_local[o + 2] = (uint8_t)z;
-    }
-    if (out_global) {
-      out_global[o] = d.vbase + x;
-      out_global[o + 1] = d.vbase + y;
-      out_global[o + 2] = d.vbase + z;
-    }
-  }
-  // vertices
-  const Grid g = load_grid(a.grids + d.grid);
-  const uint32_t *pw = sw + 2 * ((d.T + 31) >> 5) + ((d.T + 2 - d.V) * d.w + 31) / 32;
-  for (uint32_t v = lane; v < d.V; v += 32) {
-    const uint64_t o = 3ull * (d.vbase + v);
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-      uint32_t q = extract(pw, (3 * v + c) * d.b, d.b);
-      out_pos[o + c] = dequant(d.L[c] + q, g.G[c], g.D[c]);
-    }
-  }
+  if (!decode_dispatch<CHECKED>(d, g, sw, sI, lane, out_local, out_global, out_pos) && lane == 0)
+    set_status(status, MC_ERR_CORRUPT);
   __syncwarp();
 }
 
@@ -77,7 +55,7 @@ __global__ void decode_plain_kernel(BatchArgs a, uint32_t first, uint32_t count,
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   uint8_t *base = smem + warp * smem_per_warp;
   uint32_t *sw = reinterpret_cast<uint32_t *>(base);
-  uint8_t *sI = base + smem_per_warp - 272;
+  uint8_t *sI = base + smem_per_warp - kStreamBytes;
   const uint32_t i = blockIdx.x * (blockDim.x >> 5) + warp;
   if (i >= count) return;
   decode_one<CHECKED>(a, first + i, sw, sI, lane, out_local, out_global, out_pos, status);
@@ -86,23 +64,69 @@ __global__ void decode_plain_kernel(BatchArgs a, uint32_t first, uint32_t count,
 // Scratch words used by the persistent kernels.
 enum { kQueue = 0, kDone = 1, kCount = 2 };
 
+// Persistent batched decode.  Each warp takes `per_grab` (<= 16) consecutive
+// meshlets from the work queue; because consecutive meshlets have
+// consecutive payload blocks, the warp loads all their descriptors and the
+// whole payload range in one pass of 16-byte loads (one memory latency per
+// grab), then decodes them one after another from shared memory.  A grab
+// whose range does not look contiguous falls back to staging meshlet by
+// meshlet.
 template <bool CHECKED>
-__global__ void decode_batch_kernel(BatchArgs a, uint32_t per_grab, uint32_t smem_per_warp,
-                                    uint8_t *out_local, uint32_t *out_global, float *out_pos,
-                                    uint32_t *status, uint32_t *scratch) {
+__global__ void __launch_bounds__(512) decode_batch_kernel(BatchArgs a, uint32_t per_grab,
+                                                           uint32_t smem_per_warp, uint8_t *out_local,
+                                                           uint32_t *out_global, float *out_pos,
+                                                           uint32_t *status, uint32_t *scratch) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   uint8_t *base = smem + warp * smem_per_warp;
-  uint32_t *sw = reinterpret_cast<uint32_t *>(base);
-  uint8_t *sI = base + smem_per_warp - 272;
+  uint32_t *sdesc = reinterpret_cast<uint32_t *>(base);
+  uint32_t *spay = sdesc + 8 * per_grab;
+  uint8_t *sI = base + smem_per_warp - kStreamBytes;
+  const uint32_t cap16 = (per_grab * ((a.max_block_words + 3) & ~3u)) / 4;
+  const uint32_t bytes16 = a.payload_bytes / 16 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)(a.payload_bytes / 16);
+  const uint4 *gdesc = reinterpret_cast<const uint4 *>(a.desc);
+  const uint4 *gpay = reinterpret_cast<const uint4 *>(a.payload);
   for (;;) {
     uint32_t m0 = 0;
     if (lane == 0) m0 = atomicAdd(scratch + kQueue, per_grab);
     m0 = __shfl_sync(kFull, m0, 0);
     if (m0 >= a.n_meshlets) break;
-    uint32_t m1 = min(a.n_meshlets, m0 + per_grab);
-    for (uint32_t m = m0; m < m1; m++)
-      decode_one<CHECKED>(a, m, sw, sI, lane, out_local, out_global, out_pos, status);
+    const uint32_t cnt = min(per_grab, a.n_meshlets - m0);
+    uint4 dv = make_uint4(0, 0, 0, 0);
+    if (lane < 2 * cnt) dv = __ldg(gdesc + 2ull * m0 + lane);
+    uint32_t end16 = bytes16;
+    if (m0 + cnt < a.n_meshlets) end16 = __ldg(&a.desc[m0 + cnt].payload_off16);
+    if (lane < 2 * cnt) reinterpret_cast<uint4 *>(sdesc)[lane] = dv;
+    const uint32_t start16 = __shfl_sync(kFull, dv.x, 0);
+    bool grab_staged = end16 >= start16 && end16 - start16 <= cap16 && end16 <= bytes16;
+    if (grab_staged) {
+      uint4 *dst = reinterpret_cast<uint4 *>(spay);
+      for (uint32_t i = lane; i < end16 - start16; i += 32) dst[i] = __ldg(gpay + start16 + i);
+    }
+    __syncwarp();
+    for (uint32_t j = 0; j < cnt; j++) {
+      const uint4 *sd = reinterpret_cast<const uint4 *>(sdesc) + 2 * j;
+      const Desc d = unpack_desc(sd[0], sd[1]);
+      if (!header_ok(d, a)) {
+        if (lane == 0) set_status(status, MC_ERR_CORRUPT);
+        continue;
+      }
+      const uint32_t padded16 = ((block_words(d) + 3) & ~3u) / 4;
+      const uint32_t *sw;
+      if (grab_staged && d.off16 >= start16 && d.off16 - start16 + padded16 <= end16 - start16) {
+        sw = spay + 4 * (d.off16 - start16);
+      } else {
+        grab_staged = false;  // spay is reused meshlet by meshlet from here on
+        __syncwarp();
+        stage_payload(d, a.payload, spay, lane);
+        __syncwarp();
+        sw = spay;
+      }
+      const Grid g = load_grid(a.grids + d.grid);
+      if (!decode_dispatch<CHECKED>(d, g, sw, sI, lane, out_local, out_global, out_pos) && lane == 0)
+        set_status(status, MC_ERR_CORRUPT);
+    }
+    __syncwarp();
   }
   // the last CTA to finish leaves the queue reset for the next launch
   __syncthreads();
@@ -149,21 +173,99 @@ __device__ __forceinline__ bool box_outside(const Desc &d, const Grid &g, const 
   return any;
 }
 
+// Decode + cull of one staged meshlet; survivors (global index triples) go
+// to surv[], positions to out_pos.  Returns the number of survivors, or
+// 0xFFFFFFFF for a corrupt stream.
+template <bool CHECKED, bool B16, bool W8>
+__device__ __forceinline__ uint32_t cull_staged(const Desc &d, const Grid &g, const float *M,
+                                                const uint32_t *sw, uint8_t *sI, float *cx,
+                                                float *cy, float *cw, uint32_t *surv,
+                                                uint32_t lane, float *out_pos) {
+  if (!build_stream<CHECKED, W8>(d, sw, sI, lane)) return 0xFFFFFFFFu;
+  const uint32_t nw = (d.T + 31) >> 5;
+  const uint32_t *pw = sw + 2 * nw + ((d.T + 2 - d.V) * d.w + 31) / 32;
+  const bool small = small_coords(d);
+  float *op = out_pos + 3ull * d.vbase;
+  for (uint32_t v = lane; v < d.V; v += 32) {
+    uint32_t q[3];
+    vertex_q<B16>(pw, v, d.b, q);
+    float p[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+      p[c] = small ? dequant_small(d.L[c] + q[c], g.G[c], g.D[c]) : dequant(d.L[c] + q[c], g.G[c], g.D[c]);
+    op[3 * v] = p[0];
+    op[3 * v + 1] = p[1];
+    op[3 * v + 2] = p[2];
+    cx[v] = clip_row(M, 0, p[0], p[1], p[2]);
+    cy[v] = clip_row(M, 1, p[0], p[1], p[2]);
+    cw[v] = clip_row(M, 3, p[0], p[1], p[2]);
+  }
+  __syncwarp();
+  uint32_t n_keep = 0;
+  for (uint32_t k0 = 0; k0 < d.T; k0 += 32) {
+    const uint32_t k = k0 + lane;
+    bool keep = false;
+    uint32_t x = 0, y = 0, z = 0;
+    if (k < d.T) {
+      triangle(sw, sI, k, x, y, z);
+      if (x != y && y != z && x != z) {
+        const float w0 = cw[x], w1 = cw[y], w2 = cw[z];
+        if (w0 <= 0.0f || w1 <= 0.0f || w2 <= 0.0f) {
+          keep = true;
+        } else {
+          const float x0 = cx[x], y0 = cy[x], x1 = cx[y], y1 = cy[y];
+          const float x2 = cx[z], y2 = cy[z];
+          const float c0 = __fmaf_rn(y1, w2, -__fmul_rn(w1, y2));
+          const float c1 = __fmaf_rn(x1, w2, -__fmul_rn(w1, x2));
+          const float c2 = __fmaf_rn(x1, y2, -__fmul_rn(y1, x2));
+          const float det = __fmaf_rn(w0, c2, __fmaf_rn(-y0, c1, __fmul_rn(x0, c0)));
+          keep = det > 0.0f;
+        }
+      }
+    }
+    const uint32_t bal = __ballot_sync(kFull, keep);
+    if (keep) {
+      const uint32_t o = n_keep + __popc(bal & ((1u << lane) - 1u));
+      surv[3 * o] = d.vbase + x;
+      surv[3 * o + 1] = d.vbase + y;
+      surv[3 * o + 2] = d.vbase + z;
+    }
+    n_keep += __popc(bal);
+  }
+  return n_keep;
+}
+
+template <bool CHECKED>
+__device__ __forceinline__ uint32_t cull_dispatch(const Desc &d, const Grid &g, const float *M,
+                                                  const uint32_t *sw, uint8_t *sI, float *cx,
+                                                  float *cy, float *cw, uint32_t *surv,
+                                                  uint32_t lane, float *out_pos) {
+  if (d.b == 16) {
+    if (d.w == 8) return cull_staged<CHECKED, true, true>(d, g, M, sw, sI, cx, cy, cw, surv, lane, out_pos);
+    return cull_staged<CHECKED, true, false>(d, g, M, sw, sI, cx, cy, cw, surv, lane, out_pos);
+  }
+  if (d.w == 8) return cull_staged<CHECKED, false, true>(d, g, M, sw, sI, cx, cy, cw, surv, lane, out_pos);
+  return cull_staged<CHECKED, false, false>(d, g, M, sw, sI, cx, cy, cw, surv, lane, out_pos);
+}
+
+// Fused decode + cull + compaction.  A CTA takes one meshlet per warp per
+// round; survivors are compacted in the warp (ballot/popc) into shared
+// memory, the CTA reserves output space with one atomicAdd per round, and
+// each warp copies its survivors out.
 template <bool CHECKED>
 __global__ void decode_cull_kernel(BatchArgs a, const float *view_proj, uint32_t smem_per_warp,
                                    uint32_t *tri_out, uint32_t *tri_count, float *out_pos,
                                    uint32_t *status, uint32_t *scratch) {
   extern __shared__ __align__(16) uint8_t smem[];
-  __shared__ uint32_t s_meshlet[32];
   __shared__ uint32_t s_cnt[32];
-  __shared__ uint32_t s_base;
+  __shared__ uint32_t s_base, s_out;
   __shared__ float s_M[16];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint32_t nwarps = blockDim.x >> 5;
   uint8_t *base = smem + warp * smem_per_warp;
   uint32_t *sw = reinterpret_cast<uint32_t *>(base);
   const uint32_t ws = smem_per_warp - (3 * 4 * 256 + 3 * 4 * 256);  // decode part
-  uint8_t *sI = base + ws - 272;
+  uint8_t *sI = base + ws - kStreamBytes;
   float *cx = reinterpret_cast<float *>(base + ws);
   float *cy = cx + 256;
   float *cw = cy + 256;
@@ -171,7 +273,6 @@ __global__ void decode_cull_kernel(BatchArgs a, const float *view_proj, uint32_t
   if (threadIdx.x < 16) s_M[threadIdx.x] = view_proj[threadIdx.x];
   __syncthreads();
   for (;;) {
-    // one round: every warp takes one meshlet of a chunk grabbed by the CTA
     if (threadIdx.x == 0) s_base = atomicAdd(scratch + kQueue, nwarps);
     __syncthreads();
     const uint32_t m = s_base + warp;
@@ -179,63 +280,17 @@ __global__ void decode_cull_kernel(BatchArgs a, const float *view_proj, uint32_t
     uint32_t n_keep = 0;
     if (round_live && m < a.n_meshlets) {
       const Desc d = load_desc(a.desc + m);
-      bool ok = header_ok(d, a);
-      if (!ok && lane == 0) set_status(status, MC_ERR_CORRUPT);
-      if (ok) {
+      if (!header_ok(d, a)) {
+        if (lane == 0) set_status(status, MC_ERR_CORRUPT);
+      } else {
         const Grid g = load_grid(a.grids + d.grid);
         if (!box_outside(d, g, s_M)) {
           stage_payload(d, a.payload, sw, lane);
           __syncwarp();
-          if (!build_stream<CHECKED>(d, sw, sI, lane)) {
+          n_keep = cull_dispatch<CHECKED>(d, g, s_M, sw, sI, cx, cy, cw, surv, lane, out_pos);
+          if (n_keep == 0xFFFFFFFFu) {
+            n_keep = 0;
             if (lane == 0) set_status(status, MC_ERR_CORRUPT);
-          } else {
-            const uint32_t *pw = sw + 2 * ((d.T + 31) >> 5) + ((d.T + 2 - d.V) * d.w + 31) / 32;
-            for (uint32_t v = lane; v < d.V; v += 32) {
-              float p[3];
-#pragma unroll
-              for (int c = 0; c < 3; c++) {
-                uint32_t q = extract(pw, (3 * v + c) * d.b, d.b);
-                p[c] = dequant(d.L[c] + q, g.G[c], g.D[c]);
-              }
-              const uint64_t o = 3ull * (d.vbase + v);
-              out_pos[o] = p[0];
-              out_pos[o + 1] = p[1];
-              out_pos[o + 2] = p[2];
-              cx[v] = clip_row(s_M, 0, p[0], p[1], p[2]);
-              cy[v] = clip_row(s_M, 1, p[0], p[1], p[2]);
-              cw[v] = clip_row(s_M, 3, p[0], p[1], p[2]);
-            }
-            __syncwarp();
-            for (uint32_t k0 = 0; k0 < d.T; k0 += 32) {
-              const uint32_t k = k0 + lane;
-              bool keep = false;
-              uint32_t x = 0, y = 0, z = 0;
-              if (k < d.T) {
-                triangle(sw, sI, k, x, y, z);
-                if (x != y && y != z && x != z) {
-                  const float w0 = cw[x], w1 = cw[y], w2 = cw[z];
-                  if (w0 <= 0.0f || w1 <= 0.0f || w2 <= 0.0f) {
-                    keep = true;
-                  } else {
-                    const float x0 = cx[x], y0 = cy[x], x1 = cx[y], y1 = cy[y];
-                    const float x2 = cx[z], y2 = cy[z];
-                    const float c0 = __fmaf_rn(y1, w2, -__fmul_rn(w1, y2));
-                    const float c1 = __fmaf_rn(x1, w2, -__fmul_rn(w1, x2));
-                    const float c2 = __fmaf_rn(x1, y2, -__fmul_rn(y1, x2));
-                    const float det = __fmaf_rn(w0, c2, __fmaf_rn(-y0, c1, __fmul_rn(x0, c0)));
-                    keep = det > 0.0f;
-                  }
-                }
-              }
-              const uint32_t bal = __ballot_sync(kFull, keep);
-              if (keep) {
-                const uint32_t o = n_keep + __popc(bal & ((1u << lane) - 1u));
-                surv[3 * o] = d.vbase + x;
-                surv[3 * o + 1] = d.vbase + y;
-                surv[3 * o + 2] = d.vbase + z;
-              }
-              n_keep += __popc(bal);
-            }
           }
         }
       }
@@ -246,18 +301,15 @@ __global__ void decode_cull_kernel(BatchArgs a, const float *view_proj, uint32_t
     if (threadIdx.x == 0) {
       uint32_t tot = 0;
       for (uint32_t w = 0; w < nwarps; w++) {
-        uint32_t c = s_cnt[w];
+        const uint32_t c = s_cnt[w];
         s_cnt[w] = tot;
         tot += c;
       }
-      s_meshlet[0] = tot ? atomicAdd(scratch + kCount, tot) : 0;
+      s_out = tot ? atomicAdd(scratch + kCount, tot) : 0;
     }
     __syncthreads();
-    {
-      const uint32_t dst = s_meshlet[0] + s_cnt[warp];
-      __syncwarp();
-      for (uint32_t i = lane; i < 3 * n_keep; i += 32) tri_out[3ull * dst + i] = surv[i];
-    }
+    const uint32_t dst = s_out + s_cnt[warp];
+    for (uint32_t i = lane; i < 3 * n_keep; i += 32) tri_out[3ull * dst + i] = surv[i];
     __syncthreads();
   }
   // the last CTA publishes the count and resets the scratch
@@ -298,7 +350,7 @@ cudaError_t launch_batch(const BatchArgs &a, uint32_t ctas, uint32_t warps, uint
                          uint32_t max_block_words, bool checked, uint8_t *out_local,
                          uint32_t *out_global, float *out_pos, uint32_t *status,
                          uint32_t *scratch, cudaStream_t s) {
-  const uint32_t spw = warp_smem_bytes(max_block_words);
+  const uint32_t spw = batch_smem_per_warp(max_block_words, per_grab);
   const uint32_t smem = spw * warps;
   if (checked) {
     cudaFuncSetAttribute(decode_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -330,13 +382,13 @@ cudaError_t launch_cull(const BatchArgs &a, const float *view_proj, uint32_t cta
   return cudaGetLastError();
 }
 
-int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words) {
+int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words, uint32_t per_grab) {
   int n = 0;
-  const int smem = (int)(warp_smem_bytes(max_block_words) * warps);
+  const int smem = (int)(batch_smem_per_warp(max_block_words, per_grab) * warps);
+  if (smem > 227 * 1024) return 0;
   cudaFuncSetAttribute(decode_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(decode_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_batch_kernel<false>, warps * 32,
-                                                warp_smem_bytes(max_block_words) * warps);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_batch_kernel<false>, warps * 32, smem);
   return n;
 }
 
