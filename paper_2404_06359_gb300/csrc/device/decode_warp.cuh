@@ -10,8 +10,10 @@
 //     (unpacked from w bits with a funnel shift).  I[0..2] = 0,1,2.
 //   third vertex (Sec. 4.2): the last triangle j < k whose L/R flag differs
 //     from flag k, found by masking the flag word (inverted when flag k is
-//     set) below bit k and taking 31 - __clz, walking back word by word
-//     when a fan spans more than 32 triangles; old = I[j + 1] (I[0] if none).
+//     set) below bit k and taking 31 - __clz; when a fan reaches back past
+//     the current 32-triangle word, j comes from running registers holding
+//     the last flag-0 / flag-1 positions of the earlier words;
+//     old = I[j + 1] (I[0] if none).
 //   triangle (Sec. 4.2, orientation by the flag): R -> (I[k+1], old, I[k+2]),
 //     L -> (old, I[k+1], I[k+2]).
 //   position (Sec. 4.4): g = L_c + q (q = b bits at (3v+c) b), then
@@ -131,74 +133,70 @@ __device__ __forceinline__ void stage_payload(const Desc &d, const uint8_t *payl
   for (uint32_t i = lane; i < n4; i += 32) dst[i] = __ldg(src + i);
 }
 
-// Builds the strip stream I[0..T+1] in shared memory (sI).  CHECKED: returns
-// false (warp-uniform) when the stream contradicts V, R or reuse bounds.
-template <bool CHECKED, bool W8>
-__device__ __forceinline__ bool build_stream(const Desc &d, const uint32_t *sw, uint8_t *sI,
-                                             uint32_t lane) {
+// Stream-level consistency checks of the checked build: bit 0 of both flag
+// words clear, no flag bit past T', and V = 3 + (number of increment flags).
+__device__ __forceinline__ bool stream_header_ok(const Desc &d, const uint32_t *sw) {
+  const uint32_t nw = (d.T + 31) >> 5;
+  uint32_t incs = 0;
+  for (uint32_t i = 0; i < nw; i++) incs += __popc(sw[nw + i]);
+  const uint32_t tail = d.T & 31u;
+  return incs + 3 == d.V && !(sw[0] & 1u) && !(sw[nw] & 1u) &&
+         !(tail && ((sw[nw - 1] >> tail) | (sw[2 * nw - 1] >> tail)));
+}
+
+// Walks the meshlet's triangles 32 at a time, calling
+//   emit(k, a, b, c, live)
+// on every lane (live = k < T') with triangle k = (a, b, c).  One pass per
+// 32-triangle word builds the strip entries of the word (add-scan of the
+// increment word; reuse entries read at slot k + 1 - s), stores them to sI,
+// and assembles the word's triangles: I[k+1] comes from the neighbouring
+// lane (shuffle), I[k+2] is the lane's own entry, and the third vertex is
+// I[j+1] for the last j < k whose L/R flag differs from flag k -- found in
+// the current word by 31 - clz of the masked flag word, otherwise taken
+// from two running registers holding the last flag-0 and flag-1 positions
+// of the earlier words (no loop, no divergence).  CHECKED: returns false
+// (warp-uniform) if a reuse entry names a vertex not yet seen.
+template <bool CHECKED, bool W8, class Emit>
+__device__ __forceinline__ bool walk_triangles(const Desc &d, const uint32_t *sw, uint8_t *sI,
+                                               uint32_t lane, Emit &&emit) {
   const uint32_t nw = (d.T + 31) >> 5;
   const uint32_t *rw = sw + 2 * nw;  // reuse section
   const uint8_t *rb = reinterpret_cast<const uint8_t *>(rw);
   if (lane < 3) sI[lane] = (uint8_t)lane;
-  uint32_t base = 2;
-  bool bad = false;
   const uint32_t le = (2u << lane) - 1u;  // bits 0..lane
+  const uint32_t lt = (1u << lane) - 1u;  // bits below lane
+  uint32_t base = 2;                      // s of the last triangle of the previous words
+  uint32_t carry = 1;                     // I[32 i + 1]: the entry before this word's first
+  int last0 = -1, last1 = -1;             // last earlier position with flag 0 / flag 1
+  bool bad = false;
   for (uint32_t i = 0; i < nw; i++) {
+    const uint32_t f = sw[i];
     const uint32_t inc = sw[nw + i];
     const uint32_t k = 32 * i + lane;
     const uint32_t s = base + __popc(inc & le);
-    if (k >= 1 && k < d.T) {
-      uint32_t n;
-      if ((inc >> lane) & 1u) {
-        n = s;
-      } else {
-        const uint32_t slot = k + 1 - s;
-        n = W8 ? rb[slot] : extract(rw, slot * d.w, d.w);
-        if (CHECKED && n > s) bad = true;  // entries seen so far: 0..s
-      }
-      if (CHECKED && n > 255) bad = true;
-      sI[k + 2] = (uint8_t)n;
-    }
+    const bool is_new = (inc >> lane) & 1u;
+    const uint32_t slot = (is_new || k == 0) ? 0u : k + 1 - s;
+    const uint32_t r = W8 ? (uint32_t)rb[slot] : extract(rw, slot * d.w, d.w);
+    const uint32_t n = k == 0 ? 2u : (is_new ? s : r);
+    const bool live = k < d.T;
+    if (CHECKED && live && !is_new && k != 0 && r > s) bad = true;  // seen so far: 0..s
+    if (live) sI[k + 2] = (uint8_t)n;
+    uint32_t prev = __shfl_up_sync(kFull, n, 1);
+    if (lane == 0) prev = carry;
+    carry = __shfl_sync(kFull, n, 31);
+    __syncwarp();
+    const uint32_t fk = (f >> lane) & 1u;
+    const uint32_t x = (f ^ (0u - fk)) & lt;
+    const int j = x ? (int)(32 * i + 31 - __clz(x)) : (fk ? last0 : last1);
+    const uint32_t old = sI[j + 1];
+    emit(k, fk ? prev : old, fk ? old : prev, n, live);
+    if (f) last1 = (int)(32 * i + 31 - __clz(f));
+    if (~f) last0 = (int)(32 * i + 31 - __clz(~f));
     base += __popc(inc);
   }
-  if (CHECKED) {
-    if (base + 1 != d.V) bad = true;
-    if ((sw[0] & 1u) || (sw[nw] & 1u)) bad = true;
-    // bits past T' in the last flag words must be clear
-    const uint32_t tail = d.T & 31u;
-    if (tail && ((sw[nw - 1] >> tail) | (sw[2 * nw - 1] >> tail))) bad = true;
-    bad = __any_sync(kFull, bad);
-  }
+  if (CHECKED) bad = __any_sync(kFull, bad);
   __syncwarp();
   return !bad;
-}
-
-// Triangle k of the meshlet (sI built, flags in sw[0..nw)).
-__device__ __forceinline__ void triangle(const uint32_t *sw, const uint8_t *sI, uint32_t k,
-                                         uint32_t &a, uint32_t &b, uint32_t &c) {
-  const uint32_t wi = k >> 5, bit = k & 31u;
-  const uint32_t f = sw[wi];
-  const uint32_t fk = (f >> bit) & 1u;
-  const uint32_t inv = 0u - fk;  // all ones when flag k is set
-  const uint32_t x = (f ^ inv) & ((1u << bit) - 1u);
-  int j = -1;
-  if (x) {
-    j = (int)(32 * wi + 31 - __clz(x));
-  } else {
-    for (int w = (int)wi - 1; w >= 0; w--) {
-      const uint32_t y = sw[w] ^ inv;
-      if (y) {
-        j = 32 * w + 31 - __clz(y);
-        break;
-      }
-    }
-  }
-  const uint32_t old = sI[j + 1];
-  const uint32_t prev = sI[k + 1];
-  const uint32_t cur = sI[k + 2];
-  a = fk ? prev : old;
-  b = fk ? old : prev;
-  c = cur;
 }
 
 // Position fields of vertex v (q for x, y, z).
@@ -229,24 +227,25 @@ template <bool CHECKED, bool B16, bool W8>
 __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, const uint32_t *sw,
                                               uint8_t *sI, uint32_t lane, uint8_t *out_local,
                                               uint32_t *out_global, float *out_pos) {
-  if (!build_stream<CHECKED, W8>(d, sw, sI, lane)) return false;
+  if (CHECKED && !stream_header_ok(d, sw)) return false;
   const uint32_t nw = (d.T + 31) >> 5;
   uint8_t *ol = out_local ? out_local + 3ull * d.tbase : nullptr;
   uint32_t *og = out_global ? out_global + 3ull * d.tbase : nullptr;
-  for (uint32_t k = lane; k < d.T; k += 32) {
-    uint32_t x, y, z;
-    triangle(sw, sI, k, x, y, z);
-    if (ol) {
-      ol[3 * k] = (uint8_t)x;
-      ol[3 * k + 1] = (uint8_t)y;
-      ol[3 * k + 2] = (uint8_t)z;
-    }
-    if (og) {
-      og[3 * k] = d.vbase + x;
-      og[3 * k + 1] = d.vbase + y;
-      og[3 * k + 2] = d.vbase + z;
-    }
-  }
+  const uint32_t vb = d.vbase;
+  const bool ok = walk_triangles<CHECKED, W8>(
+      d, sw, sI, lane, [&](uint32_t k, uint32_t x, uint32_t y, uint32_t z, bool live) {
+        if (!live) return;
+        if (ol) {
+          ol[3 * k] = (uint8_t)x;
+          ol[3 * k + 1] = (uint8_t)y;
+          ol[3 * k + 2] = (uint8_t)z;
+        }
+        if (og) {
+          og[3 * k] = vb + x;
+          og[3 * k + 1] = vb + y;
+          og[3 * k + 2] = vb + z;
+        }
+      });
   const uint32_t *pw = sw + 2 * nw + ((d.T + 2 - d.V) * d.w + 31) / 32;
   float *op = out_pos + 3ull * d.vbase;
   if (small_coords(d)) {
@@ -265,7 +264,7 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
     }
   }
   __syncwarp();
-  return true;
+  return ok;
 }
 
 template <bool CHECKED>

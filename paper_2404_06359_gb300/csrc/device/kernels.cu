@@ -181,7 +181,7 @@ __device__ __forceinline__ uint32_t cull_staged(const Desc &d, const Grid &g, co
                                                 const uint32_t *sw, uint8_t *sI, float *cx,
                                                 float *cy, float *cw, uint32_t *surv,
                                                 uint32_t lane, float *out_pos) {
-  if (!build_stream<CHECKED, W8>(d, sw, sI, lane)) return 0xFFFFFFFFu;
+  if (CHECKED && !stream_header_ok(d, sw)) return 0xFFFFFFFFu;
   const uint32_t nw = (d.T + 31) >> 5;
   const uint32_t *pw = sw + 2 * nw + ((d.T + 2 - d.V) * d.w + 31) / 32;
   const bool small = small_coords(d);
@@ -202,37 +202,34 @@ __device__ __forceinline__ uint32_t cull_staged(const Desc &d, const Grid &g, co
   }
   __syncwarp();
   uint32_t n_keep = 0;
-  for (uint32_t k0 = 0; k0 < d.T; k0 += 32) {
-    const uint32_t k = k0 + lane;
-    bool keep = false;
-    uint32_t x = 0, y = 0, z = 0;
-    if (k < d.T) {
-      triangle(sw, sI, k, x, y, z);
-      if (x != y && y != z && x != z) {
-        const float w0 = cw[x], w1 = cw[y], w2 = cw[z];
-        if (w0 <= 0.0f || w1 <= 0.0f || w2 <= 0.0f) {
-          keep = true;
-        } else {
-          const float x0 = cx[x], y0 = cy[x], x1 = cx[y], y1 = cy[y];
-          const float x2 = cx[z], y2 = cy[z];
-          const float c0 = __fmaf_rn(y1, w2, -__fmul_rn(w1, y2));
-          const float c1 = __fmaf_rn(x1, w2, -__fmul_rn(w1, x2));
-          const float c2 = __fmaf_rn(x1, y2, -__fmul_rn(y1, x2));
-          const float det = __fmaf_rn(w0, c2, __fmaf_rn(-y0, c1, __fmul_rn(x0, c0)));
-          keep = det > 0.0f;
+  const uint32_t vb = d.vbase;
+  const bool ok = walk_triangles<CHECKED, W8>(
+      d, sw, sI, lane, [&](uint32_t k, uint32_t x, uint32_t y, uint32_t z, bool live) {
+        bool keep = false;
+        if (live && x != y && y != z && x != z) {
+          const float w0 = cw[x], w1 = cw[y], w2 = cw[z];
+          if (w0 <= 0.0f || w1 <= 0.0f || w2 <= 0.0f) {
+            keep = true;
+          } else {
+            const float x0 = cx[x], y0 = cy[x], x1 = cx[y], y1 = cy[y];
+            const float x2 = cx[z], y2 = cy[z];
+            const float c0 = __fmaf_rn(y1, w2, -__fmul_rn(w1, y2));
+            const float c1 = __fmaf_rn(x1, w2, -__fmul_rn(w1, x2));
+            const float c2 = __fmaf_rn(x1, y2, -__fmul_rn(y1, x2));
+            const float det = __fmaf_rn(w0, c2, __fmaf_rn(-y0, c1, __fmul_rn(x0, c0)));
+            keep = det > 0.0f;
+          }
         }
-      }
-    }
-    const uint32_t bal = __ballot_sync(kFull, keep);
-    if (keep) {
-      const uint32_t o = n_keep + __popc(bal & ((1u << lane) - 1u));
-      surv[3 * o] = d.vbase + x;
-      surv[3 * o + 1] = d.vbase + y;
-      surv[3 * o + 2] = d.vbase + z;
-    }
-    n_keep += __popc(bal);
-  }
-  return n_keep;
+        const uint32_t bal = __ballot_sync(kFull, keep);
+        if (keep) {
+          const uint32_t o = n_keep + __popc(bal & ((1u << lane) - 1u));
+          surv[3 * o] = vb + x;
+          surv[3 * o + 1] = vb + y;
+          surv[3 * o + 2] = vb + z;
+        }
+        n_keep += __popc(bal);
+      });
+  return ok ? n_keep : 0xFFFFFFFFu;
 }
 
 template <bool CHECKED>
