@@ -189,7 +189,6 @@ typedef struct {
   uint64_t total_tris;  /* capacity of the outputs, triangles (sum of T') */
   uint64_t total_verts; /* capacity of the outputs, vertices (sum of V) */
   uint32_t max_block_words; /* from mc_blob_view (sizes shared-memory staging) */
-  uint32_t max_tris;        /* largest T' (from mc_blob_view); 0 = 256 */
 } mc_device_batch;
 
 /* Launch shape; zero fields take the library defaults or the autotuned
@@ -210,8 +209,7 @@ size_t mc_scratch_bytes(void);
 
 /* Plain decode: one launch over meshlets [first, first + count), one warp per
  * meshlet (the baseline; a per-mesh decode issues one call per mesh).
- * Outputs (any of d_local / d_global may be NULL, d_pos may not; d_local and
- * d_global must be 16-byte aligned):
+ * Outputs (any of d_local / d_global may be NULL, d_pos may not):
  *   d_local  u8  [3 * total_tris]  local triangle indices, meshlet m at
  *            3 * tri_base(m); degenerates are kept (Sec. 4.2)
  *   d_global u32 [3 * total_tris]  vertex_base(m) + local

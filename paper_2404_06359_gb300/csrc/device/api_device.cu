@@ -69,7 +69,6 @@ BatchArgs args_of(const mc_device_batch *b) {
   a.total_tris = b->total_tris;
   a.total_verts = b->total_verts;
   a.max_block_words = b->max_block_words;
-  a.max_tris = (b->max_tris == 0 || b->max_tris > 256) ? 256 : b->max_tris;
   return a;
 }
 
@@ -92,8 +91,7 @@ mc_tuning resolve_batch(const mc_device_batch *b, const mc_tuning *t) {
   if (!r.meshlets_per_grab) r.meshlets_per_grab = 2;
   if (r.meshlets_per_grab > 16) r.meshlets_per_grab = 16;
   if (!r.ctas_per_sm) {
-    int occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, args_of(b).max_tris,
-                                    r.meshlets_per_grab);
+    int occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, r.meshlets_per_grab);
     r.ctas_per_sm = occ > 0 ? (uint32_t)occ : 1;
   }
   return r;
@@ -105,15 +103,14 @@ mc_status launch_batch_checked(const mc_device_batch *b, uint8_t *d_local, uint3
   if (r.warps_per_cta < 1 || r.warps_per_cta > 32 || r.meshlets_per_grab < 1 ||
       r.meshlets_per_grab > 16)
     return MC_ERR_INVALID_ARG;
-  int occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, args_of(b).max_tris,
-                                    r.meshlets_per_grab);
+  int occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, r.meshlets_per_grab);
   if (occ <= 0) return MC_ERR_INVALID_ARG;
   uint32_t per_sm = std::min<uint32_t>(r.ctas_per_sm, (uint32_t)occ);
   uint32_t ctas = per_sm * (uint32_t)sm_count();
   if (ctas == 0) return MC_ERR_CUDA;
   cudaError_t e = launch_batch(args_of(b), ctas, r.warps_per_cta, r.meshlets_per_grab,
-                               r.checked != 0, d_local, d_global, d_pos, d_status,
-                               static_cast<uint32_t *>(d_scratch), s);
+                               b->max_block_words, r.checked != 0, d_local, d_global, d_pos,
+                               d_status, static_cast<uint32_t *>(d_scratch), s);
   if (e == cudaSuccess) g_launches++;
   return from_cuda(e);
 }
@@ -135,9 +132,9 @@ extern "C" mc_status mc_decode_plain(const mc_device_batch *b, uint32_t first, u
   uint32_t warps = (t && t->warps_per_cta) ? t->warps_per_cta : 8;
   if (warps > 32) return MC_ERR_INVALID_ARG;
   if (count == 0) return MC_OK;
-  if (!aligned(d_local, 16) || !aligned(d_global, 16)) return MC_ERR_INVALID_ARG;
-  cudaError_t e = launch_plain(args_of(b), first, count, warps, t && t->checked, d_local, d_global,
-                               d_pos, d_status, static_cast<cudaStream_t>(stream));
+  cudaError_t e = launch_plain(args_of(b), first, count, warps, b->max_block_words,
+                               t && t->checked, d_local, d_global, d_pos, d_status,
+                               static_cast<cudaStream_t>(stream));
   if (e == cudaSuccess) g_launches++;
   return from_cuda(e);
 }
@@ -149,9 +146,7 @@ extern "C" mc_status mc_decode_batch(const mc_device_batch *b, uint8_t *d_local,
   if (b->n_meshlets == 0) return MC_OK;
   mc_status st = check_batch(b);
   if (st != MC_OK) return st;
-  if (!d_pos || !d_scratch || !aligned(d_scratch, 16) || !aligned(d_local, 16) ||
-      !aligned(d_global, 16))
-    return MC_ERR_INVALID_ARG;
+  if (!d_pos || !d_scratch || !aligned(d_scratch, 16)) return MC_ERR_INVALID_ARG;
   mc_tuning r = resolve_batch(b, t);
   return launch_batch_checked(b, d_local, d_global, d_pos, d_status, d_scratch, r,
                               static_cast<cudaStream_t>(stream));
@@ -207,7 +202,7 @@ extern "C" mc_status mc_autotune(const mc_device_batch *b, uint8_t *d_local, uin
   st = MC_OK;
   for (uint32_t w : warps_c) {
     for (uint32_t g : grab_c) {
-      int occ = max_ctas_per_sm_batch(w, b->max_block_words, args_of(b).max_tris, g);
+      int occ = max_ctas_per_sm_batch(w, b->max_block_words, g);
       if (occ <= 0) continue;
       for (uint32_t frac = 0; frac < 2; frac++) {
         mc_tuning c{};
@@ -363,7 +358,6 @@ extern "C" mc_status mc_decode_batch_host(const mc_blob_view_t *v, mc_desc *d_de
   b.total_tris = v->total_tris;
   b.total_verts = v->total_verts;
   b.max_block_words = v->max_block_words;
-  b.max_tris = v->max_tris;
   mc_status st = mc_decode_batch(&b, d_local, d_global, d_pos, d_status, d_scratch, t, stream);
   if (st != MC_OK) return st;
   if (h_local) e = cudaMemcpyAsync(h_local, d_local, 3 * v->total_tris, cudaMemcpyDeviceToHost, s);

@@ -89,27 +89,7 @@ struct BatchArgs {
   uint32_t n_meshlets, n_grids;
   uint64_t payload_bytes, total_tris, total_verts;
   uint32_t max_block_words;  // capacity of one meshlet's shared-memory slot
-  uint32_t max_tris;         // capacity of the output staging areas (T')
 };
-
-// Per-warp shared memory of the decode kernels (bytes, all 16-byte aligned):
-//   [descriptors of one grab][payload blocks + slack][strip stream]
-//   [u8 index staging][u32 index staging]
-struct WarpLayout {
-  uint32_t desc, pay, stream, out_local, out_global, bytes;
-};
-__host__ __device__ inline WarpLayout warp_layout(uint32_t max_block_words, uint32_t max_tris,
-                                                  uint32_t per_grab, bool grab_descs) {
-  WarpLayout l;
-  const uint32_t mbw4 = (max_block_words + 3) & ~3u;
-  l.desc = 0;
-  l.pay = grab_descs ? 32 * per_grab : 0;
-  l.stream = l.pay + 4 * (per_grab * mbw4 + kSlackWords);
-  l.out_local = l.stream + kStreamBytes;
-  l.out_global = l.out_local + ((3 * max_tris + 16 + 15) & ~15u);
-  l.bytes = l.out_global + 4 * ((3 * max_tris + 4 + 3) & ~3u);
-  return l;
-}
 
 // Header sanity (all builds): a descriptor that passes cannot make the decode
 // read or write outside its buffers.
@@ -118,7 +98,7 @@ __device__ __forceinline__ bool header_ok(const Desc &d, const BatchArgs &a) {
             d.w <= 8 && d.b >= 1 && d.b <= 32 && d.grid < a.n_grids;
   if (!ok) return false;
   const uint32_t padded = (block_words(d) + 3) & ~3u;
-  return padded <= a.max_block_words && d.T <= a.max_tris &&
+  return padded <= a.max_block_words &&
          16ull * d.off16 + 4ull * padded <= a.payload_bytes &&
          (uint64_t)d.tbase + d.T <= a.total_tris && (uint64_t)d.vbase + d.V <= a.total_verts;
 }
@@ -242,65 +222,30 @@ __device__ __forceinline__ bool small_coords(const Desc &d) {
   return d.L[0] <= lim && d.L[1] <= lim && d.L[2] <= lim;
 }
 
-// Writes n bytes staged at area[a0 .. a0+n) (area 16-byte aligned, a0 < 16)
-// to gbase[a0 .. a0+n) (gbase 16-byte aligned): whole 16-byte chunks as
-// vector stores, the ragged head and tail (< 16 bytes each) byte by byte.
-__device__ __forceinline__ void copy_out_bytes(const uint8_t *area, uint32_t a0, uint32_t n,
-                                               uint8_t *gbase, uint32_t lane) {
-  const uint32_t end = a0 + n;
-  const uint32_t c0 = (a0 + 15) >> 4, c1 = end >> 4;
-  for (uint32_t c = c0 + lane; c < c1; c += 32)
-    reinterpret_cast<uint4 *>(gbase)[c] = reinterpret_cast<const uint4 *>(area)[c];
-  const uint32_t hend = min(16 * c0, end);
-  const uint32_t tstart = max(16 * c1, hend);
-  const uint32_t idx = lane < 16 ? a0 + lane : tstart + lane - 16;
-  if (idx < (lane < 16 ? hend : end)) gbase[idx] = area[idx];
-}
-
-// Same for n u32 words staged at area[a1 .. a1+n) (a1 < 4), chunks of 4 words.
-__device__ __forceinline__ void copy_out_words(const uint32_t *area, uint32_t a1, uint32_t n,
-                                               uint32_t *gbase, uint32_t lane) {
-  const uint32_t end = a1 + n;
-  const uint32_t c0 = (a1 + 3) >> 2, c1 = end >> 2;
-  for (uint32_t c = c0 + lane; c < c1; c += 32)
-    reinterpret_cast<uint4 *>(gbase)[c] = reinterpret_cast<const uint4 *>(area)[c];
-  const uint32_t hend = min(4 * c0, end);
-  const uint32_t tstart = max(4 * c1, hend);
-  const uint32_t idx = lane < 4 ? a1 + lane : tstart + lane - 4;
-  if (lane < 8 && idx < (lane < 4 ? hend : end)) gbase[idx] = area[idx];
-}
-
 // Full decode of one staged meshlet into the batch outputs.
 template <bool CHECKED, bool B16, bool W8>
 __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, const uint32_t *sw,
-                                              uint8_t *sI, uint8_t *sOL, uint32_t *sOG,
-                                              uint32_t lane, uint8_t *out_local,
+                                              uint8_t *sI, uint32_t lane, uint8_t *out_local,
                                               uint32_t *out_global, float *out_pos) {
   if (CHECKED && !stream_header_ok(d, sw)) return false;
   const uint32_t nw = (d.T + 31) >> 5;
-  // index outputs are staged at the 16-byte phase of their destination
-  const uint64_t e0 = 3ull * d.tbase;
-  const uint32_t a0 = (uint32_t)e0 & 15u, a1 = (uint32_t)e0 & 3u;
-  uint8_t *lb = sOL + a0;
-  uint32_t *gb = sOG + a1;
-  const bool want_l = out_local != nullptr, want_g = out_global != nullptr;
+  uint8_t *ol = out_local ? out_local + 3ull * d.tbase : nullptr;
+  uint32_t *og = out_global ? out_global + 3ull * d.tbase : nullptr;
   const uint32_t vb = d.vbase;
   const bool ok = walk_triangles<CHECKED, W8>(
       d, sw, sI, lane, [&](uint32_t k, uint32_t x, uint32_t y, uint32_t z, bool live) {
         if (!live) return;
-        if (want_l) {
-          lb[3 * k] = (uint8_t)x;
-          lb[3 * k + 1] = (uint8_t)y;
-          lb[3 * k + 2] = (uint8_t)z;
+        if (ol) {
+          ol[3 * k] = (uint8_t)x;
+          ol[3 * k + 1] = (uint8_t)y;
+          ol[3 * k + 2] = (uint8_t)z;
         }
-        if (want_g) {
-          gb[3 * k] = vb + x;
-          gb[3 * k + 1] = vb + y;
-          gb[3 * k + 2] = vb + z;
+        if (og) {
+          og[3 * k] = vb + x;
+          og[3 * k + 1] = vb + y;
+          og[3 * k + 2] = vb + z;
         }
       });
-  if (want_l) copy_out_bytes(sOL, a0, 3 * d.T, out_local + (e0 - a0), lane);
-  if (want_g) copy_out_words(sOG, a1, 3 * d.T, out_global + (e0 - a1), lane);
   const uint32_t *pw = sw + 2 * nw + ((d.T + 2 - d.V) * d.w + 31) / 32;
   float *op = out_pos + 3ull * d.vbase;
   if (small_coords(d)) {
@@ -324,17 +269,14 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
 
 template <bool CHECKED>
 __device__ __forceinline__ bool decode_dispatch(const Desc &d, const Grid &g, const uint32_t *sw,
-                                                uint8_t *sI, uint8_t *sOL, uint32_t *sOG,
-                                                uint32_t lane, uint8_t *out_local,
+                                                uint8_t *sI, uint32_t lane, uint8_t *out_local,
                                                 uint32_t *out_global, float *out_pos) {
   if (d.b == 16) {
-    if (d.w == 8)
-      return decode_staged<CHECKED, true, true>(d, g, sw, sI, sOL, sOG, lane, out_local, out_global, out_pos);
-    return decode_staged<CHECKED, true, false>(d, g, sw, sI, sOL, sOG, lane, out_local, out_global, out_pos);
+    if (d.w == 8) return decode_staged<CHECKED, true, true>(d, g, sw, sI, lane, out_local, out_global, out_pos);
+    return decode_staged<CHECKED, true, false>(d, g, sw, sI, lane, out_local, out_global, out_pos);
   }
-  if (d.w == 8)
-    return decode_staged<CHECKED, false, true>(d, g, sw, sI, sOL, sOG, lane, out_local, out_global, out_pos);
-  return decode_staged<CHECKED, false, false>(d, g, sw, sI, sOL, sOG, lane, out_local, out_global, out_pos);
+  if (d.w == 8) return decode_staged<CHECKED, false, true>(d, g, sw, sI, lane, out_local, out_global, out_pos);
+  return decode_staged<CHECKED, false, false>(d, g, sw, sI, lane, out_local, out_global, out_pos);
 }
 
 }  // namespace mcdev

@@ -8,19 +8,21 @@
 
 namespace mcdev {
 
-// Per-warp shared memory of the culling kernel: payload words (plus
-// over-read slack), the strip stream, clip coordinates and survivors.
+// Per-warp shared memory of the single-meshlet kernels: payload words (plus
+// over-read slack), then the strip stream.
 __host__ __device__ inline uint32_t warp_words(uint32_t max_block_words) {
   return ((max_block_words + 3) & ~3u) + kSlackWords;
 }
 __host__ __device__ inline uint32_t warp_smem_bytes(uint32_t max_block_words) {
   return 4 * warp_words(max_block_words) + kStreamBytes;
 }
-uint32_t decode_smem_per_warp(uint32_t max_block_words, uint32_t max_tris) {
-  return warp_layout(max_block_words, max_tris, 1, false).bytes;
+// Batched kernel: descriptors of one grab, the grab's payload blocks, stream.
+__host__ __device__ inline uint32_t grab_words(uint32_t max_block_words, uint32_t per_grab) {
+  return 8 * per_grab + per_grab * ((max_block_words + 3) & ~3u) + kSlackWords;
 }
-uint32_t batch_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, uint32_t per_grab) {
-  return warp_layout(max_block_words, max_tris, per_grab, true).bytes;
+uint32_t decode_smem_per_warp(uint32_t max_block_words) { return warp_smem_bytes(max_block_words); }
+uint32_t batch_smem_per_warp(uint32_t max_block_words, uint32_t per_grab) {
+  return 4 * grab_words(max_block_words, per_grab) + kStreamBytes;
 }
 uint32_t cull_smem_per_warp(uint32_t max_block_words) {
   // + clip (x, y, w) per vertex + survivor triples
@@ -28,8 +30,8 @@ uint32_t cull_smem_per_warp(uint32_t max_block_words) {
 }
 
 template <bool CHECKED>
-__device__ __forceinline__ void decode_one(const BatchArgs &a, uint32_t m, uint8_t *base,
-                                           const WarpLayout &L, uint32_t lane, uint8_t *out_local,
+__device__ __forceinline__ void decode_one(const BatchArgs &a, uint32_t m, uint32_t *sw,
+                                           uint8_t *sI, uint32_t lane, uint8_t *out_local,
                                            uint32_t *out_global, float *out_pos,
                                            uint32_t *status) {
   const Desc d = load_desc(a.desc + m);
@@ -38,28 +40,25 @@ __device__ __forceinline__ void decode_one(const BatchArgs &a, uint32_t m, uint8
     return;
   }
   const Grid g = load_grid(a.grids + d.grid);
-  uint32_t *sw = reinterpret_cast<uint32_t *>(base + L.pay);
   stage_payload(d, a.payload, sw, lane);
   __syncwarp();
-  if (!decode_dispatch<CHECKED>(d, g, sw, base + L.stream, base + L.out_local,
-                                reinterpret_cast<uint32_t *>(base + L.out_global), lane, out_local,
-                                out_global, out_pos) &&
-      lane == 0)
+  if (!decode_dispatch<CHECKED>(d, g, sw, sI, lane, out_local, out_global, out_pos) && lane == 0)
     set_status(status, MC_ERR_CORRUPT);
   __syncwarp();
 }
 
 template <bool CHECKED>
 __global__ void decode_plain_kernel(BatchArgs a, uint32_t first, uint32_t count,
-                                    uint8_t *out_local, uint32_t *out_global, float *out_pos,
-                                    uint32_t *status) {
+                                    uint32_t smem_per_warp, uint8_t *out_local,
+                                    uint32_t *out_global, float *out_pos, uint32_t *status) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-  const WarpLayout L = warp_layout(a.max_block_words, a.max_tris, 1, false);
+  uint8_t *base = smem + warp * smem_per_warp;
+  uint32_t *sw = reinterpret_cast<uint32_t *>(base);
+  uint8_t *sI = base + smem_per_warp - kStreamBytes;
   const uint32_t i = blockIdx.x * (blockDim.x >> 5) + warp;
   if (i >= count) return;
-  decode_one<CHECKED>(a, first + i, smem + warp * L.bytes, L, lane, out_local, out_global, out_pos,
-                      status);
+  decode_one<CHECKED>(a, first + i, sw, sI, lane, out_local, out_global, out_pos, status);
 }
 
 // Scratch words used by the persistent kernels.
@@ -74,18 +73,15 @@ enum { kQueue = 0, kDone = 1, kCount = 2 };
 // meshlet.
 template <bool CHECKED>
 __global__ void __launch_bounds__(512) decode_batch_kernel(BatchArgs a, uint32_t per_grab,
-                                                           uint8_t *out_local, uint32_t *out_global,
-                                                           float *out_pos, uint32_t *status,
-                                                           uint32_t *scratch) {
+                                                           uint32_t smem_per_warp, uint8_t *out_local,
+                                                           uint32_t *out_global, float *out_pos,
+                                                           uint32_t *status, uint32_t *scratch) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-  const WarpLayout L = warp_layout(a.max_block_words, a.max_tris, per_grab, true);
-  uint8_t *base = smem + warp * L.bytes;
-  uint32_t *sdesc = reinterpret_cast<uint32_t *>(base + L.desc);
-  uint32_t *spay = reinterpret_cast<uint32_t *>(base + L.pay);
-  uint8_t *sI = base + L.stream;
-  uint8_t *sOL = base + L.out_local;
-  uint32_t *sOG = reinterpret_cast<uint32_t *>(base + L.out_global);
+  uint8_t *base = smem + warp * smem_per_warp;
+  uint32_t *sdesc = reinterpret_cast<uint32_t *>(base);
+  uint32_t *spay = sdesc + 8 * per_grab;
+  uint8_t *sI = base + smem_per_warp - kStreamBytes;
   const uint32_t cap16 = (per_grab * ((a.max_block_words + 3) & ~3u)) / 4;
   const uint32_t bytes16 = a.payload_bytes / 16 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)(a.payload_bytes / 16);
   const uint4 *gdesc = reinterpret_cast<const uint4 *>(a.desc);
@@ -127,8 +123,7 @@ __global__ void __launch_bounds__(512) decode_batch_kernel(BatchArgs a, uint32_t
         sw = spay;
       }
       const Grid g = load_grid(a.grids + d.grid);
-      if (!decode_dispatch<CHECKED>(d, g, sw, sI, sOL, sOG, lane, out_local, out_global, out_pos) &&
-          lane == 0)
+      if (!decode_dispatch<CHECKED>(d, g, sw, sI, lane, out_local, out_global, out_pos) && lane == 0)
         set_status(status, MC_ERR_CORRUPT);
     }
     __syncwarp();
@@ -329,35 +324,39 @@ __global__ void decode_cull_kernel(BatchArgs a, const float *view_proj, uint32_t
 
 // ------------------------------------------------------------- launchers
 cudaError_t launch_plain(const BatchArgs &a, uint32_t first, uint32_t count, uint32_t warps,
-                         bool checked, uint8_t *out_local, uint32_t *out_global, float *out_pos,
-                         uint32_t *status, cudaStream_t s) {
+                         uint32_t max_block_words, bool checked, uint8_t *out_local,
+                         uint32_t *out_global, float *out_pos, uint32_t *status,
+                         cudaStream_t s) {
   if (count == 0) return cudaSuccess;
-  const uint32_t smem = decode_smem_per_warp(a.max_block_words, a.max_tris) * warps;
+  const uint32_t spw = warp_smem_bytes(max_block_words);
+  const uint32_t smem = spw * warps;
   const uint32_t grid = (count + warps - 1) / warps;
   if (checked) {
     cudaFuncSetAttribute(decode_plain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    decode_plain_kernel<true><<<grid, warps * 32, smem, s>>>(a, first, count, out_local, out_global,
-                                                             out_pos, status);
+    decode_plain_kernel<true><<<grid, warps * 32, smem, s>>>(a, first, count, spw, out_local,
+                                                             out_global, out_pos, status);
   } else {
     cudaFuncSetAttribute(decode_plain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    decode_plain_kernel<false><<<grid, warps * 32, smem, s>>>(a, first, count, out_local, out_global,
-                                                              out_pos, status);
+    decode_plain_kernel<false><<<grid, warps * 32, smem, s>>>(a, first, count, spw, out_local,
+                                                              out_global, out_pos, status);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_batch(const BatchArgs &a, uint32_t ctas, uint32_t warps, uint32_t per_grab,
-                         bool checked, uint8_t *out_local, uint32_t *out_global, float *out_pos,
-                         uint32_t *status, uint32_t *scratch, cudaStream_t s) {
-  const uint32_t smem = batch_smem_per_warp(a.max_block_words, a.max_tris, per_grab) * warps;
+                         uint32_t max_block_words, bool checked, uint8_t *out_local,
+                         uint32_t *out_global, float *out_pos, uint32_t *status,
+                         uint32_t *scratch, cudaStream_t s) {
+  const uint32_t spw = batch_smem_per_warp(max_block_words, per_grab);
+  const uint32_t smem = spw * warps;
   if (checked) {
     cudaFuncSetAttribute(decode_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    decode_batch_kernel<true><<<ctas, warps * 32, smem, s>>>(a, per_grab, out_local, out_global,
-                                                             out_pos, status, scratch);
+    decode_batch_kernel<true><<<ctas, warps * 32, smem, s>>>(a, per_grab, spw, out_local,
+                                                             out_global, out_pos, status, scratch);
   } else {
     cudaFuncSetAttribute(decode_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    decode_batch_kernel<false><<<ctas, warps * 32, smem, s>>>(a, per_grab, out_local, out_global,
-                                                              out_pos, status, scratch);
+    decode_batch_kernel<false><<<ctas, warps * 32, smem, s>>>(a, per_grab, spw, out_local,
+                                                              out_global, out_pos, status, scratch);
   }
   return cudaGetLastError();
 }
@@ -380,10 +379,9 @@ cudaError_t launch_cull(const BatchArgs &a, const float *view_proj, uint32_t cta
   return cudaGetLastError();
 }
 
-int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words, uint32_t max_tris,
-                          uint32_t per_grab) {
+int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words, uint32_t per_grab) {
   int n = 0;
-  const int smem = (int)(batch_smem_per_warp(max_block_words, max_tris, per_grab) * warps);
+  const int smem = (int)(batch_smem_per_warp(max_block_words, per_grab) * warps);
   if (smem > 227 * 1024) return 0;
   cudaFuncSetAttribute(decode_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(decode_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
