@@ -222,49 +222,118 @@ __device__ __forceinline__ bool small_coords(const Desc &d) {
   return d.L[0] <= lim && d.L[1] <= lim && d.L[2] <= lim;
 }
 
-// Full decode of one staged meshlet into the batch outputs.
+// 32-bit shared-window accessors (explicit LDS/STS addressing).
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t lds_u8(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u16(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts_u8(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u8 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+// position of the highest set bit, 0xFFFFFFFF for 0
+__device__ __forceinline__ uint32_t msb(uint32_t x) {
+  uint32_t r;
+  asm("bfind.u32 %0, %1;" : "=r"(r) : "r"(x));
+  return r;
+}
+
+// Full decode of one staged meshlet into the batch outputs: the strip walk
+// of walk_triangles (same arithmetic) written out flat, with the first
+// triangle folded into the scan (increment bit 0 forced on and the scan
+// seeded with 1, so triangle 0 gets entry s = 2 with no special case) and
+// per-lane output pointers advanced by one word of triangles per pass.
 template <bool CHECKED, bool B16, bool W8>
 __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, const uint32_t *sw,
                                               uint8_t *sI, uint32_t lane, uint8_t *out_local,
                                               uint32_t *out_global, float *out_pos) {
   if (CHECKED && !stream_header_ok(d, sw)) return false;
   const uint32_t nw = (d.T + 31) >> 5;
-  uint8_t *ol = out_local ? out_local + 3ull * d.tbase : nullptr;
-  uint32_t *og = out_global ? out_global + 3ull * d.tbase : nullptr;
+  const uint32_t a_sw = smem_addr(sw);
+  const uint32_t a_rb = a_sw + 8 * nw;  // reuse section (bytes)
+  const uint32_t a_sI = smem_addr(sI);
+  if (lane < 2) sts_u8(a_sI + lane, lane);  // I[0], I[1]; I[2] is triangle 0's entry
+  const uint32_t le = (2u << lane) - 1u, lt = (1u << lane) - 1u;
+  uint8_t *pl = out_local ? out_local + 3ull * (d.tbase + lane) : nullptr;
+  uint32_t *pg = out_global ? out_global + 3ull * (d.tbase + lane) : nullptr;
   const uint32_t vb = d.vbase;
-  const bool ok = walk_triangles<CHECKED, W8>(
-      d, sw, sI, lane, [&](uint32_t k, uint32_t x, uint32_t y, uint32_t z, bool live) {
-        if (!live) return;
-        if (ol) {
-          ol[3 * k] = (uint8_t)x;
-          ol[3 * k + 1] = (uint8_t)y;
-          ol[3 * k + 2] = (uint8_t)z;
-        }
-        if (og) {
-          og[3 * k] = vb + x;
-          og[3 * k + 1] = vb + y;
-          og[3 * k + 2] = vb + z;
-        }
-      });
+  uint32_t base = 1, carry = 1, last0 = 0xFFFFFFFFu, last1 = 0xFFFFFFFFu;
+  bool bad = false;
+  uint32_t k = lane;
+  for (uint32_t i = 0; i < nw; i++, k += 32) {
+    const uint32_t f = lds_u32(a_sw + 4 * i);
+    const uint32_t inc = lds_u32(a_sw + 4 * (nw + i)) | (i == 0 ? 1u : 0u);
+    const uint32_t s = base + __popc(inc & le);
+    const bool is_new = (inc & (1u << lane)) != 0;
+    const uint32_t slot = is_new ? 0u : k + 1 - s;
+    const uint32_t r = W8 ? lds_u8(a_rb + slot) : extract(sw + 2 * nw, slot * d.w, d.w);
+    const uint32_t n = is_new ? s : r;
+    const bool live = k < d.T;
+    if (CHECKED && live && !is_new && r > s) bad = true;  // entries seen so far: 0..s
+    if (live) sts_u8(a_sI + k + 2, n);
+    uint32_t prev = __shfl_up_sync(kFull, n, 1);
+    if (lane == 0) prev = carry;
+    carry = __shfl_sync(kFull, n, 31);
+    __syncwarp();
+    const uint32_t fk = (f >> lane) & 1u;
+    const uint32_t x = (f ^ (0u - fk)) & lt;
+    uint32_t j = msb(x);  // 0xFFFFFFFF when no differing flag in this word
+    j = (j == 0xFFFFFFFFu) ? (fk ? last0 : last1) : 32 * i + j;
+    const uint32_t old = lds_u8(a_sI + j + 1);  // j = 0xFFFFFFFF reads I[0]
+    const uint32_t ta = fk ? prev : old, tb = fk ? old : prev;
+    if (live) {
+      if (pl) {
+        pl[0] = (uint8_t)ta;
+        pl[1] = (uint8_t)tb;
+        pl[2] = (uint8_t)n;
+      }
+      if (pg) {
+        pg[0] = vb + ta;
+        pg[1] = vb + tb;
+        pg[2] = vb + n;
+      }
+    }
+    if (pl) pl += 96;
+    if (pg) pg += 96;
+    const uint32_t hf = msb(f), hnf = msb(~f);
+    if (hf != 0xFFFFFFFFu) last1 = 32 * i + hf;
+    if (hnf != 0xFFFFFFFFu) last0 = 32 * i + hnf;
+    base += __popc(inc);
+  }
+  if (CHECKED && __any_sync(kFull, bad)) return false;
+  // positions
   const uint32_t *pw = sw + 2 * nw + ((d.T + 2 - d.V) * d.w + 31) / 32;
-  float *op = out_pos + 3ull * d.vbase;
-  if (small_coords(d)) {
-    for (uint32_t v = lane; v < d.V; v += 32) {
-      uint32_t q[3];
-      vertex_q<B16>(pw, v, d.b, q);
-#pragma unroll
-      for (int c = 0; c < 3; c++) op[3 * v + c] = dequant_small(d.L[c] + q[c], g.G[c], g.D[c]);
+  float *op = out_pos + 3ull * (d.vbase + lane);
+  if (B16 && small_coords(d)) {
+    const uint32_t a_pw = smem_addr(pw) + 6 * lane;
+    for (uint32_t v = lane, a = a_pw; v < d.V; v += 32, a += 192, op += 96) {
+      op[0] = dequant_small(d.L[0] + lds_u16(a), g.G[0], g.D[0]);
+      op[1] = dequant_small(d.L[1] + lds_u16(a + 2), g.G[1], g.D[1]);
+      op[2] = dequant_small(d.L[2] + lds_u16(a + 4), g.G[2], g.D[2]);
     }
   } else {
-    for (uint32_t v = lane; v < d.V; v += 32) {
+    for (uint32_t v = lane; v < d.V; v += 32, op += 96) {
       uint32_t q[3];
       vertex_q<B16>(pw, v, d.b, q);
 #pragma unroll
-      for (int c = 0; c < 3; c++) op[3 * v + c] = dequant(d.L[c] + q[c], g.G[c], g.D[c]);
+      for (int c = 0; c < 3; c++) op[c] = dequant(d.L[c] + q[c], g.G[c], g.D[c]);
     }
   }
   __syncwarp();
-  return ok;
+  return true;
 }
 
 template <bool CHECKED>
