@@ -209,7 +209,8 @@ size_t mc_scratch_bytes(void);
 
 /* Plain decode: one launch over meshlets [first, first + count), one warp per
  * meshlet (the baseline; a per-mesh decode issues one call per mesh).
- * Outputs (any of d_local / d_global may be NULL, d_pos may not):
+ * Outputs (any of d_local / d_global may be NULL, d_pos may not; d_local and
+ * d_global must be 16-byte aligned):
  *   d_local  u8  [3 * total_tris]  local triangle indices, meshlet m at
  *            3 * tri_base(m); degenerates are kept (Sec. 4.2)
  *   d_global u32 [3 * total_tris]  vertex_base(m) + local

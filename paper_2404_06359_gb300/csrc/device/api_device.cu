@@ -131,7 +131,7 @@ extern "C" mc_status mc_decode_plain(const mc_device_batch *b, uint32_t first, u
   if (!d_pos || (uint64_t)first + count > b->n_meshlets) return MC_ERR_INVALID_ARG;
   uint32_t warps = (t && t->warps_per_cta) ? t->warps_per_cta : 8;
   if (warps > 32) return MC_ERR_INVALID_ARG;
-  if (count == 0) return MC_OK;
+  if (!aligned(d_local, 16) || !aligned(d_global, 16)) return MC_ERR_INVALID_ARG;
   cudaError_t e = launch_plain(args_of(b), first, count, warps, b->max_block_words,
                                t && t->checked, d_local, d_global, d_pos, d_status,
                                static_cast<cudaStream_t>(stream));
@@ -146,7 +146,9 @@ extern "C" mc_status mc_decode_batch(const mc_device_batch *b, uint8_t *d_local,
   if (b->n_meshlets == 0) return MC_OK;
   mc_status st = check_batch(b);
   if (st != MC_OK) return st;
-  if (!d_pos || !d_scratch || !aligned(d_scratch, 16)) return MC_ERR_INVALID_ARG;
+  if (!d_pos || !d_scratch || !aligned(d_scratch, 16) || !aligned(d_local, 16) ||
+      !aligned(d_global, 16))
+    return MC_ERR_INVALID_ARG;
   mc_tuning r = resolve_batch(b, t);
   return launch_batch_checked(b, d_local, d_global, d_pos, d_status, d_scratch, r,
                               static_cast<cudaStream_t>(stream));
