@@ -288,6 +288,10 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
     if (lane == 1) il |= 1u;
     Fs = r ? (fh << r) | (fl >> (32 - r)) : fh;
     Is = r ? (ih << r) | (il >> (32 - r)) : ih;
+    if (lane == 0 && r) {
+      Is |= (1u << r) - 1u;  // virtual triangles -r..-1: entries k + 2 from the scan
+      Fs |= 1u << (r - 1);   // virtual triangle -1 flagged R: "no differing flag" -> I[0]
+    }
   }
   uint32_t pre = __popc(Is);                               // -> exclusive prefix of popcounts
   int hi1 = Fs ? (int)(32 * lane + msb(Fs)) : -1;          // -> last flag-1 position before word
@@ -328,18 +332,16 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
     const int L1 = __shfl_sync(kFull, hi1, q), L0 = __shfl_sync(kFull, hi0, q);
     const int kk = (int)(4 * grp) - (int)r;
     const uint32_t fn = (Fq >> sh) & 0xFu, in = (Iq >> sh) & 0xFu;
-    uint32_t s = 1 + Pq + __popc(Iq & ((1u << sh) - 1u));
+    uint32_t s = 1 - r + Pq + __popc(Iq & ((1u << sh) - 1u));
     uint32_t n[4];
 #pragma unroll
     for (int e = 0; e < 4; e++) {
-      const int k = kk + e;
       const uint32_t isn = (in >> e) & 1u;
       s += isn;
-      const uint32_t slot = (isn || k < 0) ? 0u : (uint32_t)k + 1 - s;
-      const uint32_t rv = W8 ? lds_u8(a_rb + min(slot, 255u))
-                             : extract(sw + 2 * nw, min(slot, 255u) * d.w, d.w);
-      if (CHECKED && !isn && k > 0 && k < (int)T && rv > s) bad = true;
-      n[e] = k < 0 ? (uint32_t)(k + 2) : (isn ? s : rv);
+      const uint32_t slot = isn ? 0u : ((uint32_t)(kk + e) + 1 - s) & 255u;  // bounded for idle lanes
+      const uint32_t rv = W8 ? lds_u8(a_rb + slot) : extract(sw + 2 * nw, slot * d.w, d.w);
+      if (CHECKED && !isn && kk + e < (int)T && rv > s) bad = true;
+      n[e] = isn ? s : rv;
     }
     if (kk < (int)T)
       asm volatile("st.shared.u32 [%0], %1;" ::"r"(S + kk + 2),
@@ -355,8 +357,7 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
       const uint32_t fk = (fn >> e) & 1u;
       const uint32_t x = (Fq ^ (0u - fk)) & ((1u << (sh + e)) - 1u);
       const int jj = x ? (int)(32 * q + msb(x)) : (fk ? L0 : L1);
-      const int j = jj < 0 ? -1 : jj - (int)r;
-      const uint32_t old = lds_u8(S + min((uint32_t)(j + 1), 255u));  // bound for idle lanes
+      const uint32_t old = lds_u8(S + ((uint32_t)(jj + 1 - (int)r) & 255u));  // I[j+1], j = jj - r
       const uint32_t pv = e == 0 ? prev : n[e - 1];
       ta[e] = fk ? pv : old;
       tb[e] = fk ? old : pv;
