@@ -251,154 +251,71 @@ __device__ __forceinline__ uint32_t msb(uint32_t x) {
   return r;
 }
 
-// Full decode of one staged meshlet into the batch outputs.
-//
-// Each lane decodes four consecutive triangles per pass.  Lane groups are
-// aligned to the batch output, not to the meshlet: group g covers the
-// meshlet's triangles k = 4g - r .. 4g - r + 3 with r = tri_base mod 4, so a
-// full group writes its 12 index bytes as three 4-byte stores and its 12
-// global indices as three 16-byte stores.  To make each group's four L/R and
-// increment flags one aligned nibble, the flag words are first shifted left
-// by r (positions below r are virtual triangles with flag 0 / no increment).
-// With the increment bit of triangle 0 forced on and the scan seeded with 1,
-// the entry of triangle k is s_k = 1 + (set increment bits up to k) when its
-// bit is set -- triangle 0 gets 2 -- and reuse[k + 1 - s_k] otherwise
-// (Sec. 4.3).  The third vertex is I[j + 1] for the last j < k whose flag
-// differs (Sec. 4.2): 31 - clz within the shifted word, else the last such
-// position in earlier words from a per-word max-scan computed once per
-// meshlet; virtual positions never win because flag 0 of triangle 0 is real.
-// Stream entries of virtual triangles k < 0 are k + 2, which reproduces
-// I[0] = 0 and I[1] = 1.
+// Full decode of one staged meshlet into the batch outputs: the strip walk
+// of walk_triangles (same arithmetic) written out flat, with the first
+// triangle folded into the scan (increment bit 0 forced on and the scan
+// seeded with 1, so triangle 0 gets entry s = 2 with no special case) and
+// per-lane output pointers advanced by one word of triangles per pass.
 template <bool CHECKED, bool B16, bool W8>
 __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, const uint32_t *sw,
                                               uint8_t *sI, uint32_t lane, uint8_t *out_local,
                                               uint32_t *out_global, float *out_pos) {
   if (CHECKED && !stream_header_ok(d, sw)) return false;
-  const uint32_t T = d.T;
-  const uint32_t nw = (T + 31) >> 5;
-  const uint32_t r = d.tbase & 3u;
-  const uint32_t nws = (T + r + 31) >> 5;  // shifted words
-  // ---- per meshlet: shifted flag words, increment prefix, last-flag scans
-  uint32_t Fs = 0, Is = 0;
-  if (lane < nws) {
-    const uint32_t fh = lane < nw ? sw[lane] : 0u, fl = (lane >= 1 && lane - 1 < nw) ? sw[lane - 1] : 0u;
-    uint32_t ih = lane < nw ? sw[nw + lane] : 0u;
-    uint32_t il = (lane >= 1 && lane - 1 < nw) ? sw[nw + lane - 1] : 0u;
-    if (lane == 0) ih |= 1u;  // triangle 0 counts as new (seed of the scan)
-    if (lane == 1) il |= 1u;
-    Fs = r ? (fh << r) | (fl >> (32 - r)) : fh;
-    Is = r ? (ih << r) | (il >> (32 - r)) : ih;
-    if (lane == 0 && r) {
-      Is |= (1u << r) - 1u;  // virtual triangles -r..-1: entries k + 2 from the scan
-      Fs |= 1u << (r - 1);   // virtual triangle -1 flagged R: "no differing flag" -> I[0]
-    }
-  }
-  uint32_t pre = __popc(Is);                               // -> exclusive prefix of popcounts
-  int hi1 = Fs ? (int)(32 * lane + msb(Fs)) : -1;          // -> last flag-1 position before word
-  int hi0 = (lane < nws && ~Fs) ? (int)(32 * lane + msb(~Fs)) : -1;
-#pragma unroll
-  for (uint32_t o = 1; o < 16; o <<= 1) {
-    const uint32_t p2 = __shfl_up_sync(kFull, pre, o);
-    const int a1 = __shfl_up_sync(kFull, hi1, o), a0 = __shfl_up_sync(kFull, hi0, o);
-    if (lane >= o) {
-      pre += p2;
-      hi1 = max(hi1, a1);
-      hi0 = max(hi0, a0);
-    }
-  }
-  // make them exclusive (word q needs the values of words < q)
-  pre = __shfl_up_sync(kFull, pre, 1);
-  hi1 = __shfl_up_sync(kFull, hi1, 1);
-  hi0 = __shfl_up_sync(kFull, hi0, 1);
-  if (lane == 0) {
-    pre = 0;
-    hi1 = -1;
-    hi0 = -1;
-  }
-  // ---- strip entries, four per lane, into sI (base S: I[4g - r + 2] 4-byte aligned)
+  const uint32_t nw = (d.T + 31) >> 5;
   const uint32_t a_sw = smem_addr(sw);
-  const uint32_t a_rb = a_sw + 8 * nw;
-  const uint32_t S = smem_addr(sI) + 4 + ((r + 2) & 3u);
-  const uint32_t passes = (T + r + 127) >> 7;
+  const uint32_t a_rb = a_sw + 8 * nw;  // reuse section (bytes)
+  const uint32_t a_sI = smem_addr(sI);
+  if (lane < 2) sts_u8(a_sI + lane, lane);  // I[0], I[1]; I[2] is triangle 0's entry
+  const uint32_t le = (2u << lane) - 1u, lt = (1u << lane) - 1u;
+  uint8_t *pl = out_local ? out_local + 3ull * (d.tbase + lane) : nullptr;
+  uint32_t *pg = out_global ? out_global + 3ull * (d.tbase + lane) : nullptr;
   const uint32_t vb = d.vbase;
-  if (lane < 2) sts_u8(S + lane, lane);  // I[0] = 0, I[1] = 1
+  uint32_t base = 1, carry = 1, last0 = 0xFFFFFFFFu, last1 = 0xFFFFFFFFu;
   bool bad = false;
-  uint32_t carry = 1u - r;  // entry before the first group (virtual when r > 0)
-  for (uint32_t p = 0; p < passes; p++) {
-    const uint32_t grp = lane + 32 * p;
-    const uint32_t q = grp >> 3, sh = (grp & 7u) * 4;
-    const uint32_t Fq = __shfl_sync(kFull, Fs, q), Iq = __shfl_sync(kFull, Is, q);
-    const uint32_t Pq = __shfl_sync(kFull, pre, q);
-    const int L1 = __shfl_sync(kFull, hi1, q), L0 = __shfl_sync(kFull, hi0, q);
-    const int kk = (int)(4 * grp) - (int)r;
-    const uint32_t fn = (Fq >> sh) & 0xFu, in = (Iq >> sh) & 0xFu;
-    uint32_t s = 1 - r + Pq + __popc(Iq & ((1u << sh) - 1u));
-    uint32_t n[4];
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-      const uint32_t isn = (in >> e) & 1u;
-      s += isn;
-      const uint32_t slot = isn ? 0u : ((uint32_t)(kk + e) + 1 - s) & 255u;  // bounded for idle lanes
-      const uint32_t rv = W8 ? lds_u8(a_rb + slot) : extract(sw + 2 * nw, slot * d.w, d.w);
-      if (CHECKED && !isn && kk + e < (int)T && rv > s) bad = true;
-      n[e] = isn ? s : rv;
-    }
-    if (kk < (int)T)
-      asm volatile("st.shared.u32 [%0], %1;" ::"r"(S + kk + 2),
-                   "r"((n[0] & 0xFFu) | ((n[1] & 0xFFu) << 8) | ((n[2] & 0xFFu) << 16) | (n[3] << 24))
-                   : "memory");
-    uint32_t prev = __shfl_up_sync(kFull, n[3], 1);
+  uint32_t k = lane;
+  for (uint32_t i = 0; i < nw; i++, k += 32) {
+    const uint32_t f = lds_u32(a_sw + 4 * i);
+    const uint32_t inc = lds_u32(a_sw + 4 * (nw + i)) | (i == 0 ? 1u : 0u);
+    const uint32_t s = base + __popc(inc & le);
+    const bool is_new = (inc & (1u << lane)) != 0;
+    const uint32_t slot = is_new ? 0u : k + 1 - s;
+    const uint32_t r = W8 ? lds_u8(a_rb + slot) : extract(sw + 2 * nw, slot * d.w, d.w);
+    const uint32_t n = is_new ? s : r;
+    const bool live = k < d.T;
+    if (CHECKED && live && !is_new && r > s) bad = true;  // entries seen so far: 0..s
+    if (live) sts_u8(a_sI + k + 2, n);
+    uint32_t prev = __shfl_up_sync(kFull, n, 1);
     if (lane == 0) prev = carry;
-    carry = __shfl_sync(kFull, n[3], 31);
+    carry = __shfl_sync(kFull, n, 31);
     __syncwarp();
-    uint32_t ta[4], tb[4];
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-      const uint32_t fk = (fn >> e) & 1u;
-      const uint32_t x = (Fq ^ (0u - fk)) & ((1u << (sh + e)) - 1u);
-      const int jj = x ? (int)(32 * q + msb(x)) : (fk ? L0 : L1);
-      const uint32_t old = lds_u8(S + ((uint32_t)(jj + 1 - (int)r) & 255u));  // I[j+1], j = jj - r
-      const uint32_t pv = e == 0 ? prev : n[e - 1];
-      ta[e] = fk ? pv : old;
-      tb[e] = fk ? old : pv;
-    }
-    // ---- outputs
-    if (kk >= 0 && kk + 3 < (int)T) {
-      const uint64_t o = 3ull * (d.tbase + (uint32_t)kk);  // multiple of 12
-      if (out_local) {
-        uint32_t *pl = reinterpret_cast<uint32_t *>(out_local + o);
-        pl[0] = (ta[0] & 0xFFu) | ((tb[0] & 0xFFu) << 8) | ((n[0] & 0xFFu) << 16) | (ta[1] << 24);
-        pl[1] = (tb[1] & 0xFFu) | ((n[1] & 0xFFu) << 8) | ((ta[2] & 0xFFu) << 16) | (tb[2] << 24);
-        pl[2] = (n[2] & 0xFFu) | ((ta[3] & 0xFFu) << 8) | ((tb[3] & 0xFFu) << 16) | (n[3] << 24);
+    const uint32_t fk = (f >> lane) & 1u;
+    const uint32_t x = (f ^ (0u - fk)) & lt;
+    uint32_t j = msb(x);  // 0xFFFFFFFF when no differing flag in this word
+    j = (j == 0xFFFFFFFFu) ? (fk ? last0 : last1) : 32 * i + j;
+    const uint32_t old = lds_u8(a_sI + j + 1);  // j = 0xFFFFFFFF reads I[0]
+    const uint32_t ta = fk ? prev : old, tb = fk ? old : prev;
+    if (live) {
+      if (pl) {
+        pl[0] = (uint8_t)ta;
+        pl[1] = (uint8_t)tb;
+        pl[2] = (uint8_t)n;
       }
-      if (out_global) {
-        uint4 *pg = reinterpret_cast<uint4 *>(out_global + o);
-        pg[0] = make_uint4(vb + ta[0], vb + tb[0], vb + n[0], vb + ta[1]);
-        pg[1] = make_uint4(vb + tb[1], vb + n[1], vb + ta[2], vb + tb[2]);
-        pg[2] = make_uint4(vb + n[2], vb + ta[3], vb + tb[3], vb + n[3]);
-      }
-    } else {
-#pragma unroll
-      for (int e = 0; e < 4; e++) {
-        const int k = kk + e;
-        if (k < 0 || k >= (int)T) continue;
-        const uint64_t o = 3ull * (d.tbase + (uint32_t)k);
-        if (out_local) {
-          out_local[o] = (uint8_t)ta[e];
-          out_local[o + 1] = (uint8_t)tb[e];
-          out_local[o + 2] = (uint8_t)n[e];
-        }
-        if (out_global) {
-          out_global[o] = vb + ta[e];
-          out_global[o + 1] = vb + tb[e];
-          out_global[o + 2] = vb + n[e];
-        }
+      if (pg) {
+        pg[0] = vb + ta;
+        pg[1] = vb + tb;
+        pg[2] = vb + n;
       }
     }
+    if (pl) pl += 96;
+    if (pg) pg += 96;
+    const uint32_t hf = msb(f), hnf = msb(~f);
+    if (hf != 0xFFFFFFFFu) last1 = 32 * i + hf;
+    if (hnf != 0xFFFFFFFFu) last0 = 32 * i + hnf;
+    base += __popc(inc);
   }
   if (CHECKED && __any_sync(kFull, bad)) return false;
-  // ---- positions
-  const uint32_t *pw = sw + 2 * nw + ((T + 2 - d.V) * d.w + 31) / 32;
+  // positions
+  const uint32_t *pw = sw + 2 * nw + ((d.T + 2 - d.V) * d.w + 31) / 32;
   float *op = out_pos + 3ull * (d.vbase + lane);
   if (B16 && small_coords(d)) {
     const uint32_t a_pw = smem_addr(pw) + 6 * lane;
