@@ -233,6 +233,28 @@ mc_status mc_decode_batch(const mc_device_batch *b, uint8_t *d_local, uint32_t *
                           float *d_pos, uint32_t *d_status, void *d_scratch,
                           const mc_tuning *t, void *stream);
 
+/* Allocation-free form of mc_decode_batch (no counterpart in the paper: it
+ * only changes where the decoder's scratch lives).  Some callers cannot hand
+ * the library a scratch buffer: hosts that own every device allocation and
+ * forbid libraries from allocating, or render loops where a cudaMalloc would
+ * implicitly synchronise the device mid-frame.  This call takes no d_scratch;
+ * the work-queue counters live in a 256-byte file-scope device array of the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  The call allocates nothing (no cudaMalloc / cudaFree): it clears
+ * the counters with cudaMemsetAsync on `stream` and launches the same kernel
+ * with the same outputs and launch shapes as mc_decode_batch.
+ *   - The first call on a device looks up the array's device address for
+ *     that device (with that device current); make that first call before
+ *     any stream capture.
+ *   - All calls on a device share the array: calls whose kernels overlap on
+ *     the GPU (e.g. on two streams) race and give wrong results; serialise
+ *     them.
+ *   - MC_ERR_LIMIT if the batch has more than 2^31 meshlets (the 32-bit
+ *     counters need headroom) or the device ordinal is 64 or more. */
+mc_status mc_decode_batch_noalloc(const mc_device_batch *b, uint8_t *d_local, uint32_t *d_global,
+                                  float *d_pos, uint32_t *d_status, const mc_tuning *t,
+                                  void *stream);
+
 /* Fused decode + cull + compaction in one persistent launch.
  *   d_view_proj  16 FP32, row-major clip matrix: clip = M [x y z 1]^T
  *   d_tri_out    u32 [3 * total_tris]: surviving triangles as global index

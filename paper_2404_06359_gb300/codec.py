@@ -75,6 +75,8 @@ _SIGS = [
                                   C.POINTER(mc_tuning), P]),
     ("mc_decode_batch", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P,
                                   C.POINTER(mc_tuning), P]),
+    ("mc_decode_batch_noalloc", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P,
+                                          C.POINTER(mc_tuning), P]),
     ("mc_decode_cull", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P, P,
                                  C.POINTER(mc_tuning), P]),
     ("mc_autotune", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P, P,
@@ -334,6 +336,15 @@ def mc_decode_batch(db: DeviceBatch, d_local, d_global, d_pos, d_status, d_scrat
     _check(lib().mc_decode_batch(C.byref(db.c), _tptr(d_local), _tptr(d_global), _tptr(d_pos),
                                  _tptr(d_status), _tptr(d_scratch), _tuning(tuning), _stream(stream)),
            "mc_decode_batch")
+
+
+def mc_decode_batch_noalloc(db: DeviceBatch, d_local, d_global, d_pos, d_status, tuning=None,
+                            stream=None):
+    """mc_decode_batch without a scratch argument (the library's own static
+    device array holds the work-queue counters; nothing is allocated)."""
+    _check(lib().mc_decode_batch_noalloc(C.byref(db.c), _tptr(d_local), _tptr(d_global),
+                                         _tptr(d_pos), _tptr(d_status), _tuning(tuning),
+                                         _stream(stream)), "mc_decode_batch_noalloc")
 
 
 def mc_decode_cull(db: DeviceBatch, d_view_proj, d_tri_out, d_tri_count, d_pos, d_status, d_scratch,

@@ -139,6 +139,61 @@ extern "C" mc_status mc_decode_plain(const mc_device_batch *b, uint32_t first, u
   return from_cuda(e);
 }
 
+// ------------------------------------------------ allocation-free variant
+//
+// mc_decode_batch needs a small caller-provided device scratch buffer for its
+// work-queue counters.  Some callers cannot provide one: hosts that own every
+// device allocation and forbid libraries from allocating (engines running a
+// fixed memory budget), or code paths where a cudaMalloc would implicitly
+// synchronise the device in the middle of a frame.  For them the counters
+// live in this file-scope device array instead.  It is created when the
+// library's device code is loaded and every GPU that loads the library keeps
+// it until the process exits; all calls on a device share it.
+namespace {
+constexpr size_t kNoAllocScratchBytes = 256;  // the counters need mc_scratch_bytes()
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocScratchBytes / 4];
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (the name alone is a host-side stand-in, not a device address).
+mc_status noalloc_scratch_address(void **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MC_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return MC_ERR_LIMIT;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MC_ERR_CUDA;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return MC_OK;
+}
+}  // namespace
+
+extern "C" mc_status mc_decode_batch_noalloc(const mc_device_batch *b, uint8_t *d_local,
+                                             uint32_t *d_global, float *d_pos, uint32_t *d_status,
+                                             const mc_tuning *t, void *stream) {
+  if (!b) return MC_ERR_INVALID_ARG;
+  if (b->n_meshlets == 0) return MC_OK;
+  mc_status st = check_batch(b);
+  if (st != MC_OK) return st;
+  if (!d_pos || !aligned(d_local, 16) || !aligned(d_global, 16)) return MC_ERR_INVALID_ARG;
+  // the fixed array holds the queue counters; the counters are 32-bit, so the
+  // batch must leave headroom for the grabs that run past the last meshlet
+  if (mc_scratch_bytes() > kNoAllocScratchBytes || b->n_meshlets > (1u << 31)) return MC_ERR_LIMIT;
+  void *scratch = nullptr;
+  st = noalloc_scratch_address(&scratch);
+  if (st != MC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the array keeps whatever the previous call left: start from zero
+  if (cudaMemsetAsync(scratch, 0, mc_scratch_bytes(), s) != cudaSuccess) return MC_ERR_CUDA;
+  mc_tuning r = resolve_batch(b, t);
+  return launch_batch_checked(b, d_local, d_global, d_pos, d_status, scratch, r, s);
+}
+
 extern "C" mc_status mc_decode_batch(const mc_device_batch *b, uint8_t *d_local, uint32_t *d_global,
                                      float *d_pos, uint32_t *d_status, void *d_scratch,
                                      const mc_tuning *t, void *stream) {
