@@ -49,9 +49,10 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# DRAM bytes per launch of the decode kernel from one ncu capture, valid only
-# while the kernel sources hash to `sources`; scaled by decoded triangle slots.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) of one decode_batch launch from an ncu capture
+# (profiles/decode_batch_cfg2.md), per decoded triangle slot and keyed by the
+# kernel-source hash it was taken on; reported only while the sources match.
+NCU_TRAFFIC = {"3d9d30eda6b818df": {2: 429.408e6 / 18015946}}
 
 
 def _kernel_hash():
