@@ -37,6 +37,9 @@ WORKLOADS = {
        "b in {12,16,20} per meshlet, shuffled, u8 + u32 + f32, one persistent launch (CUDA graph)",
     4: "cfg4: cfg2 generator grown to >=50M triangles, fused decode + frustum/back-face cull + "
        "compaction, 64 camera poses, one CUDA graph",
+    5: "cfg5: serving loop, Poisson arrivals (2000 meshes/s) over a resident pool of seeded "
+       "spheres/tori/height fields (1k-2M triangles, mixed meshlet limits), 8 GB output budget, "
+       "continuous batching over 4 streams",
 }
 
 
@@ -138,13 +141,21 @@ def _dist():
 
 
 def _allreduce_max(x: float, ws: int) -> float:
+    """Max over ranks (timing is reported as the slowest rank's)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_gtps(ws: int, tris_per_rank: int, steps: int, max_total_ms: float) -> float:
+    """Whole-job throughput: every rank decodes its own batch each step
+    (weak scaling), divided by the slowest rank's time."""
+    return ws * tris_per_rank * steps / (max_total_ms * 1e-3) / 1e9
 
 
 def _barrier(ws):
@@ -212,6 +223,43 @@ def run_reference(args, ws, rank):
     print(json.dumps(out), flush=True)
 
 
+def run_serving(args, ws, rank):
+    """cfg5: the continuous-batching loop for --serve-seconds of arrivals."""
+    import torch
+    from paper_2404_06359_gb300 import meshgen as G
+    from paper_2404_06359_gb300 import serving as S
+    t_build = time.time()
+    pool, _ = S.build_pool(args.pool_meshes, seed=G.SEED_BASE + 5 + 1000 * rank)
+    t_build = time.time() - t_build
+    srv = S.Server(pool, budget_bytes=8 << 30, n_streams=4)
+    # warm-up: a short burst (not reported)
+    wa, wm = G.poisson_arrivals(args.rate, 0.2, len(srv.meshes), G.SEED_BASE + 7)
+    srv.run(wa, wm)
+    srv.launches = 0
+    arr, mid = G.poisson_arrivals(args.rate, args.serve_seconds, len(srv.meshes), G.SEED_BASE + 6)
+    n0 = mc_launches()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        done, st = srv.run(arr, mid)
+    launches = mc_launches() - n0
+    g = _allreduce_max(st["wall_s"], ws)
+    value = aggregate_gtps(ws, st["input_triangles"], 1, g * 1e3)
+    res = {"metric": METRIC, "value": round(value, 4), "unit": "Gtps", "n_gpus": ws, "steps": 1,
+           "warmup": args.warmup, "ms_per_step": round(g * 1e3, 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32", "data": "synthetic",
+           "config": {"workload": WORKLOADS[5], "pool_meshes": args.pool_meshes,
+                      "rate_per_s": args.rate, "seconds": args.serve_seconds},
+           "latency_ms": {"p50": round(st["p50_ms"], 3), "p99": round(st["p99_ms"], 3)},
+           "serving": st, "gpu_launches": int(launches), "clocks": clk.summary(),
+           "roofline": None, "build_s": round(t_build, 1)}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+def mc_launches():
+    from paper_2404_06359_gb300 import codec as mc
+    return mc.mc_launch_count()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -225,6 +273,9 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--tuning", default="", help="warps,ctas_per_sm,meshlets_per_grab (skips the autotuner)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--pool-meshes", type=int, default=128)
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
@@ -236,6 +287,9 @@ def main():
 
     assert args.warmup >= 3, "at least 3 warm-up steps"
     torch.cuda.set_device(local)
+    if args.config == 5:
+        run_serving(args, ws, rank)
+        return
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -361,10 +415,14 @@ def main():
                    "d2h_bytes_per_step": int(3 * T + (12 * T if want_global else 0) + 12 * V)}
 
     ms_step = total_ms / args.steps
-    value = ws * input_tris * args.steps / (total_ms * 1e-3) / 1e9
+    views = len(vps) if cull else 1  # the cull step decodes the batch once per view
+    value = aggregate_gtps(ws, input_tris * views, args.steps, total_ms)
     peak, peak_kind = _peaks()
     per_launch_s = (times.mean() * 1e-3) / launches_per_step
     bytes_per_launch = nbytes["total"] if not cull else None
+    if cull:
+        counts_np = counts.cpu().numpy().astype(np.int64)
+        bytes_per_launch = W.cull_bytes(stats, arrays, vps, counts_np)
     roof = None
     if bytes_per_launch:
         ach = bytes_per_launch / per_launch_s / 1e9
@@ -377,10 +435,9 @@ def main():
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS hbm_gbs)",
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "bytes_per_input_triangle": round(bytes_per_launch / input_tris, 2)}
-    else:
-        counts_np = counts.cpu().numpy()
+    if cull:
         extra["cull"] = {"kept_fraction_mean": float(counts_np.mean() / input_tris),
-                         "views": len(vps)}
+                         "views": len(vps), "triangles_per_step": input_tris * len(vps)}
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gtps", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True,

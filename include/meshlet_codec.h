@@ -233,6 +233,35 @@ mc_status mc_decode_batch(const mc_device_batch *b, uint8_t *d_local, uint32_t *
                           float *d_pos, uint32_t *d_status, void *d_scratch,
                           const mc_tuning *t, void *stream);
 
+/* One decode request of a serving batch: a range of meshlets of a resident
+ * pool batch (e.g. one mesh of it) and the request's own output buffers.
+ * Its decoded triangles and vertices are numbered from the range's first
+ * meshlet: global index = (vertex_base(m) - vertex_base) + local. */
+typedef struct {
+  uint32_t first_meshlet; /* range of the pool batch */
+  uint32_t n_meshlets;
+  uint32_t work_start;    /* sum of n_meshlets of the requests before this one */
+  uint32_t reserved0;
+  uint32_t tri_base;      /* tri_base / vertex_base of first_meshlet */
+  uint32_t vertex_base;
+  uint32_t tri_count;     /* output capacity: sum of T' / V over the range */
+  uint32_t vert_count;
+  uint8_t *d_local;       /* u8 [3 tri_count] or NULL, 16-byte aligned */
+  uint32_t *d_global;     /* u32 [3 tri_count] or NULL, 16-byte aligned */
+  float *d_pos;           /* f32 [3 vert_count] */
+  void *reserved1;
+} mc_request;
+
+/* Continuous-batching decode: the meshlet ranges of n_reqs requests (a device
+ * array, work_start ascending, total_work = sum of n_meshlets) in one
+ * persistent launch whose warps pull meshlets from the work queue in
+ * d_scratch, each written to its request's buffers.  The decoded bits are
+ * those of mc_decode_batch on the same meshlets (Sec. 4.2-4.4), only renumbered
+ * per request, so a request decodes the same alone or in any mix. */
+mc_status mc_decode_requests(const mc_device_batch *pool, const mc_request *d_reqs,
+                             uint32_t n_reqs, uint32_t total_work, uint32_t *d_status,
+                             void *d_scratch, const mc_tuning *t, void *stream);
+
 /* Allocation-free form of mc_decode_batch (no counterpart in the paper: it
  * only changes where the decoder's scratch lives).  Some callers cannot hand
  * the library a scratch buffer: hosts that own every device allocation and

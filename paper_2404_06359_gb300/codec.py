@@ -48,6 +48,13 @@ class mc_device_batch(C.Structure):
                 ("max_block_words", u32)]
 
 
+class mc_request(C.Structure):
+    _fields_ = [("first_meshlet", u32), ("n_meshlets", u32), ("work_start", u32),
+                ("reserved0", u32), ("tri_base", u32), ("vertex_base", u32), ("tri_count", u32),
+                ("vert_count", u32), ("d_local", P), ("d_global", P), ("d_pos", P),
+                ("reserved1", P)]
+
+
 class mc_tuning(C.Structure):
     _fields_ = [("warps_per_cta", u32), ("ctas_per_sm", u32), ("meshlets_per_grab", u32),
                 ("checked", u32)]
@@ -79,6 +86,8 @@ _SIGS = [
                                           C.POINTER(mc_tuning), P]),
     ("mc_decode_cull", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P, P,
                                  C.POINTER(mc_tuning), P]),
+    ("mc_decode_requests", C.c_int, [C.POINTER(mc_device_batch), P, u32, u32, P, P,
+                                     C.POINTER(mc_tuning), P]),
     ("mc_autotune", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P, P,
                               C.POINTER(mc_tuning), C.POINTER(C.c_float)]),
     ("mc_graph_capture_batch", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P,
@@ -352,6 +361,21 @@ def mc_decode_cull(db: DeviceBatch, d_view_proj, d_tri_out, d_tri_count, d_pos, 
     _check(lib().mc_decode_cull(C.byref(db.c), _tptr(d_view_proj), _tptr(d_tri_out),
                                 _tptr(d_tri_count), _tptr(d_pos), _tptr(d_status), _tptr(d_scratch),
                                 _tuning(tuning), _stream(stream)), "mc_decode_cull")
+
+
+REQUEST_DTYPE = np.dtype([("first_meshlet", "<u4"), ("n_meshlets", "<u4"), ("work_start", "<u4"),
+                          ("reserved0", "<u4"), ("tri_base", "<u4"), ("vertex_base", "<u4"),
+                          ("tri_count", "<u4"), ("vert_count", "<u4"), ("d_local", "<u8"),
+                          ("d_global", "<u8"), ("d_pos", "<u8"), ("reserved1", "<u8")])
+assert REQUEST_DTYPE.itemsize == C.sizeof(mc_request) == 64
+
+
+def mc_decode_requests(db: DeviceBatch, d_reqs, n_reqs: int, total_work: int, d_status, d_scratch,
+                       tuning=None, stream=None):
+    """d_reqs: a device tensor holding n_reqs mc_request records (REQUEST_DTYPE)."""
+    _check(lib().mc_decode_requests(C.byref(db.c), _tptr(d_reqs), n_reqs, total_work,
+                                    _tptr(d_status), _tptr(d_scratch), _tuning(tuning),
+                                    _stream(stream)), "mc_decode_requests")
 
 
 def mc_autotune(db: DeviceBatch, d_local, d_global, d_pos, d_status, d_scratch, stream=None):

@@ -243,6 +243,32 @@ extern "C" mc_status mc_decode_cull(const mc_device_batch *b, const float *d_vie
                              static_cast<cudaStream_t>(stream));
 }
 
+extern "C" mc_status mc_decode_requests(const mc_device_batch *pool, const mc_request *d_reqs,
+                                        uint32_t n_reqs, uint32_t total_work, uint32_t *d_status,
+                                        void *d_scratch, const mc_tuning *t, void *stream) {
+  if (!pool) return MC_ERR_INVALID_ARG;
+  if (n_reqs == 0 || total_work == 0) return MC_OK;
+  mc_status st = check_batch(pool);
+  if (st != MC_OK) return st;
+  if (!d_reqs || !aligned(d_reqs, 16) || !d_scratch || !aligned(d_scratch, 16) ||
+      total_work > (1u << 31))
+    return MC_ERR_INVALID_ARG;
+  const uint32_t warps = (t && t->warps_per_cta) ? t->warps_per_cta : 8;
+  const uint32_t per_grab = (t && t->meshlets_per_grab) ? t->meshlets_per_grab : 2;
+  if (warps > 32 || per_grab > 64) return MC_ERR_INVALID_ARG;
+  int occ = max_ctas_per_sm_requests(warps, pool->max_block_words);
+  if (occ <= 0) return MC_ERR_INVALID_ARG;
+  uint32_t per_sm = (t && t->ctas_per_sm) ? std::min<uint32_t>(t->ctas_per_sm, occ) : (uint32_t)occ;
+  // small request batches do not need the whole GPU
+  uint32_t ctas = std::min<uint32_t>(per_sm * (uint32_t)sm_count(),
+                                     std::max<uint32_t>(1u, (total_work + warps * per_grab - 1) / (warps * per_grab)));
+  cudaError_t e = launch_requests(args_of(pool), d_reqs, n_reqs, total_work, ctas, warps, per_grab,
+                                  t && t->checked, d_status, static_cast<uint32_t *>(d_scratch),
+                                  static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) g_launches++;
+  return from_cuda(e);
+}
+
 extern "C" mc_status mc_autotune(const mc_device_batch *b, uint8_t *d_local, uint32_t *d_global,
                                  float *d_pos, uint32_t *d_status, void *d_scratch, void *stream,
                                  mc_tuning *best, float *best_ms) {

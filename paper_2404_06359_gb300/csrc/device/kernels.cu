@@ -139,6 +139,83 @@ __global__ void __launch_bounds__(512) decode_batch_kernel(BatchArgs a, uint32_t
   }
 }
 
+// Continuous-batching decode: persistent warps take `per_grab` work items
+// (meshlets of the concatenated request ranges); each item is mapped to its
+// request by binary search over work_start, its descriptor is renumbered
+// relative to the request's first meshlet, and it decodes into the request's
+// buffers.
+template <bool CHECKED>
+__global__ void __launch_bounds__(512) decode_requests_kernel(BatchArgs a, const mc_request *reqs,
+                                                              uint32_t n_reqs, uint32_t total_work,
+                                                              uint32_t per_grab, uint32_t *status,
+                                                              uint32_t *scratch) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const uint32_t spw = 4 * (((a.max_block_words + 3) & ~3u) + kSlackWords) + kStreamBytes;
+  uint8_t *base = smem + warp * spw;
+  uint32_t *sw = reinterpret_cast<uint32_t *>(base);
+  uint8_t *sI = base + spw - kStreamBytes;
+  for (;;) {
+    uint32_t w0 = 0;
+    if (lane == 0) w0 = atomicAdd(scratch + kQueue, per_grab);
+    w0 = __shfl_sync(kFull, w0, 0);
+    if (w0 >= total_work) break;
+    const uint32_t w1 = min(total_work, w0 + per_grab);
+    // request holding w0: the last with work_start <= w0
+    uint32_t lo = 0, hi = n_reqs;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (__ldg(&reqs[mid].work_start) <= w0) lo = mid; else hi = mid;
+    }
+    uint32_t r = lo;
+    for (uint32_t w = w0; w < w1; w++) {
+      while (r + 1 < n_reqs && __ldg(&reqs[r + 1].work_start) <= w) r++;
+      const mc_request *q = reqs + r;
+      const uint32_t item = w - __ldg(&q->work_start);
+      if (item >= __ldg(&q->n_meshlets)) {  // work past a request's range: malformed table
+        if (lane == 0) set_status(status, MC_ERR_INVALID_ARG);
+        continue;
+      }
+      const uint32_t m = __ldg(&q->first_meshlet) + item;
+      if (m >= a.n_meshlets) {
+        if (lane == 0) set_status(status, MC_ERR_INVALID_ARG);
+        continue;
+      }
+      Desc d = load_desc(a.desc + m);
+      d.tbase -= __ldg(&q->tri_base);
+      d.vbase -= __ldg(&q->vertex_base);
+      BatchArgs ra = a;
+      ra.total_tris = __ldg(&q->tri_count);
+      ra.total_verts = __ldg(&q->vert_count);
+      if (!header_ok(d, ra)) {
+        if (lane == 0) set_status(status, MC_ERR_CORRUPT);
+        continue;
+      }
+      uint8_t *ol = reinterpret_cast<uint8_t *>(__ldg(reinterpret_cast<const unsigned long long *>(&q->d_local)));
+      uint32_t *og = reinterpret_cast<uint32_t *>(__ldg(reinterpret_cast<const unsigned long long *>(&q->d_global)));
+      float *op = reinterpret_cast<float *>(__ldg(reinterpret_cast<const unsigned long long *>(&q->d_pos)));
+      if (!op) {
+        if (lane == 0) set_status(status, MC_ERR_INVALID_ARG);
+        continue;
+      }
+      const Grid g = load_grid(a.grids + d.grid);
+      stage_payload(d, a.payload, sw, lane);
+      __syncwarp();
+      if (!decode_dispatch<CHECKED>(d, g, sw, sI, lane, ol, og, op) && lane == 0)
+        set_status(status, MC_ERR_CORRUPT);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(scratch + kDone, 1u) == gridDim.x - 1) {
+      atomicExch(scratch + kQueue, 0u);
+      atomicExch(scratch + kDone, 0u);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- culling
 __device__ __forceinline__ float clip_row(const float *M, int r, float x, float y, float z) {
   return __fmaf_rn(M[4 * r + 2], z, __fmaf_rn(M[4 * r + 1], y, __fmaf_rn(M[4 * r + 0], x, M[4 * r + 3])));
@@ -377,6 +454,32 @@ cudaError_t launch_cull(const BatchArgs &a, const float *view_proj, uint32_t cta
                                                              out_pos, status, scratch);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_requests(const BatchArgs &a, const mc_request *reqs, uint32_t n_reqs,
+                            uint32_t total_work, uint32_t ctas, uint32_t warps, uint32_t per_grab,
+                            bool checked, uint32_t *status, uint32_t *scratch, cudaStream_t s) {
+  const uint32_t spw = 4 * (((a.max_block_words + 3) & ~3u) + kSlackWords) + kStreamBytes;
+  const uint32_t smem = spw * warps;
+  if (checked) {
+    cudaFuncSetAttribute(decode_requests_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    decode_requests_kernel<true><<<ctas, warps * 32, smem, s>>>(a, reqs, n_reqs, total_work, per_grab,
+                                                                status, scratch);
+  } else {
+    cudaFuncSetAttribute(decode_requests_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    decode_requests_kernel<false><<<ctas, warps * 32, smem, s>>>(a, reqs, n_reqs, total_work, per_grab,
+                                                                 status, scratch);
+  }
+  return cudaGetLastError();
+}
+
+int max_ctas_per_sm_requests(uint32_t warps, uint32_t max_block_words) {
+  int n = 0;
+  const int smem = (int)((4 * (((max_block_words + 3) & ~3u) + kSlackWords) + kStreamBytes) * warps);
+  cudaFuncSetAttribute(decode_requests_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(decode_requests_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_requests_kernel<false>, warps * 32, smem);
+  return n;
 }
 
 int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words, uint32_t per_grab) {

@@ -30,4 +30,9 @@ cudaError_t launch_cull(const BatchArgs &a, const float *view_proj, uint32_t cta
 int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words, uint32_t per_grab);
 int max_ctas_per_sm_cull(uint32_t warps, uint32_t max_block_words);
 
+cudaError_t launch_requests(const BatchArgs &a, const mc_request *reqs, uint32_t n_reqs,
+                            uint32_t total_work, uint32_t ctas, uint32_t warps, uint32_t per_grab,
+                            bool checked, uint32_t *status, uint32_t *scratch, cudaStream_t s);
+int max_ctas_per_sm_requests(uint32_t warps, uint32_t max_block_words);
+
 }  // namespace mcdev

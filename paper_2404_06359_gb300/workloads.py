@@ -89,3 +89,35 @@ def algorithmic_bytes(stats: dict, desc: np.ndarray, local=True, global_=True) -
     write = (3 * Tt if local else 0) + (12 * Tt if global_ else 0) + 12 * Vt
     return {"read": read, "write": write, "total": read + write,
             "padding": 4 * int(((words + 3) // 4 * 4 - words).sum())}
+
+
+def cull_bytes(stats: dict, arrays: dict, vps: np.ndarray, counts: np.ndarray) -> int:
+    """Mean algorithmic bytes of one fused decode+cull launch: every descriptor
+    and grid entry, the payload and positions of the meshlets whose
+    quantisation box is not wholly outside one clip plane (box test in FP64 --
+    exact decisions near a plane do not matter for a byte count), and the
+    surviving triangles (12 B each)."""
+    w = arrays["desc"].view(np.uint32).reshape(-1, 8)
+    V = (w[:, 3] & 0xFFFF).astype(np.int64)
+    T = (w[:, 3] >> 16).astype(np.int64)
+    rw = (w[:, 4] & 0xFF).astype(np.int64)
+    b = ((w[:, 4] >> 8) & 0xFF).astype(np.int64)
+    words = 2 * ((T + 31) // 32) + ((T + 2 - V) * rw + 31) // 32 + (3 * V * b + 31) // 32
+    g = arrays["grids"].view(np.float32).reshape(-1, 8).astype(np.float64)
+    gid = (w[:, 4] >> 16).astype(np.int64)
+    L = w[:, 5:8].astype(np.float64)
+    lo = g[gid, 0:3] + L * g[gid, 4:7]
+    hi = g[gid, 0:3] + (L + (2.0 ** b - 1)[:, None]) * g[gid, 4:7]
+    corners = np.stack([np.where(np.array([(k >> c) & 1 for c in range(3)], bool), hi, lo)
+                        for k in range(8)], 1)                      # [M, 8, 3]
+    ch = np.concatenate([corners, np.ones(corners.shape[:2] + (1,))], 2)
+    total = 0.0
+    for vp, cnt in zip(vps, counts):
+        clip = ch @ vp.reshape(4, 4).astype(np.float64).T           # [M, 8, 4]
+        wv = clip[..., 3]
+        out = np.zeros(w.shape[0], bool)
+        for c in range(3):
+            out |= (clip[..., c] > wv).all(1) | (clip[..., c] < -wv).all(1)
+        keep = ~out
+        total += (4 * words[keep].sum() + 12 * V[keep].sum() + 12 * int(cnt))
+    return int(32 * w.shape[0] + 32 * stats["n_grids"] + total / len(vps))
