@@ -189,6 +189,7 @@ typedef struct {
   uint64_t total_tris;  /* capacity of the outputs, triangles (sum of T') */
   uint64_t total_verts; /* capacity of the outputs, vertices (sum of V) */
   uint32_t max_block_words; /* from mc_blob_view (sizes shared-memory staging) */
+  uint32_t max_tris;        /* largest T' (from mc_blob_view); 0 = 256 */
 } mc_device_batch;
 
 /* Launch shape; zero fields take the library defaults or the autotuned

@@ -45,7 +45,7 @@ class mc_blob_view_t(C.Structure):
 class mc_device_batch(C.Structure):
     _fields_ = [("desc", P), ("payload", P), ("grids", P), ("n_meshlets", u32), ("n_grids", u32),
                 ("payload_bytes", u64), ("total_tris", u64), ("total_verts", u64),
-                ("max_block_words", u32)]
+                ("max_block_words", u32), ("max_tris", u32)]
 
 
 class mc_request(C.Structure):
@@ -293,13 +293,14 @@ class DeviceBatch:
 
     @classmethod
     def from_arrays(cls, desc, payload, grids, total_tris, total_verts, max_block_words,
-                    device="cuda"):
+                    max_tris=256, device="cuda"):
         """Wrap blob arrays that did not come from ``mc_encode`` (e.g. a
         hand-packed stream); sizes are the caller's."""
         self = cls.__new__(cls)
         stats = {"n_meshlets": desc.shape[0], "n_grids": grids.shape[0],
                  "payload_bytes": payload.size, "total_tris": total_tris,
-                 "total_verts": total_verts, "max_block_words": max_block_words}
+                 "total_verts": total_verts, "max_block_words": max_block_words,
+                 "max_tris": max_tris}
         self._init(np.asarray(desc, np.uint8), np.asarray(payload, np.uint8),
                    np.asarray(grids, np.uint8), stats, device)
         self.meshes = []
@@ -315,7 +316,8 @@ class DeviceBatch:
         s = self.stats
         self.c = mc_device_batch(self.desc.data_ptr(), self.payload.data_ptr(), self.grids.data_ptr(),
                                  s["n_meshlets"], s["n_grids"], s["payload_bytes"], s["total_tris"],
-                                 s["total_verts"], max(1, s["max_block_words"]))
+                                 s["total_verts"], max(1, s["max_block_words"]),
+                                 s.get("max_tris", 256))
 
     def outputs(self, local=True, global_=True, device="cuda"):
         import torch

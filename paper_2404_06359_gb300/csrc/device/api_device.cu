@@ -69,6 +69,7 @@ BatchArgs args_of(const mc_device_batch *b) {
   a.total_tris = b->total_tris;
   a.total_verts = b->total_verts;
   a.max_block_words = b->max_block_words;
+  a.max_tris = (b->max_tris == 0 || b->max_tris > 256) ? 256 : b->max_tris;
   return a;
 }
 
@@ -213,16 +214,17 @@ namespace {
 mc_status launch_cull_checked(const mc_device_batch *b, const float *d_vp, uint32_t *d_tri_out,
                               uint32_t *d_tri_count, float *d_pos, uint32_t *d_status,
                               void *d_scratch, const mc_tuning *t, cudaStream_t s) {
-  uint32_t warps = (t && t->warps_per_cta) ? t->warps_per_cta : 8;
-  if (warps < 1 || warps > 32) return MC_ERR_INVALID_ARG;
-  int occ = max_ctas_per_sm_cull(warps, b->max_block_words);
+  const uint32_t warps = (t && t->warps_per_cta) ? t->warps_per_cta : 4;
+  const uint32_t per_grab = (t && t->meshlets_per_grab) ? t->meshlets_per_grab : 4;
+  if (warps < 1 || warps > 32 || per_grab < 1 || per_grab > 16) return MC_ERR_INVALID_ARG;
+  const BatchArgs a = args_of(b);
+  int occ = max_ctas_per_sm_cull(warps, b->max_block_words, a.max_tris, per_grab);
   if (occ <= 0) return MC_ERR_INVALID_ARG;
   uint32_t per_sm = (t && t->ctas_per_sm) ? std::min<uint32_t>(t->ctas_per_sm, occ) : (uint32_t)occ;
   uint32_t ctas = per_sm * (uint32_t)sm_count();
   if (ctas == 0) return MC_ERR_CUDA;
-  cudaError_t e = launch_cull(args_of(b), d_vp, ctas, warps, b->max_block_words, t && t->checked,
-                              d_tri_out, d_tri_count, d_pos, d_status,
-                              static_cast<uint32_t *>(d_scratch), s);
+  cudaError_t e = launch_cull(a, d_vp, ctas, warps, per_grab, t && t->checked, d_tri_out, d_tri_count,
+                              d_pos, d_status, static_cast<uint32_t *>(d_scratch), s);
   if (e == cudaSuccess) g_launches++;
   return from_cuda(e);
 }
@@ -441,6 +443,7 @@ extern "C" mc_status mc_decode_batch_host(const mc_blob_view_t *v, mc_desc *d_de
   b.total_tris = v->total_tris;
   b.total_verts = v->total_verts;
   b.max_block_words = v->max_block_words;
+  b.max_tris = v->max_tris;
   mc_status st = mc_decode_batch(&b, d_local, d_global, d_pos, d_status, d_scratch, t, stream);
   if (st != MC_OK) return st;
   if (h_local) e = cudaMemcpyAsync(h_local, d_local, 3 * v->total_tris, cudaMemcpyDeviceToHost, s);

@@ -89,6 +89,7 @@ struct BatchArgs {
   uint32_t n_meshlets, n_grids;
   uint64_t payload_bytes, total_tris, total_verts;
   uint32_t max_block_words;  // capacity of one meshlet's shared-memory slot
+  uint32_t max_tris;         // largest T' of the batch (sizes per-warp output buffers)
 };
 
 // Header sanity (all builds): a descriptor that passes cannot make the decode
@@ -98,7 +99,7 @@ __device__ __forceinline__ bool header_ok(const Desc &d, const BatchArgs &a) {
             d.w <= 8 && d.b >= 1 && d.b <= 32 && d.grid < a.n_grids;
   if (!ok) return false;
   const uint32_t padded = (block_words(d) + 3) & ~3u;
-  return padded <= a.max_block_words &&
+  return padded <= a.max_block_words && d.T <= a.max_tris &&
          16ull * d.off16 + 4ull * padded <= a.payload_bytes &&
          (uint64_t)d.tbase + d.T <= a.total_tris && (uint64_t)d.vbase + d.V <= a.total_verts;
 }
@@ -133,6 +134,35 @@ __device__ __forceinline__ void stage_payload(const Desc &d, const uint8_t *payl
   for (uint32_t i = lane; i < n4; i += 32) dst[i] = __ldg(src + i);
 }
 
+// 32-bit shared-window accessors (explicit LDS/STS addressing).
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t lds_u8(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u16(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts_u8(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u8 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+// position of the highest set bit, 0xFFFFFFFF for 0
+__device__ __forceinline__ uint32_t msb(uint32_t x) {
+  uint32_t r;
+  asm("bfind.u32 %0, %1;" : "=r"(r) : "r"(x));
+  return r;
+}
+
 // Stream-level consistency checks of the checked build: bit 0 of both flag
 // words clear, no flag bit past T', and V = 3 + (number of increment flags).
 __device__ __forceinline__ bool stream_header_ok(const Desc &d, const uint32_t *sw) {
@@ -146,52 +176,50 @@ __device__ __forceinline__ bool stream_header_ok(const Desc &d, const uint32_t *
 
 // Walks the meshlet's triangles 32 at a time, calling
 //   emit(k, a, b, c, live)
-// on every lane (live = k < T') with triangle k = (a, b, c).  One pass per
-// 32-triangle word builds the strip entries of the word (add-scan of the
-// increment word; reuse entries read at slot k + 1 - s), stores them to sI,
-// and assembles the word's triangles: I[k+1] comes from the neighbouring
-// lane (shuffle), I[k+2] is the lane's own entry, and the third vertex is
-// I[j+1] for the last j < k whose L/R flag differs from flag k -- found in
-// the current word by 31 - clz of the masked flag word, otherwise taken
-// from two running registers holding the last flag-0 and flag-1 positions
-// of the earlier words (no loop, no divergence).  CHECKED: returns false
-// (warp-uniform) if a reuse entry names a vertex not yet seen.
+// on every lane (live = k < T') with triangle k = (a, b, c) -- the same
+// arithmetic as decode_staged below: strip entries from the increment-word
+// add-scan (triangle 0 folded in as "new" with the scan seeded at 1) or the
+// reuse buffer, stored to sI; I[k+1] from the neighbouring lane; the third
+// vertex I[j+1] from the masked flag word's highest set bit or, for fans
+// reaching back past the word, from the running last-flag-0/1 positions.
+// CHECKED: returns false (warp-uniform) if a reuse entry names a vertex not
+// yet seen.
 template <bool CHECKED, bool W8, class Emit>
 __device__ __forceinline__ bool walk_triangles(const Desc &d, const uint32_t *sw, uint8_t *sI,
                                                uint32_t lane, Emit &&emit) {
   const uint32_t nw = (d.T + 31) >> 5;
-  const uint32_t *rw = sw + 2 * nw;  // reuse section
-  const uint8_t *rb = reinterpret_cast<const uint8_t *>(rw);
-  if (lane < 3) sI[lane] = (uint8_t)lane;
-  const uint32_t le = (2u << lane) - 1u;  // bits 0..lane
-  const uint32_t lt = (1u << lane) - 1u;  // bits below lane
-  uint32_t base = 2;                      // s of the last triangle of the previous words
-  uint32_t carry = 1;                     // I[32 i + 1]: the entry before this word's first
-  int last0 = -1, last1 = -1;             // last earlier position with flag 0 / flag 1
+  const uint32_t a_sw = smem_addr(sw);
+  const uint32_t a_rb = a_sw + 8 * nw;
+  const uint32_t a_sI = smem_addr(sI);
+  if (lane < 2) sts_u8(a_sI + lane, lane);
+  const uint32_t le = (2u << lane) - 1u, lt = (1u << lane) - 1u;
+  uint32_t base = 1, carry = 1, last0 = 0xFFFFFFFFu, last1 = 0xFFFFFFFFu;
   bool bad = false;
-  for (uint32_t i = 0; i < nw; i++) {
-    const uint32_t f = sw[i];
-    const uint32_t inc = sw[nw + i];
-    const uint32_t k = 32 * i + lane;
+  uint32_t k = lane;
+  for (uint32_t i = 0; i < nw; i++, k += 32) {
+    const uint32_t f = lds_u32(a_sw + 4 * i);
+    const uint32_t inc = lds_u32(a_sw + 4 * (nw + i)) | (i == 0 ? 1u : 0u);
     const uint32_t s = base + __popc(inc & le);
-    const bool is_new = (inc >> lane) & 1u;
-    const uint32_t slot = (is_new || k == 0) ? 0u : k + 1 - s;
-    const uint32_t r = W8 ? (uint32_t)rb[slot] : extract(rw, slot * d.w, d.w);
-    const uint32_t n = k == 0 ? 2u : (is_new ? s : r);
+    const bool is_new = (inc & (1u << lane)) != 0;
+    const uint32_t slot = is_new ? 0u : k + 1 - s;
+    const uint32_t r = W8 ? lds_u8(a_rb + slot) : extract(sw + 2 * nw, slot * d.w, d.w);
+    const uint32_t n = is_new ? s : r;
     const bool live = k < d.T;
-    if (CHECKED && live && !is_new && k != 0 && r > s) bad = true;  // seen so far: 0..s
-    if (live) sI[k + 2] = (uint8_t)n;
+    if (CHECKED && live && !is_new && r > s) bad = true;
+    if (live) sts_u8(a_sI + k + 2, n);
     uint32_t prev = __shfl_up_sync(kFull, n, 1);
     if (lane == 0) prev = carry;
     carry = __shfl_sync(kFull, n, 31);
     __syncwarp();
     const uint32_t fk = (f >> lane) & 1u;
     const uint32_t x = (f ^ (0u - fk)) & lt;
-    const int j = x ? (int)(32 * i + 31 - __clz(x)) : (fk ? last0 : last1);
-    const uint32_t old = sI[j + 1];
+    uint32_t j = msb(x);
+    j = (j == 0xFFFFFFFFu) ? (fk ? last0 : last1) : 32 * i + j;
+    const uint32_t old = lds_u8(a_sI + j + 1);
     emit(k, fk ? prev : old, fk ? old : prev, n, live);
-    if (f) last1 = (int)(32 * i + 31 - __clz(f));
-    if (~f) last0 = (int)(32 * i + 31 - __clz(~f));
+    const uint32_t hf = msb(f), hnf = msb(~f);
+    if (hf != 0xFFFFFFFFu) last1 = 32 * i + hf;
+    if (hnf != 0xFFFFFFFFu) last0 = 32 * i + hnf;
     base += __popc(inc);
   }
   if (CHECKED) bad = __any_sync(kFull, bad);
@@ -220,35 +248,6 @@ __device__ __forceinline__ bool small_coords(const Desc &d) {
   if (d.b > 24) return false;
   const uint32_t lim = (1u << 24) - (1u << d.b);  // L + 2^b - 1 < 2^24
   return d.L[0] <= lim && d.L[1] <= lim && d.L[2] <= lim;
-}
-
-// 32-bit shared-window accessors (explicit LDS/STS addressing).
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint32_t lds_u8(uint32_t a) {
-  uint32_t v;
-  asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint32_t lds_u16(uint32_t a) {
-  uint32_t v;
-  asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
-  uint32_t v;
-  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-  return v;
-}
-__device__ __forceinline__ void sts_u8(uint32_t a, uint32_t v) {
-  asm volatile("st.shared.u8 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
-// position of the highest set bit, 0xFFFFFFFF for 0
-__device__ __forceinline__ uint32_t msb(uint32_t x) {
-  uint32_t r;
-  asm("bfind.u32 %0, %1;" : "=r"(r) : "r"(x));
-  return r;
 }
 
 // Full decode of one staged meshlet into the batch outputs: the strip walk

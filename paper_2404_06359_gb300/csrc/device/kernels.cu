@@ -24,10 +24,6 @@ uint32_t decode_smem_per_warp(uint32_t max_block_words) { return warp_smem_bytes
 uint32_t batch_smem_per_warp(uint32_t max_block_words, uint32_t per_grab) {
   return 4 * grab_words(max_block_words, per_grab) + kStreamBytes;
 }
-uint32_t cull_smem_per_warp(uint32_t max_block_words) {
-  // + clip (x, y, w) per vertex + survivor triples
-  return warp_smem_bytes(max_block_words) + 3 * 4 * 256 + 3 * 4 * 256;
-}
 
 template <bool CHECKED>
 __device__ __forceinline__ void decode_one(const BatchArgs &a, uint32_t m, uint32_t *sw,
@@ -222,42 +218,59 @@ __device__ __forceinline__ float clip_row(const float *M, int r, float x, float 
 }
 
 // true when all 8 corners of the meshlet's quantisation box are outside one
-// clip plane
-__device__ __forceinline__ bool box_outside(const Desc &d, const Grid &g, const float *M) {
-  float lo[3], hi[3];
+// clip plane.  Lanes 0..7 each take one corner and collect the planes it is
+// outside of; the warp AND-reduces the plane masks.
+__device__ __forceinline__ bool box_outside(const Desc &d, const Grid &g, const float *M,
+                                            uint32_t lane) {
+  uint32_t mask = 0x3Fu;
+  if (lane < 8) {
+    float p[3];
 #pragma unroll
-  for (int c = 0; c < 3; c++) {
-    uint32_t top = d.L[c] + (d.b >= 32 ? 0xFFFFFFFFu : ((1u << d.b) - 1u));
-    lo[c] = dequant(d.L[c], g.G[c], g.D[c]);
-    hi[c] = dequant(top, g.G[c], g.D[c]);
-  }
-  bool any = false;
-#pragma unroll
-  for (int plane = 0; plane < 6; plane++) {
-    bool all_out = true;
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-      float x = (k & 1) ? hi[0] : lo[0];
-      float y = (k & 2) ? hi[1] : lo[1];
-      float z = (k & 4) ? hi[2] : lo[2];
-      float comp = clip_row(M, plane >> 1, x, y, z);
-      float w = clip_row(M, 3, x, y, z);
-      float dist = (plane & 1) ? __fsub_rn(w, comp) : __fadd_rn(w, comp);
-      all_out = all_out && (dist < 0.0f);
+    for (int c = 0; c < 3; c++) {
+      const uint32_t top = d.L[c] + (d.b >= 32 ? 0xFFFFFFFFu : ((1u << d.b) - 1u));
+      p[c] = dequant((lane >> c) & 1u ? top : d.L[c], g.G[c], g.D[c]);
     }
-    any = any || all_out;
+    const float w = clip_row(M, 3, p[0], p[1], p[2]);
+    mask = 0;
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+      const float comp = clip_row(M, r, p[0], p[1], p[2]);
+      if (__fadd_rn(w, comp) < 0.0f) mask |= 1u << (2 * r);
+      if (__fsub_rn(w, comp) < 0.0f) mask |= 2u << (2 * r);
+    }
   }
-  return any;
+  return __reduce_and_sync(kFull, mask) != 0;
 }
 
-// Decode + cull of one staged meshlet; survivors (global index triples) go
-// to surv[], positions to out_pos.  Returns the number of survivors, or
-// 0xFFFFFFFF for a corrupt stream.
+// Per-warp shared memory of the culling kernel (bytes, 16-byte aligned parts):
+// descriptors of a grab, its payload blocks + slack, the strip stream, clip
+// x / y / w per vertex, and the grab's surviving triangles.
+struct CullLayout {
+  uint32_t desc, pay, stream, clip, surv, bytes;
+};
+__host__ __device__ inline CullLayout cull_layout(uint32_t max_block_words, uint32_t max_tris,
+                                                  uint32_t per_grab) {
+  CullLayout l;
+  l.desc = 0;
+  l.pay = 32 * per_grab;
+  l.stream = l.pay + 4 * (per_grab * ((max_block_words + 3) & ~3u) + kSlackWords);
+  l.clip = l.stream + kStreamBytes;
+  l.surv = l.clip + 3 * 4 * 256;
+  l.bytes = l.surv + ((12 * per_grab * max_tris + 15) & ~15u);
+  return l;
+}
+uint32_t cull_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, uint32_t per_grab) {
+  return cull_layout(max_block_words, max_tris, per_grab).bytes;
+}
+
+// Decode + cull of one staged meshlet; survivors (global index triples)
+// are appended to surv[] from position n_keep.  Returns the new count, or
+// 0xFFFFFFFF for a corrupt stream (checked build).
 template <bool CHECKED, bool B16, bool W8>
 __device__ __forceinline__ uint32_t cull_staged(const Desc &d, const Grid &g, const float *M,
                                                 const uint32_t *sw, uint8_t *sI, float *cx,
                                                 float *cy, float *cw, uint32_t *surv,
-                                                uint32_t lane, float *out_pos) {
+                                                uint32_t n_keep, uint32_t lane, float *out_pos) {
   if (CHECKED && !stream_header_ok(d, sw)) return 0xFFFFFFFFu;
   const uint32_t nw = (d.T + 31) >> 5;
   const uint32_t *pw = sw + 2 * nw + ((d.T + 2 - d.V) * d.w + 31) / 32;
@@ -278,7 +291,6 @@ __device__ __forceinline__ uint32_t cull_staged(const Desc &d, const Grid &g, co
     cw[v] = clip_row(M, 3, p[0], p[1], p[2]);
   }
   __syncwarp();
-  uint32_t n_keep = 0;
   const uint32_t vb = d.vbase;
   const bool ok = walk_triangles<CHECKED, W8>(
       d, sw, sI, lane, [&](uint32_t k, uint32_t x, uint32_t y, uint32_t z, bool live) {
@@ -313,80 +325,101 @@ template <bool CHECKED>
 __device__ __forceinline__ uint32_t cull_dispatch(const Desc &d, const Grid &g, const float *M,
                                                   const uint32_t *sw, uint8_t *sI, float *cx,
                                                   float *cy, float *cw, uint32_t *surv,
-                                                  uint32_t lane, float *out_pos) {
+                                                  uint32_t n_keep, uint32_t lane, float *out_pos) {
   if (d.b == 16) {
-    if (d.w == 8) return cull_staged<CHECKED, true, true>(d, g, M, sw, sI, cx, cy, cw, surv, lane, out_pos);
-    return cull_staged<CHECKED, true, false>(d, g, M, sw, sI, cx, cy, cw, surv, lane, out_pos);
+    if (d.w == 8) return cull_staged<CHECKED, true, true>(d, g, M, sw, sI, cx, cy, cw, surv, n_keep, lane, out_pos);
+    return cull_staged<CHECKED, true, false>(d, g, M, sw, sI, cx, cy, cw, surv, n_keep, lane, out_pos);
   }
-  if (d.w == 8) return cull_staged<CHECKED, false, true>(d, g, M, sw, sI, cx, cy, cw, surv, lane, out_pos);
-  return cull_staged<CHECKED, false, false>(d, g, M, sw, sI, cx, cy, cw, surv, lane, out_pos);
+  if (d.w == 8) return cull_staged<CHECKED, false, true>(d, g, M, sw, sI, cx, cy, cw, surv, n_keep, lane, out_pos);
+  return cull_staged<CHECKED, false, false>(d, g, M, sw, sI, cx, cy, cw, surv, n_keep, lane, out_pos);
 }
 
-// Fused decode + cull + compaction.  A CTA takes one meshlet per warp per
-// round; survivors are compacted in the warp (ballot/popc) into shared
-// memory, the CTA reserves output space with one atomicAdd per round, and
-// each warp copies its survivors out.
+// Fused decode + cull + compaction.  Persistent warps take `per_grab`
+// consecutive meshlets (staged like the batched decoder), drop meshlets whose
+// box is outside the frustum before touching their triangles, decode and cull
+// the rest, collect the grab's survivors in shared memory and reserve their
+// output space with one atomicAdd per grab.
 template <bool CHECKED>
-__global__ void decode_cull_kernel(BatchArgs a, const float *view_proj, uint32_t smem_per_warp,
-                                   uint32_t *tri_out, uint32_t *tri_count, float *out_pos,
-                                   uint32_t *status, uint32_t *scratch) {
+__global__ void __launch_bounds__(512) decode_cull_kernel(BatchArgs a, const float *view_proj,
+                                                          uint32_t per_grab, uint32_t *tri_out,
+                                                          uint32_t *tri_count, float *out_pos,
+                                                          uint32_t *status, uint32_t *scratch) {
   extern __shared__ __align__(16) uint8_t smem[];
-  __shared__ uint32_t s_cnt[32];
-  __shared__ uint32_t s_base, s_out;
   __shared__ float s_M[16];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-  const uint32_t nwarps = blockDim.x >> 5;
-  uint8_t *base = smem + warp * smem_per_warp;
-  uint32_t *sw = reinterpret_cast<uint32_t *>(base);
-  const uint32_t ws = smem_per_warp - (3 * 4 * 256 + 3 * 4 * 256);  // decode part
-  uint8_t *sI = base + ws - kStreamBytes;
-  float *cx = reinterpret_cast<float *>(base + ws);
+  const CullLayout L = cull_layout(a.max_block_words, a.max_tris, per_grab);
+  uint8_t *base = smem + warp * L.bytes;
+  uint32_t *sdesc = reinterpret_cast<uint32_t *>(base + L.desc);
+  uint32_t *spay = reinterpret_cast<uint32_t *>(base + L.pay);
+  uint8_t *sI = base + L.stream;
+  float *cx = reinterpret_cast<float *>(base + L.clip);
   float *cy = cx + 256;
   float *cw = cy + 256;
-  uint32_t *surv = reinterpret_cast<uint32_t *>(cw + 256);
+  uint32_t *surv = reinterpret_cast<uint32_t *>(base + L.surv);
   if (threadIdx.x < 16) s_M[threadIdx.x] = view_proj[threadIdx.x];
   __syncthreads();
+  const uint32_t cap16 = (per_grab * ((a.max_block_words + 3) & ~3u)) / 4;
+  const uint32_t bytes16 = a.payload_bytes / 16 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)(a.payload_bytes / 16);
+  const uint4 *gdesc = reinterpret_cast<const uint4 *>(a.desc);
+  const uint4 *gpay = reinterpret_cast<const uint4 *>(a.payload);
   for (;;) {
-    if (threadIdx.x == 0) s_base = atomicAdd(scratch + kQueue, nwarps);
-    __syncthreads();
-    const uint32_t m = s_base + warp;
-    const bool round_live = s_base < a.n_meshlets;
+    uint32_t m0 = 0;
+    if (lane == 0) m0 = atomicAdd(scratch + kQueue, per_grab);
+    m0 = __shfl_sync(kFull, m0, 0);
+    if (m0 >= a.n_meshlets) break;
+    const uint32_t cnt = min(per_grab, a.n_meshlets - m0);
+    uint4 dv = make_uint4(0, 0, 0, 0);
+    if (lane < 2 * cnt) dv = __ldg(gdesc + 2ull * m0 + lane);
+    uint32_t end16 = bytes16;
+    if (m0 + cnt < a.n_meshlets) end16 = __ldg(&a.desc[m0 + cnt].payload_off16);
+    if (lane < 2 * cnt) reinterpret_cast<uint4 *>(sdesc)[lane] = dv;
+    const uint32_t start16 = __shfl_sync(kFull, dv.x, 0);
+    bool grab_staged = end16 >= start16 && end16 - start16 <= cap16 && end16 <= bytes16;
+    if (grab_staged) {
+      uint4 *dst = reinterpret_cast<uint4 *>(spay);
+      for (uint32_t i = lane; i < end16 - start16; i += 32) dst[i] = __ldg(gpay + start16 + i);
+    }
+    __syncwarp();
     uint32_t n_keep = 0;
-    if (round_live && m < a.n_meshlets) {
-      const Desc d = load_desc(a.desc + m);
+    for (uint32_t j = 0; j < cnt; j++) {
+      const uint4 *sd = reinterpret_cast<const uint4 *>(sdesc) + 2 * j;
+      const Desc d = unpack_desc(sd[0], sd[1]);
       if (!header_ok(d, a)) {
         if (lane == 0) set_status(status, MC_ERR_CORRUPT);
+        continue;
+      }
+      const Grid g = load_grid(a.grids + d.grid);
+      if (box_outside(d, g, s_M, lane)) continue;
+      const uint32_t padded16 = ((block_words(d) + 3) & ~3u) / 4;
+      const uint32_t *sw;
+      if (grab_staged && d.off16 >= start16 && d.off16 - start16 + padded16 <= end16 - start16) {
+        sw = spay + 4 * (d.off16 - start16);
       } else {
-        const Grid g = load_grid(a.grids + d.grid);
-        if (!box_outside(d, g, s_M)) {
-          stage_payload(d, a.payload, sw, lane);
-          __syncwarp();
-          n_keep = cull_dispatch<CHECKED>(d, g, s_M, sw, sI, cx, cy, cw, surv, lane, out_pos);
-          if (n_keep == 0xFFFFFFFFu) {
-            n_keep = 0;
-            if (lane == 0) set_status(status, MC_ERR_CORRUPT);
-          }
-        }
+        grab_staged = false;
+        __syncwarp();
+        stage_payload(d, a.payload, spay, lane);
+        __syncwarp();
+        sw = spay;
       }
-    }
-    if (lane == 0) s_cnt[warp] = n_keep;
-    __syncthreads();
-    if (!round_live) break;
-    if (threadIdx.x == 0) {
-      uint32_t tot = 0;
-      for (uint32_t w = 0; w < nwarps; w++) {
-        const uint32_t c = s_cnt[w];
-        s_cnt[w] = tot;
-        tot += c;
+      const uint32_t r = cull_dispatch<CHECKED>(d, g, s_M, sw, sI, cx, cy, cw, surv, n_keep, lane, out_pos);
+      if (r == 0xFFFFFFFFu) {
+        if (lane == 0) set_status(status, MC_ERR_CORRUPT);
+      } else {
+        n_keep = r;
       }
-      s_out = tot ? atomicAdd(scratch + kCount, tot) : 0;
+      __syncwarp();
     }
-    __syncthreads();
-    const uint32_t dst = s_out + s_cnt[warp];
-    for (uint32_t i = lane; i < 3 * n_keep; i += 32) tri_out[3ull * dst + i] = surv[i];
-    __syncthreads();
+    if (n_keep) {
+      uint32_t dst = 0;
+      if (lane == 0) dst = atomicAdd(scratch + kCount, n_keep);
+      dst = __shfl_sync(kFull, dst, 0);
+      uint32_t *o = tri_out + 3ull * dst;
+      for (uint32_t i = lane; i < 3 * n_keep; i += 32) o[i] = surv[i];
+    }
+    __syncwarp();
   }
   // the last CTA publishes the count and resets the scratch
+  __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     if (atomicAdd(scratch + kDone, 1u) == gridDim.x - 1) {
@@ -439,18 +472,16 @@ cudaError_t launch_batch(const BatchArgs &a, uint32_t ctas, uint32_t warps, uint
 }
 
 cudaError_t launch_cull(const BatchArgs &a, const float *view_proj, uint32_t ctas, uint32_t warps,
-                        uint32_t max_block_words, bool checked, uint32_t *tri_out,
-                        uint32_t *tri_count, float *out_pos, uint32_t *status, uint32_t *scratch,
-                        cudaStream_t s) {
-  const uint32_t spw = cull_smem_per_warp(max_block_words);
-  const uint32_t smem = spw * warps;
+                        uint32_t per_grab, bool checked, uint32_t *tri_out, uint32_t *tri_count,
+                        float *out_pos, uint32_t *status, uint32_t *scratch, cudaStream_t s) {
+  const uint32_t smem = cull_smem_per_warp(a.max_block_words, a.max_tris, per_grab) * warps;
   if (checked) {
     cudaFuncSetAttribute(decode_cull_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    decode_cull_kernel<true><<<ctas, warps * 32, smem, s>>>(a, view_proj, spw, tri_out, tri_count,
+    decode_cull_kernel<true><<<ctas, warps * 32, smem, s>>>(a, view_proj, per_grab, tri_out, tri_count,
                                                             out_pos, status, scratch);
   } else {
     cudaFuncSetAttribute(decode_cull_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    decode_cull_kernel<false><<<ctas, warps * 32, smem, s>>>(a, view_proj, spw, tri_out, tri_count,
+    decode_cull_kernel<false><<<ctas, warps * 32, smem, s>>>(a, view_proj, per_grab, tri_out, tri_count,
                                                              out_pos, status, scratch);
   }
   return cudaGetLastError();
@@ -492,14 +523,16 @@ int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words, uint32_t per
   return n;
 }
 
-int max_ctas_per_sm_cull(uint32_t warps, uint32_t max_block_words) {
+int max_ctas_per_sm_cull(uint32_t warps, uint32_t max_block_words, uint32_t max_tris,
+                         uint32_t per_grab) {
   int n = 0;
-  const int smem = (int)(cull_smem_per_warp(max_block_words) * warps);
+  const int smem = (int)(cull_smem_per_warp(max_block_words, max_tris, per_grab) * warps);
+  if (smem > 227 * 1024) return 0;
   cudaFuncSetAttribute(decode_cull_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(decode_cull_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_cull_kernel<false>, warps * 32,
-                                                cull_smem_per_warp(max_block_words) * warps);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_cull_kernel<false>, warps * 32, smem);
   return n;
 }
+
 
 }  // namespace mcdev

@@ -10,7 +10,7 @@
 namespace mcdev {
 
 uint32_t decode_smem_per_warp(uint32_t max_block_words);
-uint32_t cull_smem_per_warp(uint32_t max_block_words);
+uint32_t cull_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, uint32_t per_grab);
 uint32_t batch_smem_per_warp(uint32_t max_block_words, uint32_t per_grab);
 
 cudaError_t launch_plain(const BatchArgs &a, uint32_t first, uint32_t count, uint32_t warps,
@@ -23,12 +23,12 @@ cudaError_t launch_batch(const BatchArgs &a, uint32_t ctas, uint32_t warps, uint
                          uint32_t *scratch, cudaStream_t s);
 
 cudaError_t launch_cull(const BatchArgs &a, const float *view_proj, uint32_t ctas, uint32_t warps,
-                        uint32_t max_block_words, bool checked, uint32_t *tri_out,
-                        uint32_t *tri_count, float *out_pos, uint32_t *status, uint32_t *scratch,
-                        cudaStream_t s);
+                        uint32_t per_grab, bool checked, uint32_t *tri_out, uint32_t *tri_count,
+                        float *out_pos, uint32_t *status, uint32_t *scratch, cudaStream_t s);
 
 int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words, uint32_t per_grab);
-int max_ctas_per_sm_cull(uint32_t warps, uint32_t max_block_words);
+int max_ctas_per_sm_cull(uint32_t warps, uint32_t max_block_words, uint32_t max_tris,
+                         uint32_t per_grab);
 
 cudaError_t launch_requests(const BatchArgs &a, const mc_request *reqs, uint32_t n_reqs,
                             uint32_t total_work, uint32_t ctas, uint32_t warps, uint32_t per_grab,
