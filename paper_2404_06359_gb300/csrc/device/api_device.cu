@@ -218,12 +218,16 @@ mc_status launch_cull_checked(const mc_device_batch *b, const float *d_vp, uint3
   const uint32_t per_grab = (t && t->meshlets_per_grab) ? t->meshlets_per_grab : 4;
   if (warps < 1 || warps > 32 || per_grab < 1 || per_grab > 16) return MC_ERR_INVALID_ARG;
   const BatchArgs a = args_of(b);
-  int occ = max_ctas_per_sm_cull(warps, b->max_block_words, a.max_tris, per_grab);
+  // a grab's survivors are buffered in shared memory: shrink the grab until
+  // the requested number of warps fits on an SM
+  uint32_t grab = per_grab;
+  int occ = max_ctas_per_sm_cull(warps, b->max_block_words, a.max_tris, grab);
+  while (occ <= 0 && grab > 1) occ = max_ctas_per_sm_cull(warps, b->max_block_words, a.max_tris, --grab);
   if (occ <= 0) return MC_ERR_INVALID_ARG;
   uint32_t per_sm = (t && t->ctas_per_sm) ? std::min<uint32_t>(t->ctas_per_sm, occ) : (uint32_t)occ;
   uint32_t ctas = per_sm * (uint32_t)sm_count();
   if (ctas == 0) return MC_ERR_CUDA;
-  cudaError_t e = launch_cull(a, d_vp, ctas, warps, per_grab, t && t->checked, d_tri_out, d_tri_count,
+  cudaError_t e = launch_cull(a, d_vp, ctas, warps, grab, t && t->checked, d_tri_out, d_tri_count,
                               d_pos, d_status, static_cast<uint32_t *>(d_scratch), s);
   if (e == cudaSuccess) g_launches++;
   return from_cuda(e);

@@ -19,9 +19,15 @@ def block_words_max(desc: np.ndarray) -> int:
     return int(((words + 3) // 4 * 4).max()) if words.size else 4
 
 
+def max_tris(desc: np.ndarray) -> int:
+    w = desc.view(np.uint32).reshape(-1, 8)
+    return int((w[:, 3] >> 16).max()) if w.shape[0] else 1
+
+
 def device_batch_from_oracle(blob: O.Blob) -> mc.DeviceBatch:
     return mc.DeviceBatch.from_arrays(blob.desc, blob.payload, blob.grids, blob.total_tris,
-                                      blob.total_verts, block_words_max(blob.desc))
+                                      blob.total_verts, block_words_max(blob.desc),
+                                      max_tris(blob.desc))
 
 
 def run_decode(db: mc.DeviceBatch, mode="batch", tuning=None, local=True, global_=True):
