@@ -9,11 +9,12 @@
 //     the entry is s_k if the flag is set, else reuse[k + 1 - s_k]
 //     (unpacked from w bits with a funnel shift).  I[0..2] = 0,1,2.
 //   third vertex (Sec. 4.2): the last triangle j < k whose L/R flag differs
-//     from flag k, found by masking the flag word (inverted when flag k is
-//     set) below bit k and taking 31 - __clz; when a fan reaches back past
-//     the current 32-triangle word, j comes from running registers holding
-//     the last flag-0 / flag-1 positions of the earlier words;
-//     old = I[j + 1] (I[0] if none).
+//     from flag k; old = I[j + 1] (I[0] if none).  The flags equal to flag k
+//     form a run ending at k, which starts at the highest flag transition at
+//     or below k (transition bits D_p = F_p xor F_(p-1), D_0 = 1), so
+//     j + 1 = that position: one masked highest-bit scan of D in the current
+//     32-triangle word, or a running "last transition" register when a fan
+//     reaches back past the word.
 //   triangle (Sec. 4.2, orientation by the flag): R -> (I[k+1], old, I[k+2]),
 //     L -> (old, I[k+1], I[k+2]).
 //   position (Sec. 4.4): g = L_c + q (q = b bits at (3v+c) b), then
@@ -163,6 +164,27 @@ __device__ __forceinline__ uint32_t msb(uint32_t x) {
   return r;
 }
 
+// Predicated stores (no divergent branches in the strip passes).
+__device__ __forceinline__ void sts_u8_if(uint32_t a, uint32_t v, bool p) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q st.shared.u8 [%0], %1;\n}" ::"r"(a),
+               "r"(v), "r"((uint32_t)p)
+               : "memory");
+}
+__device__ __forceinline__ void stg3_u8_if(uint8_t *g, uint32_t x, uint32_t y, uint32_t z, bool p) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %4, 0;\n @q st.global.u8 [%0], %1;\n"
+      " @q st.global.u8 [%0+1], %2;\n @q st.global.u8 [%0+2], %3;\n}" ::"l"(g),
+      "r"(x), "r"(y), "r"(z), "r"((uint32_t)p)
+      : "memory");
+}
+__device__ __forceinline__ void stg3_u32_if(uint32_t *g, uint32_t x, uint32_t y, uint32_t z, bool p) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %4, 0;\n @q st.global.u32 [%0], %1;\n"
+      " @q st.global.u32 [%0+4], %2;\n @q st.global.u32 [%0+8], %3;\n}" ::"l"(g),
+      "r"(x), "r"(y), "r"(z), "r"((uint32_t)p)
+      : "memory");
+}
+
 // Stream-level consistency checks of the checked build: bit 0 of both flag
 // words clear, no flag bit past T', and V = 3 + (number of increment flags).
 __device__ __forceinline__ bool stream_header_ok(const Desc &d, const uint32_t *sw) {
@@ -176,12 +198,14 @@ __device__ __forceinline__ bool stream_header_ok(const Desc &d, const uint32_t *
 
 // Walks the meshlet's triangles 32 at a time, calling
 //   emit(k, a, b, c, live)
-// on every lane (live = k < T') with triangle k = (a, b, c) -- the same
-// arithmetic as decode_staged below: strip entries from the increment-word
-// add-scan (triangle 0 folded in as "new" with the scan seeded at 1) or the
-// reuse buffer, stored to sI; I[k+1] from the neighbouring lane; the third
-// vertex I[j+1] from the masked flag word's highest set bit or, for fans
-// reaching back past the word, from the running last-flag-0/1 positions.
+// on every lane (live = k < T') with triangle k = (a, b, c).  Per 32-triangle
+// word: strip entries from the increment-word add-scan (triangle 0 folded in
+// as "new" with the scan seeded at 1) or the reuse buffer, stored to sI;
+// I[k+1] from the neighbouring lane.  The third vertex I[j+1] uses the flag
+// transitions D_p = [F_p != F_(p-1)] (D_0 = 1): the run of equal flags that
+// ends at k starts at r = the highest set D bit at or below k, so the last
+// differing flag is j = r - 1 and old = I[r] -- one masked bit scan, or a
+// running "last transition" register when the run starts in an earlier word.
 // CHECKED: returns false (warp-uniform) if a reuse entry names a vertex not
 // yet seen.
 template <bool CHECKED, bool W8, class Emit>
@@ -192,8 +216,8 @@ __device__ __forceinline__ bool walk_triangles(const Desc &d, const uint32_t *sw
   const uint32_t a_rb = a_sw + 8 * nw;
   const uint32_t a_sI = smem_addr(sI);
   if (lane < 2) sts_u8(a_sI + lane, lane);
-  const uint32_t le = (2u << lane) - 1u, lt = (1u << lane) - 1u;
-  uint32_t base = 1, carry = 1, last0 = 0xFFFFFFFFu, last1 = 0xFFFFFFFFu;
+  const uint32_t le = (2u << lane) - 1u;
+  uint32_t base = 1, carry = 1, cf = 1, lastT = 0;
   bool bad = false;
   uint32_t k = lane;
   for (uint32_t i = 0; i < nw; i++, k += 32) {
@@ -206,20 +230,19 @@ __device__ __forceinline__ bool walk_triangles(const Desc &d, const uint32_t *sw
     const uint32_t n = is_new ? s : r;
     const bool live = k < d.T;
     if (CHECKED && live && !is_new && r > s) bad = true;
-    if (live) sts_u8(a_sI + k + 2, n);
+    sts_u8_if(a_sI + k + 2, n, live);
     uint32_t prev = __shfl_up_sync(kFull, n, 1);
     if (lane == 0) prev = carry;
     carry = __shfl_sync(kFull, n, 31);
+    const uint32_t D = f ^ ((f << 1) | cf);
+    cf = f >> 31;
     __syncwarp();
-    const uint32_t fk = (f >> lane) & 1u;
-    const uint32_t x = (f ^ (0u - fk)) & lt;
-    uint32_t j = msb(x);
-    j = (j == 0xFFFFFFFFu) ? (fk ? last0 : last1) : 32 * i + j;
-    const uint32_t old = lds_u8(a_sI + j + 1);
+    const uint32_t m = msb(D & le);
+    const uint32_t run = m == 0xFFFFFFFFu ? lastT : 32 * i + m;
+    const uint32_t old = lds_u8(a_sI + run);
+    const bool fk = (f >> lane) & 1u;
     emit(k, fk ? prev : old, fk ? old : prev, n, live);
-    const uint32_t hf = msb(f), hnf = msb(~f);
-    if (hf != 0xFFFFFFFFu) last1 = 32 * i + hf;
-    if (hnf != 0xFFFFFFFFu) last0 = 32 * i + hnf;
+    if (D) lastT = 32 * i + msb(D);
     base += __popc(inc);
   }
   if (CHECKED) bad = __any_sync(kFull, bad);
@@ -251,10 +274,9 @@ __device__ __forceinline__ bool small_coords(const Desc &d) {
 }
 
 // Full decode of one staged meshlet into the batch outputs: the strip walk
-// of walk_triangles (same arithmetic) written out flat, with the first
-// triangle folded into the scan (increment bit 0 forced on and the scan
-// seeded with 1, so triangle 0 gets entry s = 2 with no special case) and
-// per-lane output pointers advanced by one word of triangles per pass.
+// of walk_triangles (same arithmetic) written out flat, with predicated
+// stores and per-lane output pointers advanced by one word of triangles per
+// pass.
 template <bool CHECKED, bool B16, bool W8>
 __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, const uint32_t *sw,
                                               uint8_t *sI, uint32_t lane, uint8_t *out_local,
@@ -265,11 +287,12 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
   const uint32_t a_rb = a_sw + 8 * nw;  // reuse section (bytes)
   const uint32_t a_sI = smem_addr(sI);
   if (lane < 2) sts_u8(a_sI + lane, lane);  // I[0], I[1]; I[2] is triangle 0's entry
-  const uint32_t le = (2u << lane) - 1u, lt = (1u << lane) - 1u;
+  const uint32_t le = (2u << lane) - 1u;
   uint8_t *pl = out_local ? out_local + 3ull * (d.tbase + lane) : nullptr;
   uint32_t *pg = out_global ? out_global + 3ull * (d.tbase + lane) : nullptr;
+  const bool want_l = pl != nullptr, want_g = pg != nullptr;
   const uint32_t vb = d.vbase;
-  uint32_t base = 1, carry = 1, last0 = 0xFFFFFFFFu, last1 = 0xFFFFFFFFu;
+  uint32_t base = 1, carry = 1, cf = 1, lastT = 0;
   bool bad = false;
   uint32_t k = lane;
   for (uint32_t i = 0; i < nw; i++, k += 32) {
@@ -282,34 +305,23 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
     const uint32_t n = is_new ? s : r;
     const bool live = k < d.T;
     if (CHECKED && live && !is_new && r > s) bad = true;  // entries seen so far: 0..s
-    if (live) sts_u8(a_sI + k + 2, n);
+    sts_u8_if(a_sI + k + 2, n, live);
     uint32_t prev = __shfl_up_sync(kFull, n, 1);
     if (lane == 0) prev = carry;
     carry = __shfl_sync(kFull, n, 31);
+    const uint32_t D = f ^ ((f << 1) | cf);  // flag transitions (D_0 = 1)
+    cf = f >> 31;
     __syncwarp();
-    const uint32_t fk = (f >> lane) & 1u;
-    const uint32_t x = (f ^ (0u - fk)) & lt;
-    uint32_t j = msb(x);  // 0xFFFFFFFF when no differing flag in this word
-    j = (j == 0xFFFFFFFFu) ? (fk ? last0 : last1) : 32 * i + j;
-    const uint32_t old = lds_u8(a_sI + j + 1);  // j = 0xFFFFFFFF reads I[0]
+    const uint32_t m = msb(D & le);
+    const uint32_t run = m == 0xFFFFFFFFu ? lastT : 32 * i + m;  // start of k's flag run
+    const uint32_t old = lds_u8(a_sI + run);                    // I[j+1], j = run - 1
+    const bool fk = (f >> lane) & 1u;
     const uint32_t ta = fk ? prev : old, tb = fk ? old : prev;
-    if (live) {
-      if (pl) {
-        pl[0] = (uint8_t)ta;
-        pl[1] = (uint8_t)tb;
-        pl[2] = (uint8_t)n;
-      }
-      if (pg) {
-        pg[0] = vb + ta;
-        pg[1] = vb + tb;
-        pg[2] = vb + n;
-      }
-    }
-    if (pl) pl += 96;
-    if (pg) pg += 96;
-    const uint32_t hf = msb(f), hnf = msb(~f);
-    if (hf != 0xFFFFFFFFu) last1 = 32 * i + hf;
-    if (hnf != 0xFFFFFFFFu) last0 = 32 * i + hnf;
+    stg3_u8_if(pl, ta, tb, n, live && want_l);
+    stg3_u32_if(pg, vb + ta, vb + tb, vb + n, live && want_g);
+    pl += 96;
+    pg += 96;
+    if (D) lastT = 32 * i + msb(D);
     base += __popc(inc);
   }
   if (CHECKED && __any_sync(kFull, bad)) return false;
