@@ -96,13 +96,14 @@ struct BatchArgs {
 // Header sanity (all builds): a descriptor that passes cannot make the decode
 // read or write outside its buffers.
 __device__ __forceinline__ bool header_ok(const Desc &d, const BatchArgs &a) {
-  bool ok = d.V >= 3 && d.V <= 256 && d.T >= 1 && d.T <= 256 && d.V <= d.T + 2 && d.w >= 1 &&
-            d.w <= 8 && d.b >= 1 && d.b <= 32 && d.grid < a.n_grids;
-  if (!ok) return false;
+  // evaluated without short-circuit branches (all terms are cheap)
+  const bool shape = (d.V - 3u <= 253u) & (d.T - 1u <= 255u) & (d.V <= d.T + 2) &
+                     (d.w - 1u <= 7u) & (d.b - 1u <= 31u) & (d.grid < a.n_grids) &
+                     (d.T <= a.max_tris);
   const uint32_t padded = (block_words(d) + 3) & ~3u;
-  return padded <= a.max_block_words && d.T <= a.max_tris &&
-         16ull * d.off16 + 4ull * padded <= a.payload_bytes &&
-         (uint64_t)d.tbase + d.T <= a.total_tris && (uint64_t)d.vbase + d.V <= a.total_verts;
+  return shape & (padded <= a.max_block_words) &
+         (16ull * d.off16 + 4ull * padded <= a.payload_bytes) &
+         ((uint64_t)d.tbase + d.T <= a.total_tris) & ((uint64_t)d.vbase + d.V <= a.total_verts);
 }
 
 __device__ __forceinline__ uint32_t extract(const uint32_t *w, uint32_t bit, uint32_t nbits) {
@@ -268,9 +269,16 @@ __device__ __forceinline__ void vertex_q(const uint32_t *pw, uint32_t v, uint32_
 
 // true when every grid coordinate of the meshlet is below 2^24
 __device__ __forceinline__ bool small_coords(const Desc &d) {
-  if (d.b > 24) return false;
-  const uint32_t lim = (1u << 24) - (1u << d.b);  // L + 2^b - 1 < 2^24
-  return d.L[0] <= lim && d.L[1] <= lim && d.L[2] <= lim;
+  const uint32_t lim = (1u << 24) - (1u << min(d.b, 24u));  // L + 2^b - 1 < 2^24
+  return (d.b <= 24) & (d.L[0] <= lim) & (d.L[1] <= lim) & (d.L[2] <= lim);
+}
+
+__device__ __forceinline__ void stg3_f32_if(float *g, float x, float y, float z, bool p) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %4, 0;\n @q st.global.f32 [%0], %1;\n"
+      " @q st.global.f32 [%0+4], %2;\n @q st.global.f32 [%0+8], %3;\n}" ::"l"(g),
+      "f"(x), "f"(y), "f"(z), "r"((uint32_t)p)
+      : "memory");
 }
 
 // Full decode of one staged meshlet into the batch outputs: the strip walk
@@ -328,19 +336,23 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
   // positions
   const uint32_t *pw = sw + 2 * nw + ((d.T + 2 - d.V) * d.w + 31) / 32;
   float *op = out_pos + 3ull * (d.vbase + lane);
+  const uint32_t vpasses = (d.V + 31) >> 5;
   if (B16 && small_coords(d)) {
-    const uint32_t a_pw = smem_addr(pw) + 6 * lane;
-    for (uint32_t v = lane, a = a_pw; v < d.V; v += 32, a += 192, op += 96) {
-      op[0] = dequant_small(d.L[0] + lds_u16(a), g.G[0], g.D[0]);
-      op[1] = dequant_small(d.L[1] + lds_u16(a + 2), g.G[1], g.D[1]);
-      op[2] = dequant_small(d.L[2] + lds_u16(a + 4), g.G[2], g.D[2]);
+    uint32_t a = smem_addr(pw) + 6 * lane;
+    uint32_t v = lane;
+    for (uint32_t i = 0; i < vpasses; i++, v += 32, a += 192, op += 96) {
+      const float x = dequant_small(d.L[0] + lds_u16(a), g.G[0], g.D[0]);
+      const float y = dequant_small(d.L[1] + lds_u16(a + 2), g.G[1], g.D[1]);
+      const float z = dequant_small(d.L[2] + lds_u16(a + 4), g.G[2], g.D[2]);
+      stg3_f32_if(op, x, y, z, v < d.V);
     }
   } else {
-    for (uint32_t v = lane; v < d.V; v += 32, op += 96) {
+    uint32_t v = lane;
+    for (uint32_t i = 0; i < vpasses; i++, v += 32, op += 96) {
       uint32_t q[3];
-      vertex_q<B16>(pw, v, d.b, q);
-#pragma unroll
-      for (int c = 0; c < 3; c++) op[c] = dequant(d.L[c] + q[c], g.G[c], g.D[c]);
+      vertex_q<B16>(pw, min(v, d.V - 1), d.b, q);  // idle lanes re-read the last vertex
+      stg3_f32_if(op, dequant(d.L[0] + q[0], g.G[0], g.D[0]), dequant(d.L[1] + q[1], g.G[1], g.D[1]),
+                  dequant(d.L[2] + q[2], g.G[2], g.D[2]), v < d.V);
     }
   }
   __syncwarp();
