@@ -83,11 +83,6 @@ __device__ __forceinline__ uint32_t block_words(const Desc &d) {
   return 2 * nw + (R * d.w + 31) / 32 + (3 * d.V * d.b + 31) / 32;
 }
 
-// Word offset of the position section inside a meshlet's payload block.
-__device__ __forceinline__ uint32_t pos_words(const Desc &d) {
-  return 2 * ((d.T + 31) >> 5) + ((d.T + 2 - d.V) * d.w + 31) / 32;
-}
-
 struct BatchArgs {
   const mc_desc *desc;
   const uint8_t *payload;
@@ -293,8 +288,7 @@ __device__ __forceinline__ void stg3_f32_if(float *g, float x, float y, float z,
 template <bool CHECKED, bool B16, bool W8>
 __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, const uint32_t *sw,
                                               uint8_t *sI, uint32_t lane, uint8_t *out_local,
-                                              uint32_t *out_global, float *out_pos,
-                                              uint32_t pos_word, bool small) {
+                                              uint32_t *out_global, float *out_pos) {
   if (CHECKED && !stream_header_ok(d, sw)) return false;
   const uint32_t nw = (d.T + 31) >> 5;
   const uint32_t a_sw = smem_addr(sw);
@@ -340,10 +334,10 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
   }
   if (CHECKED && __any_sync(kFull, bad)) return false;
   // positions
-  const uint32_t *pw = sw + pos_word;
+  const uint32_t *pw = sw + 2 * nw + ((d.T + 2 - d.V) * d.w + 31) / 32;
   float *op = out_pos + 3ull * (d.vbase + lane);
   const uint32_t vpasses = (d.V + 31) >> 5;
-  if (B16 && small) {
+  if (B16 && small_coords(d)) {
     uint32_t a = smem_addr(pw) + 6 * lane;
     uint32_t v = lane;
     for (uint32_t i = 0; i < vpasses; i++, v += 32, a += 192, op += 96) {
@@ -368,16 +362,13 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
 template <bool CHECKED>
 __device__ __forceinline__ bool decode_dispatch(const Desc &d, const Grid &g, const uint32_t *sw,
                                                 uint8_t *sI, uint32_t lane, uint8_t *out_local,
-                                                uint32_t *out_global, float *out_pos,
-                                                uint32_t pos_word, bool small) {
+                                                uint32_t *out_global, float *out_pos) {
   if (d.b == 16) {
-    if (d.w == 8)
-      return decode_staged<CHECKED, true, true>(d, g, sw, sI, lane, out_local, out_global, out_pos, pos_word, small);
-    return decode_staged<CHECKED, true, false>(d, g, sw, sI, lane, out_local, out_global, out_pos, pos_word, small);
+    if (d.w == 8) return decode_staged<CHECKED, true, true>(d, g, sw, sI, lane, out_local, out_global, out_pos);
+    return decode_staged<CHECKED, true, false>(d, g, sw, sI, lane, out_local, out_global, out_pos);
   }
-  if (d.w == 8)
-    return decode_staged<CHECKED, false, true>(d, g, sw, sI, lane, out_local, out_global, out_pos, pos_word, small);
-  return decode_staged<CHECKED, false, false>(d, g, sw, sI, lane, out_local, out_global, out_pos, pos_word, small);
+  if (d.w == 8) return decode_staged<CHECKED, false, true>(d, g, sw, sI, lane, out_local, out_global, out_pos);
+  return decode_staged<CHECKED, false, false>(d, g, sw, sI, lane, out_local, out_global, out_pos);
 }
 
 }  // namespace mcdev

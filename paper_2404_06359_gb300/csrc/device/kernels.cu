@@ -38,9 +38,7 @@ __device__ __forceinline__ void decode_one(const BatchArgs &a, uint32_t m, uint3
   const Grid g = load_grid(a.grids + d.grid);
   stage_payload(d, a.payload, sw, lane);
   __syncwarp();
-  if (!decode_dispatch<CHECKED>(d, g, sw, sI, lane, out_local, out_global, out_pos, pos_words(d),
-                                small_coords(d)) &&
-      lane == 0)
+  if (!decode_dispatch<CHECKED>(d, g, sw, sI, lane, out_local, out_global, out_pos) && lane == 0)
     set_status(status, MC_ERR_CORRUPT);
   __syncwarp();
 }
@@ -102,39 +100,16 @@ __global__ void __launch_bounds__(512) decode_batch_kernel(BatchArgs a, uint32_t
       for (uint32_t i = lane; i < end16 - start16; i += 32) dst[i] = __ldg(gpay + start16 + i);
     }
     __syncwarp();
-    // lane j < cnt checks meshlet j's header, locates its block in the staged
-    // range and fetches its grid; the warp then shares the results by shuffle
-    uint32_t info = 0;
-    float gG0 = 0.f, gG1 = 0.f, gG2 = 0.f, gD0 = 0.f, gD1 = 0.f, gD2 = 0.f;
-    if (lane < cnt) {
-      const uint4 *sd = reinterpret_cast<const uint4 *>(sdesc) + 2 * lane;
-      const Desc dj = unpack_desc(sd[0], sd[1]);
-      if (header_ok(dj, a)) {
-        const uint32_t padded16 = ((block_words(dj) + 3) & ~3u) / 4;
-        const bool inr = grab_staged && dj.off16 >= start16 && dj.off16 - start16 + padded16 <= end16 - start16;
-        info = 1u | (inr ? 2u : 0u) | (small_coords(dj) ? 4u : 0u) | (pos_words(dj) << 8);
-        const Grid gj = load_grid(a.grids + dj.grid);
-        gG0 = gj.G[0]; gG1 = gj.G[1]; gG2 = gj.G[2];
-        gD0 = gj.D[0]; gD1 = gj.D[1]; gD2 = gj.D[2];
-      }
-    }
     for (uint32_t j = 0; j < cnt; j++) {
-      const uint32_t inf = __shfl_sync(kFull, info, j);
-      Grid g;
-      g.G[0] = __shfl_sync(kFull, gG0, j);
-      g.G[1] = __shfl_sync(kFull, gG1, j);
-      g.G[2] = __shfl_sync(kFull, gG2, j);
-      g.D[0] = __shfl_sync(kFull, gD0, j);
-      g.D[1] = __shfl_sync(kFull, gD1, j);
-      g.D[2] = __shfl_sync(kFull, gD2, j);
-      if (!(inf & 1u)) {
+      const uint4 *sd = reinterpret_cast<const uint4 *>(sdesc) + 2 * j;
+      const Desc d = unpack_desc(sd[0], sd[1]);
+      if (!header_ok(d, a)) {
         if (lane == 0) set_status(status, MC_ERR_CORRUPT);
         continue;
       }
-      const uint4 *sd = reinterpret_cast<const uint4 *>(sdesc) + 2 * j;
-      const Desc d = unpack_desc(sd[0], sd[1]);
+      const uint32_t padded16 = ((block_words(d) + 3) & ~3u) / 4;
       const uint32_t *sw;
-      if (grab_staged && (inf & 2u)) {
+      if (grab_staged && d.off16 >= start16 && d.off16 - start16 + padded16 <= end16 - start16) {
         sw = spay + 4 * (d.off16 - start16);
       } else {
         grab_staged = false;  // spay is reused meshlet by meshlet from here on
@@ -143,9 +118,8 @@ __global__ void __launch_bounds__(512) decode_batch_kernel(BatchArgs a, uint32_t
         __syncwarp();
         sw = spay;
       }
-      if (!decode_dispatch<CHECKED>(d, g, sw, sI, lane, out_local, out_global, out_pos, inf >> 8,
-                                    (inf & 4u) != 0) &&
-          lane == 0)
+      const Grid g = load_grid(a.grids + d.grid);
+      if (!decode_dispatch<CHECKED>(d, g, sw, sI, lane, out_local, out_global, out_pos) && lane == 0)
         set_status(status, MC_ERR_CORRUPT);
     }
     __syncwarp();
@@ -223,8 +197,7 @@ __global__ void __launch_bounds__(512) decode_requests_kernel(BatchArgs a, const
       const Grid g = load_grid(a.grids + d.grid);
       stage_payload(d, a.payload, sw, lane);
       __syncwarp();
-      if (!decode_dispatch<CHECKED>(d, g, sw, sI, lane, ol, og, op, pos_words(d), small_coords(d)) &&
-          lane == 0)
+      if (!decode_dispatch<CHECKED>(d, g, sw, sI, lane, ol, og, op) && lane == 0)
         set_status(status, MC_ERR_CORRUPT);
       __syncwarp();
     }
