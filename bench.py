@@ -55,7 +55,7 @@ def _peaks():
 # DRAM bytes (read + write) of one decode_batch launch from an ncu capture
 # (profiles/decode_batch_cfg2.md), per decoded triangle slot and keyed by the
 # kernel-source hash it was taken on; reported only while the sources match.
-NCU_TRAFFIC = {"3d9d30eda6b818df": {2: 429.408e6 / 18015946}}
+NCU_TRAFFIC = {"45e7b1e39d5aae9a": {2: 428.999e6 / 18015946, 4: 898.136e6 / 55596770}}
 
 
 def _kernel_hash():
@@ -429,7 +429,7 @@ def main():
         tr = NCU_TRAFFIC.get(_kernel_hash())
         traffic = None
         if tr and args.config in tr:
-            traffic = int(tr[args.config] * stats["total_tris"])
+            traffic = int(tr[args.config] * stats["total_tris"])  # per launch (one view for cfg4)
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS hbm_gbs)",
