@@ -62,7 +62,8 @@ def _kernel_hash():
     import hashlib
     h = hashlib.sha256()
     for p in ("paper_2404_06359_gb300/csrc/device/kernels.cu",
-              "paper_2404_06359_gb300/csrc/device/decode_warp.cuh"):
+              "paper_2404_06359_gb300/csrc/device/decode_warp.cuh",
+              "paper_2404_06359_gb300/csrc/device/grab_loop.cuh"):
         with open(os.path.join(ROOT, p), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -315,10 +316,13 @@ def main():
             tri = torch.empty(3 * T + 3, dtype=torch.int32, device="cuda")
             d_vps = torch.from_numpy(np.ascontiguousarray(vps, np.float32)).cuda()
             counts = torch.zeros(len(vps), dtype=torch.int32, device="cuda")
-            graph = mc.mc_graph_capture_cull(db, d_vps, len(vps), tri, counts, out["pos"],
-                                             out["status"], scratch, None, stream)
-            launches_per_step = len(vps)
             tune = None
+            if args.tuning:
+                w_, c_, g_ = (int(x) for x in args.tuning.split(","))
+                tune = mc.mc_tuning(w_, c_, g_, 0)
+            graph = mc.mc_graph_capture_cull(db, d_vps, len(vps), tri, counts, out["pos"],
+                                             out["status"], scratch, tune, stream)
+            launches_per_step = len(vps)
         elif args.config == 1:
             graph = None
             launches_per_step = 1

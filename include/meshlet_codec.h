@@ -199,7 +199,10 @@ typedef struct {
 typedef struct {
   uint32_t warps_per_cta;     /* 1..32 */
   uint32_t ctas_per_sm;       /* persistent CTAs per SM */
-  uint32_t meshlets_per_grab; /* work-queue granularity (persistent kernels) */
+  uint32_t meshlets_per_grab; /* work-queue granularity (persistent kernels,
+                               * 1..16); a grab whose shared-memory buffers
+                               * do not fit warps_per_cta warps on an SM is
+                               * reduced until they do */
   uint32_t checked;
 } mc_tuning;
 

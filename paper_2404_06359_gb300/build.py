@@ -20,7 +20,7 @@ LIB = os.path.join(PKG, "libmeshletcodec.so")
 
 HOST_SOURCES = ["host/meshletize.cpp", "host/strip.cpp", "host/encode.cpp"]
 DEVICE_SOURCES = ["device/kernels.cu", "device/api_device.cu"]
-HEADERS = ["host/host_internal.h", "device/decode_warp.cuh", "device/kernels.h"]
+HEADERS = ["host/host_internal.h", "device/decode_warp.cuh", "device/grab_loop.cuh", "device/kernels.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -104,12 +104,16 @@ mc_status launch_batch_checked(const mc_device_batch *b, uint8_t *d_local, uint3
   if (r.warps_per_cta < 1 || r.warps_per_cta > 32 || r.meshlets_per_grab < 1 ||
       r.meshlets_per_grab > 16)
     return MC_ERR_INVALID_ARG;
-  int occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, r.meshlets_per_grab);
+  // a grab's two pipeline buffers live in shared memory: shrink the grab
+  // until the requested number of warps fits on an SM
+  uint32_t grab = r.meshlets_per_grab;
+  int occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, grab);
+  while (occ <= 0 && grab > 1) occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, --grab);
   if (occ <= 0) return MC_ERR_INVALID_ARG;
   uint32_t per_sm = std::min<uint32_t>(r.ctas_per_sm, (uint32_t)occ);
   uint32_t ctas = per_sm * (uint32_t)sm_count();
   if (ctas == 0) return MC_ERR_CUDA;
-  cudaError_t e = launch_batch(args_of(b), ctas, r.warps_per_cta, r.meshlets_per_grab,
+  cudaError_t e = launch_batch(args_of(b), ctas, r.warps_per_cta, grab,
                                b->max_block_words, r.checked != 0, d_local, d_global, d_pos,
                                d_status, static_cast<uint32_t *>(d_scratch), s);
   if (e == cudaSuccess) g_launches++;

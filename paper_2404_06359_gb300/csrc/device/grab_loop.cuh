@@ -1,0 +1,149 @@
+// Per-warp work loop of the persistent kernels.
+//
+// A warp takes `per_grab` consecutive meshlets at a time from a device work
+// queue (one atomicAdd per grab).  Consecutive meshlets have consecutive
+// payload blocks, so a grab is staged in shared memory by two bulk copies
+// (`cp.async.bulk` global -> shared, issued by lane 0 and completed on an
+// mbarrier): first its descriptors plus the next meshlet's (whose payload
+// offset ends the range), then its whole payload range.  The meshlets are
+// then handed one by one to the kernel's body.  A grab whose range does not
+// look contiguous falls back to staging meshlet by meshlet.
+//
+// Every mbarrier wait is bounded (about a second): a wait that gives up sets
+// MC_ERR_TIMEOUT in the status word and ends the warp's work; the copy it
+// waited for is the only one the warp has in flight.
+#pragma once
+
+#include "decode_warp.cuh"
+
+namespace mcdev {
+
+constexpr long long kWaitCycles = 1ll << 31;  // about one second at 2 GHz
+
+// mbarrier / bulk-copy / proxy-fence primitives (32-bit shared addresses).
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits (all lanes) for the phase with the given parity; false on every lane
+// if any lane gave up after about kWaitCycles clock cycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  bool ok = mbar_try_wait(bar, parity);
+  if (!ok) {
+    const long long t0 = clock64();
+    while (!(ok = mbar_try_wait(bar, parity)) && clock64() - t0 <= kWaitCycles) {
+    }
+  }
+  return __all_sync(kFull, ok);
+}
+
+// Shared-memory layout of the loop (bytes, per warp): the grab's descriptors
+// and the next one, the mbarrier (16 bytes), then the payload blocks of a
+// grab and the over-read slack.
+__host__ __device__ inline uint32_t grab_loop_bytes(uint32_t max_block_words, uint32_t per_grab) {
+  return 32 * (per_grab + 1) + 16 + 4 * (per_grab * ((max_block_words + 3) & ~3u) + kSlackWords);
+}
+
+// Runs the warp's share of the work queue.  body(d, sw) is called by all
+// lanes for every meshlet whose header passes header_ok, with sw its payload
+// block in shared memory; a failed header sets MC_ERR_CORRUPT.
+template <class Body>
+__device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab, uint8_t *wbase,
+                                          uint32_t lane, uint32_t *queue, uint32_t *status,
+                                          Body &&body) {
+  const uint32_t *sdesc = reinterpret_cast<const uint32_t *>(wbase);
+  const uint32_t bar = smem_addr(wbase + 32 * (per_grab + 1));
+  uint32_t *spay = reinterpret_cast<uint32_t *>(wbase + 32 * (per_grab + 1) + 16);
+  const uint32_t cap16 = (per_grab * ((a.max_block_words + 3) & ~3u)) / 4;
+  const uint32_t bytes16 =
+      a.payload_bytes / 16 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)(a.payload_bytes / 16);
+  const uint32_t N = a.n_meshlets;
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  uint32_t parity = 0;
+  for (;;) {
+    uint32_t m0 = 0;
+    if (lane == 0) m0 = atomicAdd(queue, per_grab);
+    m0 = __shfl_sync(kFull, m0, 0);
+    if (m0 >= N) break;
+    const uint32_t cnt = min(per_grab, N - m0);
+    const uint32_t nd = cnt + (m0 + cnt < N ? 1u : 0u);
+    fence_proxy_async();  // the previous grab's shared-memory accesses before the async writes
+    __syncwarp();
+    if (lane == 0) {
+      mbar_expect_tx(bar, 32 * nd);
+      bulk_g2s(smem_addr(wbase), a.desc + m0, 32 * nd, bar);
+    }
+    if (!mbar_wait(bar, parity)) {
+      if (lane == 0) set_status(status, MC_ERR_TIMEOUT);
+      return;
+    }
+    parity ^= 1u;
+    const uint32_t start16 = sdesc[0];
+    const uint32_t end16 = m0 + cnt < N ? sdesc[8 * cnt] : bytes16;
+    bool staged = end16 >= start16 && end16 - start16 <= cap16 && end16 <= bytes16;
+    if (staged && end16 > start16) {
+      if (lane == 0) {
+        mbar_expect_tx(bar, 16 * (end16 - start16));
+        bulk_g2s(smem_addr(spay), a.payload + 16ull * start16, 16 * (end16 - start16), bar);
+      }
+      if (!mbar_wait(bar, parity)) {
+        if (lane == 0) set_status(status, MC_ERR_TIMEOUT);
+        return;
+      }
+      parity ^= 1u;
+    }
+    for (uint32_t j = 0; j < cnt; j++) {
+      const uint4 *sd = reinterpret_cast<const uint4 *>(sdesc) + 2 * j;
+      const Desc d = unpack_desc(sd[0], sd[1]);
+      if (!header_ok(d, a)) {
+        if (lane == 0) set_status(status, MC_ERR_CORRUPT);
+        continue;
+      }
+      const uint32_t padded16 = ((block_words(d) + 3) & ~3u) / 4;
+      const uint32_t *sw;
+      if (staged && d.off16 >= start16 && d.off16 - start16 + padded16 <= end16 - start16) {
+        sw = spay + 4 * (d.off16 - start16);
+      } else {
+        staged = false;  // spay is reused meshlet by meshlet from here on
+        __syncwarp();
+        stage_payload(d, a.payload, spay, lane);
+        __syncwarp();
+        sw = spay;
+      }
+      body(d, sw);
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace mcdev

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "decode_warp.cuh"
+#include "grab_loop.cuh"
 #include "kernels.h"
 
 namespace mcdev {
@@ -16,13 +17,10 @@ __host__ __device__ inline uint32_t warp_words(uint32_t max_block_words) {
 __host__ __device__ inline uint32_t warp_smem_bytes(uint32_t max_block_words) {
   return 4 * warp_words(max_block_words) + kStreamBytes;
 }
-// Batched kernel: descriptors of one grab, the grab's payload blocks, stream.
-__host__ __device__ inline uint32_t grab_words(uint32_t max_block_words, uint32_t per_grab) {
-  return 8 * per_grab + per_grab * ((max_block_words + 3) & ~3u) + kSlackWords;
-}
 uint32_t decode_smem_per_warp(uint32_t max_block_words) { return warp_smem_bytes(max_block_words); }
+// Batched kernel: the grab loop's buffers, then the strip stream.
 uint32_t batch_smem_per_warp(uint32_t max_block_words, uint32_t per_grab) {
-  return 4 * grab_words(max_block_words, per_grab) + kStreamBytes;
+  return grab_loop_bytes(max_block_words, per_grab) + kStreamBytes;
 }
 
 template <bool CHECKED>
@@ -60,13 +58,8 @@ __global__ void decode_plain_kernel(BatchArgs a, uint32_t first, uint32_t count,
 // Scratch words used by the persistent kernels.
 enum { kQueue = 0, kDone = 1, kCount = 2 };
 
-// Persistent batched decode.  Each warp takes `per_grab` (<= 16) consecutive
-// meshlets from the work queue; because consecutive meshlets have
-// consecutive payload blocks, the warp loads all their descriptors and the
-// whole payload range in one pass of 16-byte loads (one memory latency per
-// grab), then decodes them one after another from shared memory.  A grab
-// whose range does not look contiguous falls back to staging meshlet by
-// meshlet.
+// Persistent batched decode: each warp runs the grab loop and decodes the
+// staged meshlets one after another from shared memory.
 template <bool CHECKED>
 __global__ void __launch_bounds__(512) decode_batch_kernel(BatchArgs a, uint32_t per_grab,
                                                            uint32_t smem_per_warp, uint8_t *out_local,
@@ -75,55 +68,14 @@ __global__ void __launch_bounds__(512) decode_batch_kernel(BatchArgs a, uint32_t
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   uint8_t *base = smem + warp * smem_per_warp;
-  uint32_t *sdesc = reinterpret_cast<uint32_t *>(base);
-  uint32_t *spay = sdesc + 8 * per_grab;
   uint8_t *sI = base + smem_per_warp - kStreamBytes;
-  const uint32_t cap16 = (per_grab * ((a.max_block_words + 3) & ~3u)) / 4;
-  const uint32_t bytes16 = a.payload_bytes / 16 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)(a.payload_bytes / 16);
-  const uint4 *gdesc = reinterpret_cast<const uint4 *>(a.desc);
-  const uint4 *gpay = reinterpret_cast<const uint4 *>(a.payload);
-  for (;;) {
-    uint32_t m0 = 0;
-    if (lane == 0) m0 = atomicAdd(scratch + kQueue, per_grab);
-    m0 = __shfl_sync(kFull, m0, 0);
-    if (m0 >= a.n_meshlets) break;
-    const uint32_t cnt = min(per_grab, a.n_meshlets - m0);
-    uint4 dv = make_uint4(0, 0, 0, 0);
-    if (lane < 2 * cnt) dv = __ldg(gdesc + 2ull * m0 + lane);
-    uint32_t end16 = bytes16;
-    if (m0 + cnt < a.n_meshlets) end16 = __ldg(&a.desc[m0 + cnt].payload_off16);
-    if (lane < 2 * cnt) reinterpret_cast<uint4 *>(sdesc)[lane] = dv;
-    const uint32_t start16 = __shfl_sync(kFull, dv.x, 0);
-    bool grab_staged = end16 >= start16 && end16 - start16 <= cap16 && end16 <= bytes16;
-    if (grab_staged) {
-      uint4 *dst = reinterpret_cast<uint4 *>(spay);
-      for (uint32_t i = lane; i < end16 - start16; i += 32) dst[i] = __ldg(gpay + start16 + i);
-    }
-    __syncwarp();
-    for (uint32_t j = 0; j < cnt; j++) {
-      const uint4 *sd = reinterpret_cast<const uint4 *>(sdesc) + 2 * j;
-      const Desc d = unpack_desc(sd[0], sd[1]);
-      if (!header_ok(d, a)) {
-        if (lane == 0) set_status(status, MC_ERR_CORRUPT);
-        continue;
-      }
-      const uint32_t padded16 = ((block_words(d) + 3) & ~3u) / 4;
-      const uint32_t *sw;
-      if (grab_staged && d.off16 >= start16 && d.off16 - start16 + padded16 <= end16 - start16) {
-        sw = spay + 4 * (d.off16 - start16);
-      } else {
-        grab_staged = false;  // spay is reused meshlet by meshlet from here on
-        __syncwarp();
-        stage_payload(d, a.payload, spay, lane);
-        __syncwarp();
-        sw = spay;
-      }
-      const Grid g = load_grid(a.grids + d.grid);
-      if (!decode_dispatch<CHECKED>(d, g, sw, sI, lane, out_local, out_global, out_pos) && lane == 0)
-        set_status(status, MC_ERR_CORRUPT);
-    }
-    __syncwarp();
-  }
+  grab_loop(a, per_grab, base, lane, scratch + kQueue, status,
+            [&](const Desc &d, const uint32_t *sw) {
+              const Grid g = load_grid(a.grids + d.grid);
+              if (!decode_dispatch<CHECKED>(d, g, sw, sI, lane, out_local, out_global, out_pos) &&
+                  lane == 0)
+                set_status(status, MC_ERR_CORRUPT);
+            });
   // the last CTA to finish leaves the queue reset for the next launch
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -242,80 +194,84 @@ __device__ __forceinline__ bool box_outside(const Desc &d, const Grid &g, const 
   return __reduce_and_sync(kFull, mask) != 0;
 }
 
-// Per-warp shared memory of the culling kernel (bytes, 16-byte aligned parts):
-// descriptors of a grab, its payload blocks + slack, the strip stream, clip
-// x / y / w per vertex, and the grab's surviving triangles.
+constexpr uint32_t kSurvSources = 32;  // meshlets one survivor buffer may reference
+constexpr uint32_t kSurvMeshlets = 6;  // survivor buffer capacity, in largest meshlets
+
 struct CullLayout {
-  uint32_t desc, pay, stream, clip, surv, bytes;
+  uint32_t stream, clip, n_clip, svb, surv, cap, bytes;
 };
+// Per-warp shared memory of the fused cull: the grab loop's buffers, the
+// strip entries, clip-space x, y, w of the meshlet's vertices
+// (V <= T' + 2 <= max_tris + 2 entries), the vertex bases of the meshlets
+// the survivor buffer references, and the survivor buffer (cap triangles,
+// one word each: three local indices and the source slot).
 __host__ __device__ inline CullLayout cull_layout(uint32_t max_block_words, uint32_t max_tris,
                                                   uint32_t per_grab) {
   CullLayout l;
-  l.desc = 0;
-  l.pay = 32 * per_grab;
-  l.stream = l.pay + 4 * (per_grab * ((max_block_words + 3) & ~3u) + kSlackWords);
+  l.stream = grab_loop_bytes(max_block_words, per_grab);
   l.clip = l.stream + kStreamBytes;
-  l.surv = l.clip + 3 * 4 * 256;
-  l.bytes = l.surv + ((12 * per_grab * max_tris + 15) & ~15u);
+  l.n_clip = ((max_tris + 2 < 256 ? max_tris + 2 : 256) + 7) & ~7u;
+  l.svb = l.clip + 12 * l.n_clip;
+  l.surv = l.svb + 4 * kSurvSources;
+  l.cap = kSurvMeshlets * max_tris;
+  l.bytes = l.surv + ((4 * l.cap + 15) & ~15u);
   return l;
 }
 uint32_t cull_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, uint32_t per_grab) {
   return cull_layout(max_block_words, max_tris, per_grab).bytes;
 }
 
-// Decode + cull of one staged meshlet; survivors (global index triples)
-// are appended to surv[] from position n_keep.  Returns the new count, or
-// 0xFFFFFFFF for a corrupt stream (checked build).
+__device__ __forceinline__ void sts_u32_if(uint32_t a, uint32_t x, bool p) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q st.shared.u32 [%0], %1;\n}" ::"r"(a),
+               "r"(x), "r"((uint32_t)p)
+               : "memory");
+}
+
+// Decode + cull of one staged meshlet; survivors are appended to surv[] from
+// position n_keep as x | y << 8 | z << 16 | tag (tag = source slot << 24).
+// Returns the new count, or 0xFFFFFFFF for a corrupt stream (checked build).
+// Clip x, y of vertex v sit in cxy[v] (float2), clip w in cw[v].
 template <bool CHECKED, bool B16, bool W8>
 __device__ __forceinline__ uint32_t cull_staged(const Desc &d, const Grid &g, const float *M,
-                                                const uint32_t *sw, uint8_t *sI, float *cx,
-                                                float *cy, float *cw, uint32_t *surv,
-                                                uint32_t n_keep, uint32_t lane, float *out_pos) {
+                                                const uint32_t *sw, uint8_t *sI, float2 *cxy,
+                                                float *cw, uint32_t *surv, uint32_t n_keep,
+                                                uint32_t tag, uint32_t lane, float *out_pos) {
   if (CHECKED && !stream_header_ok(d, sw)) return 0xFFFFFFFFu;
   const uint32_t nw = (d.T + 31) >> 5;
   const uint32_t *pw = sw + 2 * nw + ((d.T + 2 - d.V) * d.w + 31) / 32;
   const bool small = small_coords(d);
-  float *op = out_pos + 3ull * d.vbase;
-  for (uint32_t v = lane; v < d.V; v += 32) {
+  float *op = out_pos + 3ull * (d.vbase + lane);
+  const uint32_t vpasses = (d.V + 31) >> 5;
+  uint32_t v = lane;
+  for (uint32_t i = 0; i < vpasses; i++, v += 32, op += 96) {
+    const uint32_t vv = min(v, d.V - 1);  // idle lanes recompute the last vertex
     uint32_t q[3];
-    vertex_q<B16>(pw, v, d.b, q);
+    vertex_q<B16>(pw, vv, d.b, q);
     float p[3];
 #pragma unroll
     for (int c = 0; c < 3; c++)
       p[c] = small ? dequant_small(d.L[c] + q[c], g.G[c], g.D[c]) : dequant(d.L[c] + q[c], g.G[c], g.D[c]);
-    op[3 * v] = p[0];
-    op[3 * v + 1] = p[1];
-    op[3 * v + 2] = p[2];
-    cx[v] = clip_row(M, 0, p[0], p[1], p[2]);
-    cy[v] = clip_row(M, 1, p[0], p[1], p[2]);
-    cw[v] = clip_row(M, 3, p[0], p[1], p[2]);
+    stg3_f32_if(op, p[0], p[1], p[2], v < d.V);
+    cxy[vv] = make_float2(clip_row(M, 0, p[0], p[1], p[2]), clip_row(M, 1, p[0], p[1], p[2]));
+    cw[vv] = clip_row(M, 3, p[0], p[1], p[2]);
   }
   __syncwarp();
-  const uint32_t vb = d.vbase;
+  const uint32_t a_surv = smem_addr(surv);
   const bool ok = walk_triangles<CHECKED, W8>(
       d, sw, sI, lane, [&](uint32_t k, uint32_t x, uint32_t y, uint32_t z, bool live) {
-        bool keep = false;
-        if (live && x != y && y != z && x != z) {
-          const float w0 = cw[x], w1 = cw[y], w2 = cw[z];
-          if (w0 <= 0.0f || w1 <= 0.0f || w2 <= 0.0f) {
-            keep = true;
-          } else {
-            const float x0 = cx[x], y0 = cy[x], x1 = cx[y], y1 = cy[y];
-            const float x2 = cx[z], y2 = cy[z];
-            const float c0 = __fmaf_rn(y1, w2, -__fmul_rn(w1, y2));
-            const float c1 = __fmaf_rn(x1, w2, -__fmul_rn(w1, x2));
-            const float c2 = __fmaf_rn(x1, y2, -__fmul_rn(y1, x2));
-            const float det = __fmaf_rn(w0, c2, __fmaf_rn(-y0, c1, __fmul_rn(x0, c0)));
-            keep = det > 0.0f;
-          }
-        }
+        // evaluated on every lane without branches; dead lanes read vertex 0
+        const uint32_t xi = live ? x : 0u, yi = live ? y : 0u, zi = live ? z : 0u;
+        const float2 p0 = cxy[xi], p1 = cxy[yi], p2 = cxy[zi];
+        const float w0 = cw[xi], w1 = cw[yi], w2 = cw[zi];
+        const float c0 = __fmaf_rn(p1.y, w2, -__fmul_rn(w1, p2.y));
+        const float c1 = __fmaf_rn(p1.x, w2, -__fmul_rn(w1, p2.x));
+        const float c2 = __fmaf_rn(p1.x, p2.y, -__fmul_rn(p1.y, p2.x));
+        const float det = __fmaf_rn(w0, c2, __fmaf_rn(-p0.y, c1, __fmul_rn(p0.x, c0)));
+        const bool behind = (w0 <= 0.0f) | (w1 <= 0.0f) | (w2 <= 0.0f);
+        const bool keep = live & (x != y) & (y != z) & (x != z) & (behind | (det > 0.0f));
         const uint32_t bal = __ballot_sync(kFull, keep);
-        if (keep) {
-          const uint32_t o = n_keep + __popc(bal & ((1u << lane) - 1u));
-          surv[3 * o] = vb + x;
-          surv[3 * o + 1] = vb + y;
-          surv[3 * o + 2] = vb + z;
-        }
+        const uint32_t o = n_keep + __popc(bal & ((1u << lane) - 1u));
+        sts_u32_if(a_surv + 4 * o, x | (y << 8) | (z << 16) | tag, keep);
         n_keep += __popc(bal);
       });
   return ok ? n_keep : 0xFFFFFFFFu;
@@ -323,24 +279,41 @@ __device__ __forceinline__ uint32_t cull_staged(const Desc &d, const Grid &g, co
 
 template <bool CHECKED>
 __device__ __forceinline__ uint32_t cull_dispatch(const Desc &d, const Grid &g, const float *M,
-                                                  const uint32_t *sw, uint8_t *sI, float *cx,
-                                                  float *cy, float *cw, uint32_t *surv,
-                                                  uint32_t n_keep, uint32_t lane, float *out_pos) {
+                                                  const uint32_t *sw, uint8_t *sI, float2 *cxy,
+                                                  float *cw, uint32_t *surv, uint32_t n_keep,
+                                                  uint32_t tag, uint32_t lane, float *out_pos) {
   if (d.b == 16) {
-    if (d.w == 8) return cull_staged<CHECKED, true, true>(d, g, M, sw, sI, cx, cy, cw, surv, n_keep, lane, out_pos);
-    return cull_staged<CHECKED, true, false>(d, g, M, sw, sI, cx, cy, cw, surv, n_keep, lane, out_pos);
+    if (d.w == 8) return cull_staged<CHECKED, true, true>(d, g, M, sw, sI, cxy, cw, surv, n_keep, tag, lane, out_pos);
+    return cull_staged<CHECKED, true, false>(d, g, M, sw, sI, cxy, cw, surv, n_keep, tag, lane, out_pos);
   }
-  if (d.w == 8) return cull_staged<CHECKED, false, true>(d, g, M, sw, sI, cx, cy, cw, surv, n_keep, lane, out_pos);
-  return cull_staged<CHECKED, false, false>(d, g, M, sw, sI, cx, cy, cw, surv, n_keep, lane, out_pos);
+  if (d.w == 8) return cull_staged<CHECKED, false, true>(d, g, M, sw, sI, cxy, cw, surv, n_keep, tag, lane, out_pos);
+  return cull_staged<CHECKED, false, false>(d, g, M, sw, sI, cxy, cw, surv, n_keep, tag, lane, out_pos);
 }
 
-// Fused decode + cull + compaction.  Persistent warps take `per_grab`
-// consecutive meshlets (staged like the batched decoder), drop meshlets whose
-// box is outside the frustum before touching their triangles, decode and cull
-// the rest, collect the grab's survivors in shared memory and reserve their
-// output space with one atomicAdd per grab.
-template <bool CHECKED>
-__global__ void __launch_bounds__(512) decode_cull_kernel(BatchArgs a, const float *view_proj,
+// Writes a warp's buffered survivors as global index triples: one atomicAdd
+// reserves their output range, word e of which is corner e % 3 of survivor
+// e / 3 (coalesced stores).
+__device__ __forceinline__ void cull_flush(const uint32_t *surv, const uint32_t *svb, uint32_t n,
+                                           uint32_t lane, uint32_t *tri_out, uint32_t *counter) {
+  uint32_t dst = 0;
+  if (lane == 0) dst = atomicAdd(counter, n);
+  dst = __shfl_sync(kFull, dst, 0);
+  uint32_t *o = tri_out + 3ull * dst;
+  for (uint32_t e = lane; e < 3 * n; e += 32) {
+    const uint32_t t = e / 3, c = e - 3 * t;
+    const uint32_t p = surv[t];
+    o[e] = svb[p >> 24] + ((p >> (8 * c)) & 0xFFu);
+  }
+  __syncwarp();
+}
+
+// Fused decode + cull + compaction.  Persistent warps run the grab loop,
+// drop meshlets whose box is outside the frustum before touching their
+// triangles, decode and cull the rest and collect survivors in shared memory
+// across grabs; a full buffer (or the end of the work) is written out with
+// one atomicAdd.
+template <bool CHECKED, int MAX_THREADS>
+__global__ void __launch_bounds__(MAX_THREADS) decode_cull_kernel(BatchArgs a, const float *view_proj,
                                                           uint32_t per_grab, uint32_t *tri_out,
                                                           uint32_t *tri_count, float *out_pos,
                                                           uint32_t *status, uint32_t *scratch) {
@@ -349,75 +322,36 @@ __global__ void __launch_bounds__(512) decode_cull_kernel(BatchArgs a, const flo
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const CullLayout L = cull_layout(a.max_block_words, a.max_tris, per_grab);
   uint8_t *base = smem + warp * L.bytes;
-  uint32_t *sdesc = reinterpret_cast<uint32_t *>(base + L.desc);
-  uint32_t *spay = reinterpret_cast<uint32_t *>(base + L.pay);
   uint8_t *sI = base + L.stream;
-  float *cx = reinterpret_cast<float *>(base + L.clip);
-  float *cy = cx + 256;
-  float *cw = cy + 256;
+  float2 *cxy = reinterpret_cast<float2 *>(base + L.clip);
+  float *cw = reinterpret_cast<float *>(cxy + L.n_clip);
+  uint32_t *svb = reinterpret_cast<uint32_t *>(base + L.svb);
   uint32_t *surv = reinterpret_cast<uint32_t *>(base + L.surv);
+  uint32_t n_keep = 0, n_src = 0;  // buffered survivors, meshlets they reference
   if (threadIdx.x < 16) s_M[threadIdx.x] = view_proj[threadIdx.x];
   __syncthreads();
-  const uint32_t cap16 = (per_grab * ((a.max_block_words + 3) & ~3u)) / 4;
-  const uint32_t bytes16 = a.payload_bytes / 16 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)(a.payload_bytes / 16);
-  const uint4 *gdesc = reinterpret_cast<const uint4 *>(a.desc);
-  const uint4 *gpay = reinterpret_cast<const uint4 *>(a.payload);
-  for (;;) {
-    uint32_t m0 = 0;
-    if (lane == 0) m0 = atomicAdd(scratch + kQueue, per_grab);
-    m0 = __shfl_sync(kFull, m0, 0);
-    if (m0 >= a.n_meshlets) break;
-    const uint32_t cnt = min(per_grab, a.n_meshlets - m0);
-    uint4 dv = make_uint4(0, 0, 0, 0);
-    if (lane < 2 * cnt) dv = __ldg(gdesc + 2ull * m0 + lane);
-    uint32_t end16 = bytes16;
-    if (m0 + cnt < a.n_meshlets) end16 = __ldg(&a.desc[m0 + cnt].payload_off16);
-    if (lane < 2 * cnt) reinterpret_cast<uint4 *>(sdesc)[lane] = dv;
-    const uint32_t start16 = __shfl_sync(kFull, dv.x, 0);
-    bool grab_staged = end16 >= start16 && end16 - start16 <= cap16 && end16 <= bytes16;
-    if (grab_staged) {
-      uint4 *dst = reinterpret_cast<uint4 *>(spay);
-      for (uint32_t i = lane; i < end16 - start16; i += 32) dst[i] = __ldg(gpay + start16 + i);
-    }
-    __syncwarp();
-    uint32_t n_keep = 0;
-    for (uint32_t j = 0; j < cnt; j++) {
-      const uint4 *sd = reinterpret_cast<const uint4 *>(sdesc) + 2 * j;
-      const Desc d = unpack_desc(sd[0], sd[1]);
-      if (!header_ok(d, a)) {
-        if (lane == 0) set_status(status, MC_ERR_CORRUPT);
-        continue;
-      }
-      const Grid g = load_grid(a.grids + d.grid);
-      if (box_outside(d, g, s_M, lane)) continue;
-      const uint32_t padded16 = ((block_words(d) + 3) & ~3u) / 4;
-      const uint32_t *sw;
-      if (grab_staged && d.off16 >= start16 && d.off16 - start16 + padded16 <= end16 - start16) {
-        sw = spay + 4 * (d.off16 - start16);
-      } else {
-        grab_staged = false;
-        __syncwarp();
-        stage_payload(d, a.payload, spay, lane);
-        __syncwarp();
-        sw = spay;
-      }
-      const uint32_t r = cull_dispatch<CHECKED>(d, g, s_M, sw, sI, cx, cy, cw, surv, n_keep, lane, out_pos);
-      if (r == 0xFFFFFFFFu) {
-        if (lane == 0) set_status(status, MC_ERR_CORRUPT);
-      } else {
-        n_keep = r;
-      }
-      __syncwarp();
-    }
-    if (n_keep) {
-      uint32_t dst = 0;
-      if (lane == 0) dst = atomicAdd(scratch + kCount, n_keep);
-      dst = __shfl_sync(kFull, dst, 0);
-      uint32_t *o = tri_out + 3ull * dst;
-      for (uint32_t i = lane; i < 3 * n_keep; i += 32) o[i] = surv[i];
-    }
-    __syncwarp();
-  }
+  grab_loop(a, per_grab, base, lane, scratch + kQueue, status,
+                [&](const Desc &d, const uint32_t *sw) {
+                  const Grid g = load_grid(a.grids + d.grid);
+                  if (box_outside(d, g, s_M, lane)) return;
+                  // d.T <= max_tris (header_ok), so the meshlet fits an emptied buffer
+                  if (n_keep + d.T > L.cap || n_src == kSurvSources) {
+                    cull_flush(surv, svb, n_keep, lane, tri_out, scratch + kCount);
+                    n_keep = 0;
+                    n_src = 0;
+                  }
+                  if (lane == 0) svb[n_src] = d.vbase;
+                  const uint32_t r = cull_dispatch<CHECKED>(d, g, s_M, sw, sI, cxy, cw, surv, n_keep,
+                                                            n_src << 24, lane, out_pos);
+                  if (r == 0xFFFFFFFFu) {
+                    if (lane == 0) set_status(status, MC_ERR_CORRUPT);
+                  } else if (r != n_keep) {
+                    n_keep = r;
+                    n_src++;
+                  }
+                  __syncwarp();
+                });
+  if (n_keep) cull_flush(surv, svb, n_keep, lane, tri_out, scratch + kCount);
   // the last CTA publishes the count and resets the scratch
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -471,20 +405,37 @@ cudaError_t launch_batch(const BatchArgs &a, uint32_t ctas, uint32_t warps, uint
   return cudaGetLastError();
 }
 
+namespace {
+// Small CTAs (up to 4 warps) get a build whose register budget needs no
+// spills; larger CTAs the 512-thread build.
+template <int MAX_THREADS>
+cudaError_t launch_cull_t(const BatchArgs &a, const float *view_proj, uint32_t ctas, uint32_t warps,
+                          uint32_t per_grab, bool checked, uint32_t *tri_out, uint32_t *tri_count,
+                          float *out_pos, uint32_t *status, uint32_t *scratch, cudaStream_t s) {
+  const uint32_t smem = cull_smem_per_warp(a.max_block_words, a.max_tris, per_grab) * warps;
+  if (checked) {
+    cudaFuncSetAttribute(decode_cull_kernel<true, MAX_THREADS>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    decode_cull_kernel<true, MAX_THREADS><<<ctas, warps * 32, smem, s>>>(
+        a, view_proj, per_grab, tri_out, tri_count, out_pos, status, scratch);
+  } else {
+    cudaFuncSetAttribute(decode_cull_kernel<false, MAX_THREADS>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    decode_cull_kernel<false, MAX_THREADS><<<ctas, warps * 32, smem, s>>>(
+        a, view_proj, per_grab, tri_out, tri_count, out_pos, status, scratch);
+  }
+  return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_cull(const BatchArgs &a, const float *view_proj, uint32_t ctas, uint32_t warps,
                         uint32_t per_grab, bool checked, uint32_t *tri_out, uint32_t *tri_count,
                         float *out_pos, uint32_t *status, uint32_t *scratch, cudaStream_t s) {
-  const uint32_t smem = cull_smem_per_warp(a.max_block_words, a.max_tris, per_grab) * warps;
-  if (checked) {
-    cudaFuncSetAttribute(decode_cull_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    decode_cull_kernel<true><<<ctas, warps * 32, smem, s>>>(a, view_proj, per_grab, tri_out, tri_count,
-                                                            out_pos, status, scratch);
-  } else {
-    cudaFuncSetAttribute(decode_cull_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    decode_cull_kernel<false><<<ctas, warps * 32, smem, s>>>(a, view_proj, per_grab, tri_out, tri_count,
-                                                             out_pos, status, scratch);
-  }
-  return cudaGetLastError();
+  if (warps <= 4)
+    return launch_cull_t<128>(a, view_proj, ctas, warps, per_grab, checked, tri_out, tri_count,
+                              out_pos, status, scratch, s);
+  return launch_cull_t<512>(a, view_proj, ctas, warps, per_grab, checked, tri_out, tri_count,
+                            out_pos, status, scratch, s);
 }
 
 cudaError_t launch_requests(const BatchArgs &a, const mc_request *reqs, uint32_t n_reqs,
@@ -527,10 +478,16 @@ int max_ctas_per_sm_cull(uint32_t warps, uint32_t max_block_words, uint32_t max_
                          uint32_t per_grab) {
   int n = 0;
   const int smem = (int)(cull_smem_per_warp(max_block_words, max_tris, per_grab) * warps);
-  if (smem > 227 * 1024) return 0;
-  cudaFuncSetAttribute(decode_cull_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(decode_cull_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_cull_kernel<false>, warps * 32, smem);
+  if (smem > 227 * 1024 || warps > 16) return 0;
+  if (warps <= 4) {
+    cudaFuncSetAttribute(decode_cull_kernel<false, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(decode_cull_kernel<true, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_cull_kernel<false, 128>, warps * 32, smem);
+  } else {
+    cudaFuncSetAttribute(decode_cull_kernel<false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(decode_cull_kernel<true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_cull_kernel<false, 512>, warps * 32, smem);
+  }
   return n;
 }
 

@@ -86,3 +86,30 @@ def test_cull_graph_many_views(scene):
     got = tri[: 3 * counts[-1]].cpu().numpy().view(np.uint32)
     assert np.array_equal(_sorted_rows(got), _sorted_rows(last_ref))
     assert int(st.item()) == 0 and int(scratch.abs().sum()) == 0
+
+
+@pytest.mark.parametrize("tuning", [None, {"meshlets_per_grab": 1}, {"warps_per_cta": 8, "meshlets_per_grab": 16}])
+def test_cull_small_meshlets_generic_path(tuning):
+    """Meshlets of at most 8 vertices / 8 triangles with 12-bit positions and
+    3-bit reuse entries (the kernel's generic bit-extraction path), declared
+    against a 256-triangle bound: a warp's survivor buffer then fills up by
+    its meshlet count (32 sources) rather than by its triangle capacity."""
+    import torch
+    meshes = G.surface_batch(n_meshes=6, t_lo=500, t_hi=3_000, seed=21)
+    blob = O.concat([O.encode_mesh(m, (8, 8), 12, 1, mesh_id=i) for i, m in enumerate(meshes)])
+    f = blob.fields()
+    assert int(f["w"].max()) < 8 and int(f["b"].max()) == 12
+    from tests.gpu_util import block_words_max
+    db = mc.DeviceBatch.from_arrays(blob.desc, blob.payload, blob.grids, blob.total_tris,
+                                    blob.total_verts, block_words_max(blob.desc), 256)
+    pts = np.concatenate([m.pos for m in meshes])
+    c = 0.5 * (pts.min(0) + pts.max(0))
+    r = float(np.linalg.norm(pts - c, axis=1).max())
+    for vp in G.camera_poses(3, c, r, seed=22):
+        ref_tri, ref_pos, passed = O.decode_cull(blob, vp)
+        tri, pos, st = _run(db, vp, tuning)
+        assert st == 0
+        assert np.array_equal(_sorted_rows(tri), _sorted_rows(ref_tri))
+        vm = np.repeat(passed, f["V"].astype(np.int64)).astype(bool)
+        assert np.array_equal(pos.reshape(-1, 3)[vm].view(np.uint32), ref_pos[vm].view(np.uint32))
+    torch.cuda.synchronize()
