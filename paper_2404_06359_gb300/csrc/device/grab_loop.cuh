@@ -70,13 +70,19 @@ __host__ __device__ inline uint32_t grab_loop_bytes(uint32_t max_block_words, ui
   return 32 * (per_grab + 1) + 16 + 4 * (per_grab * ((max_block_words + 3) & ~3u) + kSlackWords);
 }
 
-// Runs the warp's share of the work queue.  body(d, sw) is called by all
-// lanes for every meshlet whose header passes header_ok, with sw its payload
-// block in shared memory; a failed header sets MC_ERR_CORRUPT.
-template <class Body>
+// Runs the warp's share of the work queue.  Per grab, pre(sdesc, cnt) is
+// called by all lanes once the grab's cnt descriptors are in shared memory
+// (sdesc, 8 words each, not yet validated) and returns a warp-uniform word;
+// body(d, sw, j, word) is then called by all lanes for every meshlet j of the
+// grab whose header passes header_ok, with sw its payload block in shared
+// memory; a failed header sets MC_ERR_CORRUPT.
+struct NoPre {
+  __device__ __forceinline__ uint32_t operator()(const uint32_t *, uint32_t) const { return 0; }
+};
+template <class Pre, class Body>
 __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab, uint8_t *wbase,
                                           uint32_t lane, uint32_t *queue, uint32_t *status,
-                                          Body &&body) {
+                                          Pre &&pre, Body &&body) {
   const uint32_t *sdesc = reinterpret_cast<const uint32_t *>(wbase);
   const uint32_t bar = smem_addr(wbase + 32 * (per_grab + 1));
   uint32_t *spay = reinterpret_cast<uint32_t *>(wbase + 32 * (per_grab + 1) + 16);
@@ -122,6 +128,7 @@ __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab,
       }
       parity ^= 1u;
     }
+    const uint32_t word = pre(sdesc, cnt);
     for (uint32_t j = 0; j < cnt; j++) {
       const uint4 *sd = reinterpret_cast<const uint4 *>(sdesc) + 2 * j;
       const Desc d = unpack_desc(sd[0], sd[1]);
@@ -140,7 +147,7 @@ __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab,
         __syncwarp();
         sw = spay;
       }
-      body(d, sw);
+      body(d, sw, j, word);
     }
     __syncwarp();
   }

@@ -69,8 +69,8 @@ __global__ void __launch_bounds__(512) decode_batch_kernel(BatchArgs a, uint32_t
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   uint8_t *base = smem + warp * smem_per_warp;
   uint8_t *sI = base + smem_per_warp - kStreamBytes;
-  grab_loop(a, per_grab, base, lane, scratch + kQueue, status,
-            [&](const Desc &d, const uint32_t *sw) {
+  grab_loop(a, per_grab, base, lane, scratch + kQueue, status, NoPre{},
+            [&](const Desc &d, const uint32_t *sw, uint32_t, uint32_t) {
               const Grid g = load_grid(a.grids + d.grid);
               if (!decode_dispatch<CHECKED>(d, g, sw, sI, lane, out_local, out_global, out_pos) &&
                   lane == 0)
@@ -169,29 +169,47 @@ __device__ __forceinline__ float clip_row(const float *M, int r, float x, float 
   return __fmaf_rn(M[4 * r + 2], z, __fmaf_rn(M[4 * r + 1], y, __fmaf_rn(M[4 * r + 0], x, M[4 * r + 3])));
 }
 
-// true when all 8 corners of the meshlet's quantisation box are outside one
-// clip plane.  Lanes 0..7 each take one corner and collect the planes it is
-// outside of; the warp AND-reduces the plane masks.
-__device__ __forceinline__ bool box_outside(const Desc &d, const Grid &g, const float *M,
-                                            uint32_t lane) {
-  uint32_t mask = 0x3Fu;
-  if (lane < 8) {
-    float p[3];
+// Frustum test of a grab's meshlets: bit j of the result is set when all 8
+// corners of meshlet j's quantisation box [L, L + 2^b - 1] (dequantised like
+// the vertices) are outside one clip plane.  Lane 8 i + c takes corner c of
+// meshlet 4 p + i in pass p and collects the planes the corner is outside
+// of; the eight lanes of a meshlet AND their plane masks.  A descriptor with
+// an out-of-range grid index gets no bit (its header check rejects it).
+__device__ __forceinline__ uint32_t grab_outside(const BatchArgs &a, const uint32_t *sdesc,
+                                                 uint32_t cnt, const float *M, uint32_t lane) {
+  uint32_t out = 0;
+  const uint32_t corner = lane & 7u;
+  for (uint32_t p = 0; 4 * p < cnt; p++) {
+    const uint32_t j = 4 * p + (lane >> 3);
+    uint32_t mask = 0;
+    if (j < cnt) {
+      const uint32_t *w = sdesc + 8 * j;
+      const uint32_t b = (w[4] >> 8) & 0xFFu, grid = w[4] >> 16;
+      if (grid < a.n_grids) {
+        const Grid g = load_grid(a.grids + grid);
+        const uint32_t ext = b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u);
+        float p3[3];
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
-      const uint32_t top = d.L[c] + (d.b >= 32 ? 0xFFFFFFFFu : ((1u << d.b) - 1u));
-      p[c] = dequant((lane >> c) & 1u ? top : d.L[c], g.G[c], g.D[c]);
-    }
-    const float w = clip_row(M, 3, p[0], p[1], p[2]);
-    mask = 0;
+        for (int c = 0; c < 3; c++) {
+          const uint32_t L = w[5 + c];
+          p3[c] = dequant((corner >> c) & 1u ? L + ext : L, g.G[c], g.D[c]);
+        }
+        const float cw = clip_row(M, 3, p3[0], p3[1], p3[2]);
 #pragma unroll
-    for (int r = 0; r < 3; r++) {
-      const float comp = clip_row(M, r, p[0], p[1], p[2]);
-      if (__fadd_rn(w, comp) < 0.0f) mask |= 1u << (2 * r);
-      if (__fsub_rn(w, comp) < 0.0f) mask |= 2u << (2 * r);
+        for (int r = 0; r < 3; r++) {
+          const float comp = clip_row(M, r, p3[0], p3[1], p3[2]);
+          mask |= (__fadd_rn(cw, comp) < 0.0f ? 1u : 0u) << (2 * r);
+          mask |= (__fsub_rn(cw, comp) < 0.0f ? 2u : 0u) << (2 * r);
+        }
+      }
     }
+    mask &= __shfl_xor_sync(kFull, mask, 1);
+    mask &= __shfl_xor_sync(kFull, mask, 2);
+    mask &= __shfl_xor_sync(kFull, mask, 4);
+    const uint32_t bal = __ballot_sync(kFull, mask != 0 && corner == 0);
+    out |= ((bal & 1u) | ((bal >> 7) & 2u) | ((bal >> 14) & 4u) | ((bal >> 21) & 8u)) << (4 * p);
   }
-  return __reduce_and_sync(kFull, mask) != 0;
+  return out;
 }
 
 constexpr uint32_t kSurvSources = 32;  // meshlets one survivor buffer may reference
@@ -331,9 +349,12 @@ __global__ void __launch_bounds__(MAX_THREADS) decode_cull_kernel(BatchArgs a, c
   if (threadIdx.x < 16) s_M[threadIdx.x] = view_proj[threadIdx.x];
   __syncthreads();
   grab_loop(a, per_grab, base, lane, scratch + kQueue, status,
-                [&](const Desc &d, const uint32_t *sw) {
+                [&](const uint32_t *sdesc, uint32_t cnt) {
+                  return grab_outside(a, sdesc, cnt, s_M, lane);
+                },
+                [&](const Desc &d, const uint32_t *sw, uint32_t j, uint32_t outside) {
+                  if ((outside >> j) & 1u) return;
                   const Grid g = load_grid(a.grids + d.grid);
-                  if (box_outside(d, g, s_M, lane)) return;
                   // d.T <= max_tris (header_ok), so the meshlet fits an emptied buffer
                   if (n_keep + d.T > L.cap || n_src == kSurvSources) {
                     cull_flush(surv, svb, n_keep, lane, tri_out, scratch + kCount);
