@@ -52,10 +52,11 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# DRAM bytes (read + write) of one decode_batch launch from an ncu capture
-# (profiles/decode_batch_cfg2.md), per decoded triangle slot and keyed by the
-# kernel-source hash it was taken on; reported only while the sources match.
-NCU_TRAFFIC = {"45e7b1e39d5aae9a": {2: 428.999e6 / 18015946, 4: 898.136e6 / 55596770}}
+# DRAM bytes (read + write) of one launch of the dominant kernel from an ncu
+# capture (profiles/decode_batch_cfg2.md for cfg2, profiles/decode_cull_cfg4.md
+# for cfg4), per decoded triangle slot and keyed by the kernel-source hash it
+# was taken on; reported only while the sources match.
+NCU_TRAFFIC = {"e8d0c2b13f1a5a35": {2: 429.659840e6 / 18015946, 4: 896.483840e6 / 55596770}}
 
 
 def _kernel_hash():
