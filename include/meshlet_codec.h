@@ -312,8 +312,11 @@ mc_status mc_decode_cull(const mc_device_batch *b, const float *d_view_proj,
 /* Time candidate launch shapes of mc_decode_batch on this batch (the outputs
  * are overwritten) and remember the fastest for batches with the same
  * signature (meshlet count, payload size, largest block) on this device.
- * Synchronises `stream`.  best (may be NULL) receives the chosen shape,
- * best_ms (may be NULL) its time. */
+ * Each shape runs four times, each run after the positions have been
+ * rewritten (which evicts the input from L2 when it is larger than L2, as
+ * between frames); the best of the last three counts.  Synchronises
+ * `stream`.  best (may be NULL) receives the chosen shape, best_ms (may be
+ * NULL) its time. */
 mc_status mc_autotune(const mc_device_batch *b, uint8_t *d_local, uint32_t *d_global,
                       float *d_pos, uint32_t *d_status, void *d_scratch, void *stream,
                       mc_tuning *best, float *best_ms);

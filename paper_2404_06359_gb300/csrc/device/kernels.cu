@@ -3,6 +3,12 @@
 // queue) and fused decode + cull + compaction.
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <set>
+#include <tuple>
+#include <utility>
+
 #include "decode_warp.cuh"
 #include "grab_loop.cuh"
 #include "kernels.h"
@@ -388,6 +394,57 @@ __global__ void __launch_bounds__(MAX_THREADS) decode_cull_kernel(BatchArgs a, c
 }
 
 // ------------------------------------------------------------- launchers
+namespace {
+constexpr int kMaxSmem = 227 * 1024;  // opt-in shared memory per CTA on sm_103a
+
+// Per-device, per-kernel launch set-up done once: the dynamic shared-memory
+// limit is raised to the maximum on first use (it only permits larger
+// launches), and occupancy answers are cached, so a launch costs no driver
+// calls beyond the launch itself.
+std::mutex g_attr_mu;
+std::set<std::pair<int, const void *>> g_attr_done;
+std::map<std::tuple<int, const void *, int, int>, int> g_occ;
+
+int device_now() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d;
+}
+void prepare(const void *f) {
+  const int dev = device_now();
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (!g_attr_done.insert({dev, f}).second) return;
+  // dynamic limit = the device's opt-in maximum minus the kernel's static
+  // shared memory
+  int optin = 0;
+  cudaFuncAttributes fa{};
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+      cudaFuncGetAttributes(&fa, f) == cudaSuccess && optin > (int)fa.sharedSizeBytes)
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         optin - (int)fa.sharedSizeBytes);
+  (void)cudaGetLastError();  // a refused attribute shows up as a launch error instead
+}
+int occupancy(const void *f, int threads, int smem) {
+  if (smem > kMaxSmem - 64) return 0;  // leave room for the kernels' static shared memory
+  prepare(f);
+  const auto key = std::make_tuple(device_now(), f, threads, smem);
+  {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) return it->second;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess) n = 0;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  g_occ[key] = n;
+  return n;
+}
+template <class K>
+const void *fn(K k) {
+  return reinterpret_cast<const void *>(k);
+}
+}  // namespace
+
 cudaError_t launch_plain(const BatchArgs &a, uint32_t first, uint32_t count, uint32_t warps,
                          uint32_t max_block_words, bool checked, uint8_t *out_local,
                          uint32_t *out_global, float *out_pos, uint32_t *status,
@@ -397,11 +454,11 @@ cudaError_t launch_plain(const BatchArgs &a, uint32_t first, uint32_t count, uin
   const uint32_t smem = spw * warps;
   const uint32_t grid = (count + warps - 1) / warps;
   if (checked) {
-    cudaFuncSetAttribute(decode_plain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    prepare(fn(decode_plain_kernel<true>));
     decode_plain_kernel<true><<<grid, warps * 32, smem, s>>>(a, first, count, spw, out_local,
                                                              out_global, out_pos, status);
   } else {
-    cudaFuncSetAttribute(decode_plain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    prepare(fn(decode_plain_kernel<false>));
     decode_plain_kernel<false><<<grid, warps * 32, smem, s>>>(a, first, count, spw, out_local,
                                                               out_global, out_pos, status);
   }
@@ -415,11 +472,11 @@ cudaError_t launch_batch(const BatchArgs &a, uint32_t ctas, uint32_t warps, uint
   const uint32_t spw = batch_smem_per_warp(max_block_words, per_grab);
   const uint32_t smem = spw * warps;
   if (checked) {
-    cudaFuncSetAttribute(decode_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    prepare(fn(decode_batch_kernel<true>));
     decode_batch_kernel<true><<<ctas, warps * 32, smem, s>>>(a, per_grab, spw, out_local,
                                                              out_global, out_pos, status, scratch);
   } else {
-    cudaFuncSetAttribute(decode_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    prepare(fn(decode_batch_kernel<false>));
     decode_batch_kernel<false><<<ctas, warps * 32, smem, s>>>(a, per_grab, spw, out_local,
                                                               out_global, out_pos, status, scratch);
   }
@@ -435,13 +492,11 @@ cudaError_t launch_cull_t(const BatchArgs &a, const float *view_proj, uint32_t c
                           float *out_pos, uint32_t *status, uint32_t *scratch, cudaStream_t s) {
   const uint32_t smem = cull_smem_per_warp(a.max_block_words, a.max_tris, per_grab) * warps;
   if (checked) {
-    cudaFuncSetAttribute(decode_cull_kernel<true, MAX_THREADS>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    prepare(fn(decode_cull_kernel<true, MAX_THREADS>));
     decode_cull_kernel<true, MAX_THREADS><<<ctas, warps * 32, smem, s>>>(
         a, view_proj, per_grab, tri_out, tri_count, out_pos, status, scratch);
   } else {
-    cudaFuncSetAttribute(decode_cull_kernel<false, MAX_THREADS>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    prepare(fn(decode_cull_kernel<false, MAX_THREADS>));
     decode_cull_kernel<false, MAX_THREADS><<<ctas, warps * 32, smem, s>>>(
         a, view_proj, per_grab, tri_out, tri_count, out_pos, status, scratch);
   }
@@ -465,52 +520,41 @@ cudaError_t launch_requests(const BatchArgs &a, const mc_request *reqs, uint32_t
   const uint32_t spw = 4 * (((a.max_block_words + 3) & ~3u) + kSlackWords) + kStreamBytes;
   const uint32_t smem = spw * warps;
   if (checked) {
-    cudaFuncSetAttribute(decode_requests_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    prepare(fn(decode_requests_kernel<true>));
     decode_requests_kernel<true><<<ctas, warps * 32, smem, s>>>(a, reqs, n_reqs, total_work, per_grab,
                                                                 status, scratch);
   } else {
-    cudaFuncSetAttribute(decode_requests_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    prepare(fn(decode_requests_kernel<false>));
     decode_requests_kernel<false><<<ctas, warps * 32, smem, s>>>(a, reqs, n_reqs, total_work, per_grab,
                                                                  status, scratch);
   }
   return cudaGetLastError();
 }
 
+// Occupancy of the unchecked builds (the checked ones use the same shared
+// memory; their register counts are within the same 64-per-thread class).
 int max_ctas_per_sm_requests(uint32_t warps, uint32_t max_block_words) {
-  int n = 0;
   const int smem = (int)((4 * (((max_block_words + 3) & ~3u) + kSlackWords) + kStreamBytes) * warps);
-  cudaFuncSetAttribute(decode_requests_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(decode_requests_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_requests_kernel<false>, warps * 32, smem);
-  return n;
+  prepare(fn(decode_requests_kernel<true>));
+  return occupancy(fn(decode_requests_kernel<false>), warps * 32, smem);
 }
 
 int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words, uint32_t per_grab) {
-  int n = 0;
   const int smem = (int)(batch_smem_per_warp(max_block_words, per_grab) * warps);
-  if (smem > 227 * 1024) return 0;
-  cudaFuncSetAttribute(decode_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(decode_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_batch_kernel<false>, warps * 32, smem);
-  return n;
+  prepare(fn(decode_batch_kernel<true>));
+  return occupancy(fn(decode_batch_kernel<false>), warps * 32, smem);
 }
 
 int max_ctas_per_sm_cull(uint32_t warps, uint32_t max_block_words, uint32_t max_tris,
                          uint32_t per_grab) {
-  int n = 0;
   const int smem = (int)(cull_smem_per_warp(max_block_words, max_tris, per_grab) * warps);
-  if (smem > 227 * 1024 || warps > 16) return 0;
+  if (warps > 16) return 0;
   if (warps <= 4) {
-    cudaFuncSetAttribute(decode_cull_kernel<false, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(decode_cull_kernel<true, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_cull_kernel<false, 128>, warps * 32, smem);
-  } else {
-    cudaFuncSetAttribute(decode_cull_kernel<false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(decode_cull_kernel<true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decode_cull_kernel<false, 512>, warps * 32, smem);
+    prepare(fn(decode_cull_kernel<true, 128>));
+    return occupancy(fn(decode_cull_kernel<false, 128>), warps * 32, smem);
   }
-  return n;
+  prepare(fn(decode_cull_kernel<true, 512>));
+  return occupancy(fn(decode_cull_kernel<false, 512>), warps * 32, smem);
 }
-
 
 }  // namespace mcdev
