@@ -3,12 +3,6 @@
 // queue) and fused decode + cull + compaction.
 #include <cuda_runtime.h>
 
-#include <map>
-#include <mutex>
-#include <set>
-#include <tuple>
-#include <utility>
-
 #include "decode_warp.cuh"
 #include "grab_loop.cuh"
 #include "kernels.h"
@@ -394,6 +388,15 @@ __global__ void __launch_bounds__(MAX_THREADS) decode_cull_kernel(BatchArgs a, c
 }
 
 // ------------------------------------------------------------- launchers
+}  // namespace mcdev
+
+#include <map>
+#include <mutex>
+#include <set>
+#include <tuple>
+#include <utility>
+
+namespace mcdev {
 namespace {
 constexpr int kMaxSmem = 227 * 1024;  // opt-in shared memory per CTA on sm_103a
 
