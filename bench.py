@@ -190,36 +190,48 @@ def build_workload(cfg: int, rank: int):
     raise SystemExit(f"unknown config {cfg}")
 
 
-def cpu_oracle_baseline(blob, budget_s: float = 10.0):
-    """The oracle's sequential C decode (one call over a prefix of the batch,
-    sized from a short probe to take about ``budget_s``), on one host core."""
+def cpu_oracle_baseline(blob, budget_s: float = 10.0, vp=None):
+    """The oracle's sequential C decode (or, given a view-projection matrix,
+    its fused decode + cull for that view) in one call over a prefix of the
+    batch, sized from a short probe to take about ``budget_s``, on one host
+    core."""
     import oracle as O
     a = blob.arrays()
     ob = O.Blob(a["desc"], a["payload"], a["grids"])
     n = ob.n_meshlets
+
+    def run(count):
+        if vp is None:
+            return O.decode(ob, 0, count, want_pos64=False)
+        return O.decode_cull(ob, vp, 0, count)
+
     t0 = time.perf_counter()
-    O.decode(ob, 0, min(n, 2000), want_pos64=False)
+    run(min(n, 2000))
     probe = time.perf_counter() - t0
     count = int(min(n, max(2000, 2000 * budget_s / max(probe, 1e-6))))
     t0 = time.perf_counter()
-    loc, _, _, _ = O.decode(ob, 0, count, want_pos64=False)
+    run(count)
     dt = time.perf_counter() - t0
+    # input (non-degenerate) triangles of the sample, counted outside the timing
+    loc = O.decode(ob, 0, count, want_pos64=False)[0]
     f = ob.fields()
     end = int(f["tri_base"][count - 1]) + int(f["Tp"][count - 1])
     t = loc[:end].astype(np.int16)
     tris = int(((t[:, 0] != t[:, 1]) & (t[:, 1] != t[:, 2]) & (t[:, 0] != t[:, 2])).sum())
+    what = "decode + FP32 dequant" if vp is None else "decode + frustum/back-face cull + compaction, one view"
     return {"value": tris / dt / 1e9, "unit": "Gtps", "cores": 1, "kind": "oracle",
             "sample": f"first {count} of {n} meshlets ({tris} input triangles) of the same batch, "
-                      f"sequential C decode + FP32 dequant in one call, {dt:.2f} s, 1 thread"}
+                      f"sequential C {what} in one call, {dt:.2f} s, 1 thread"}
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    blob, meshes, _ = build_workload(args.config, 0)
+    blob, meshes, vps = build_workload(args.config, 0)
+    vp = vps[0] if args.config == 4 else None
     per = []
     for i in range(args.warmup + args.steps):
-        r = cpu_oracle_baseline(blob, budget_s=max(1.0, args.ref_seconds / max(1, args.steps)))
+        r = cpu_oracle_baseline(blob, budget_s=max(1.0, args.ref_seconds / max(1, args.steps)), vp=vp)
         if i >= args.warmup:
             per.append(r["value"])
     v = float(np.mean(per))
@@ -467,7 +479,7 @@ def main():
     }
     res.update(extra)
     if rank == 0 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_oracle_baseline(blob, args.cpu_seconds)
+        res["cpu_baseline"] = cpu_oracle_baseline(blob, args.cpu_seconds, vps[0] if cull else None)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if ws > 1:
