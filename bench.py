@@ -422,13 +422,15 @@ def main():
             h_loc = torch.empty(3 * T, dtype=torch.uint8).pin_memory()
             h_glob = torch.empty(3 * T, dtype=torch.int32).pin_memory() if want_global else None
             h_pos = torch.empty(3 * V, dtype=torch.float32).pin_memory()
+            h_in = mc.pinned_inputs(blob)  # the step's inputs, in pinned host memory
             et = []
             for i in range(args.e2e_steps + 2):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 mc.mc_decode_batch_host(blob, d_desc, d_pay, d_grid, out["local"],
                                         out["global"] if want_global else None, out["pos"],
-                                        out["status"], scratch, h_loc, h_glob, h_pos, tune, stream)
+                                        out["status"], scratch, h_loc, h_glob, h_pos, tune, stream,
+                                        host_inputs=h_in)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 if i >= 2:

@@ -340,10 +340,18 @@ mc_status mc_graph_launch(mc_graph *g, void *stream);
 void mc_graph_free(mc_graph *g);
 
 /* Host-buffer decode (end to end): copies the host blob arrays of `v` into
- * the caller's device buffers d_desc / d_payload / d_grids, decodes with
- * mc_decode_batch and copies the outputs back into h_local / h_global /
- * h_pos (NULL = not copied).  Host buffers should be pinned.  Asynchronous
- * on `stream`. */
+ * the caller's device buffers d_desc / d_payload / d_grids, decodes them as
+ * mc_decode_batch does and copies the outputs back into h_local / h_global /
+ * h_pos (NULL = not copied).  The batch is cut into up to 8 chunks of
+ * consecutive meshlets whose input copies, decodes and output copies run on
+ * three library-owned streams (one set per device), so that chunk i's decode
+ * overlaps chunk i+1's input and chunk i-1's output copies; the call is
+ * ordered after earlier work on `stream` and later work on `stream` waits
+ * for all of it.  Host buffers (the view's arrays included) should be pinned
+ * for the copies to be asynchronous.  Concurrent calls from several host
+ * threads enqueue one after another.  MC_ERR_CORRUPT if the host
+ * descriptors' payload offsets, triangle or vertex bases are not
+ * non-decreasing.  Asynchronous on `stream`. */
 mc_status mc_decode_batch_host(const mc_blob_view_t *v, mc_desc *d_desc, uint8_t *d_payload,
                                mc_grid *d_grids, uint8_t *d_local, uint32_t *d_global,
                                float *d_pos, uint32_t *d_status, void *d_scratch,

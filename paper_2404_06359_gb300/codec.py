@@ -425,9 +425,25 @@ def mc_graph_launch(g: Graph, stream=None):
     _check(lib().mc_graph_launch(g._h, _stream(stream)), "mc_graph_launch")
 
 
+def pinned_inputs(blob: Blob) -> dict:
+    """Page-locked host copies of the blob's descriptor, payload and grid
+    arrays (for mc_decode_batch_host's asynchronous input copies)."""
+    import torch
+    a = blob.arrays()
+    return {k: torch.from_numpy(np.ascontiguousarray(a[k]).reshape(-1)).pin_memory()
+            for k in ("desc", "payload", "grids")}
+
+
 def mc_decode_batch_host(blob: Blob, d_desc, d_payload, d_grids, d_local, d_global, d_pos, d_status,
-                         d_scratch, h_local, h_global, h_pos, tuning=None, stream=None):
+                         d_scratch, h_local, h_global, h_pos, tuning=None, stream=None,
+                         host_inputs: dict | None = None):
+    """host_inputs: optional pinned copies of the blob arrays (pinned_inputs)
+    used as the copy sources instead of the blob's own (pageable) arrays."""
     v = blob.view()
+    if host_inputs is not None:
+        v = mc_blob_view_t.from_buffer_copy(v)
+        for k in ("desc", "payload", "grids"):
+            setattr(v, k, host_inputs[k].data_ptr())
     _check(lib().mc_decode_batch_host(C.byref(v), _tptr(d_desc), _tptr(d_payload), _tptr(d_grids),
                                       _tptr(d_local), _tptr(d_global), _tptr(d_pos), _tptr(d_status),
                                       _tptr(d_scratch), _tptr(h_local), _tptr(h_global), _tptr(h_pos),

@@ -429,6 +429,36 @@ extern "C" void mc_graph_free(mc_graph *g) {
   delete g;
 }
 
+namespace {
+// Internal streams of the host-buffer decode (input copies, decode, output
+// copies) and their events, created once per device.
+constexpr uint32_t kHostChunks = 8;
+struct HostPipe {
+  std::mutex mu;  // one call enqueues at a time (the events are shared)
+  cudaStream_t in = nullptr, comp = nullptr, out = nullptr;
+  cudaEvent_t ev[2 * kHostChunks + 3] = {};
+  bool ok = false;
+};
+std::mutex g_pipe_mu;
+std::map<int, HostPipe> g_pipes;
+
+HostPipe *host_pipe() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pipe_mu);
+  HostPipe &p = g_pipes[dev];
+  if (!p.ok) {
+    bool ok = cudaStreamCreateWithFlags(&p.in, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&p.comp, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&p.out, cudaStreamNonBlocking) == cudaSuccess;
+    for (auto &e : p.ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return nullptr;
+    p.ok = true;
+  }
+  return &p;
+}
+}  // namespace
+
 extern "C" mc_status mc_decode_batch_host(const mc_blob_view_t *v, mc_desc *d_desc,
                                           uint8_t *d_payload, mc_grid *d_grids, uint8_t *d_local,
                                           uint32_t *d_global, float *d_pos, uint32_t *d_status,
@@ -436,32 +466,91 @@ extern "C" mc_status mc_decode_batch_host(const mc_blob_view_t *v, mc_desc *d_de
                                           float *h_pos, const mc_tuning *t, void *stream) {
   if (!v || !d_desc || !d_payload || !d_grids || !d_pos) return MC_ERR_INVALID_ARG;
   if ((h_local && !d_local) || (h_global && !d_global)) return MC_ERR_INVALID_ARG;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(d_desc, v->desc, sizeof(mc_desc) * (size_t)v->n_meshlets,
-                                  cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_payload, v->payload, v->payload_bytes, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_grids, v->grids, sizeof(mc_grid) * (size_t)v->n_grids,
-                        cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return MC_ERR_CUDA;
+  const uint32_t n = v->n_meshlets;
+  if (n == 0) return MC_OK;
+  if (!v->desc || !v->payload || !v->grids) return MC_ERR_INVALID_ARG;
   mc_device_batch b{};
   b.desc = d_desc;
   b.payload = d_payload;
   b.grids = d_grids;
-  b.n_meshlets = v->n_meshlets;
+  b.n_meshlets = n;
   b.n_grids = v->n_grids;
   b.payload_bytes = v->payload_bytes;
   b.total_tris = v->total_tris;
   b.total_verts = v->total_verts;
   b.max_block_words = v->max_block_words;
   b.max_tris = v->max_tris;
-  mc_status st = mc_decode_batch(&b, d_local, d_global, d_pos, d_status, d_scratch, t, stream);
+  mc_status st = check_batch(&b);
   if (st != MC_OK) return st;
-  if (h_local) e = cudaMemcpyAsync(h_local, d_local, 3 * v->total_tris, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && h_global)
-    e = cudaMemcpyAsync(h_global, d_global, 12 * v->total_tris, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && h_pos)
-    e = cudaMemcpyAsync(h_pos, d_pos, 12 * v->total_verts, cudaMemcpyDeviceToHost, s);
+  if (!d_scratch || !aligned(d_scratch, 16) || !aligned(d_local, 16) || !aligned(d_global, 16))
+    return MC_ERR_INVALID_ARG;
+  // chunk boundaries (consecutive meshlets); their payload, triangle and
+  // vertex ranges come from the host descriptors, which must be monotonic
+  const uint32_t K = std::max<uint32_t>(1u, std::min<uint32_t>(kHostChunks, (n + 8191) / 8192));
+  uint32_t cut[kHostChunks + 1];
+  uint64_t pay[kHostChunks + 1], tri[kHostChunks + 1], vtx[kHostChunks + 1];
+  for (uint32_t i = 0; i <= K; i++) {
+    cut[i] = (uint32_t)((uint64_t)n * i / K);
+    const bool end = cut[i] == n;
+    pay[i] = end ? v->payload_bytes : 16ull * v->desc[cut[i]].payload_off16;
+    tri[i] = end ? v->total_tris : v->desc[cut[i]].tri_base;
+    vtx[i] = end ? v->total_verts : v->desc[cut[i]].vertex_base;
+    if (i > 0 && (pay[i] < pay[i - 1] || tri[i] < tri[i - 1] || vtx[i] < vtx[i - 1]))
+      return MC_ERR_CORRUPT;
+  }
+  if (pay[0] != 0 || tri[0] != 0 || vtx[0] != 0 || pay[K] > v->payload_bytes) return MC_ERR_CORRUPT;
+  HostPipe *P = host_pipe();
+  if (!P) return MC_ERR_CUDA;
+  const mc_tuning r = resolve_batch(&b, t);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lk(P->mu);
+  // chunk i: input copies on P->in, decode on P->comp, output copies on
+  // P->out, so chunk i's decode overlaps chunk i+1's input and chunk i-1's
+  // output copies; the caller's stream orders the whole call
+  cudaEvent_t *ev = P->ev;
+  cudaError_t e = cudaEventRecord(ev[0], s);
+  for (cudaStream_t q : {P->in, P->comp, P->out})
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(q, ev[0], 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_grids, v->grids, sizeof(mc_grid) * (size_t)v->n_grids,
+                        cudaMemcpyHostToDevice, P->in);
+  for (uint32_t i = 0; i < K && e == cudaSuccess && st == MC_OK; i++) {
+    const uint32_t m_a = cut[i], m_b = cut[i + 1];
+    e = cudaMemcpyAsync(d_desc + m_a, v->desc + m_a, sizeof(mc_desc) * (size_t)(m_b - m_a),
+                        cudaMemcpyHostToDevice, P->in);
+    if (e == cudaSuccess && pay[i + 1] > pay[i])
+      e = cudaMemcpyAsync(d_payload + pay[i], v->payload + pay[i], pay[i + 1] - pay[i],
+                          cudaMemcpyHostToDevice, P->in);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1 + i], P->in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->comp, ev[1 + i], 0);
+    if (e != cudaSuccess) break;
+    mc_device_batch c = b;
+    c.desc = d_desc + m_a;
+    c.n_meshlets = m_b - m_a;
+    c.payload_bytes = pay[i + 1];  // the chunk's blocks end there
+    st = launch_batch_checked(&c, d_local, d_global, d_pos, d_status, d_scratch, r, P->comp);
+    if (st != MC_OK) break;
+    e = cudaEventRecord(ev[1 + kHostChunks + i], P->comp);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->out, ev[1 + kHostChunks + i], 0);
+    if (e == cudaSuccess && h_local)
+      e = cudaMemcpyAsync(h_local + 3 * tri[i], d_local + 3 * tri[i], 3 * (tri[i + 1] - tri[i]),
+                          cudaMemcpyDeviceToHost, P->out);
+    if (e == cudaSuccess && h_global)
+      e = cudaMemcpyAsync(h_global + 3 * tri[i], d_global + 3 * tri[i], 12 * (tri[i + 1] - tri[i]),
+                          cudaMemcpyDeviceToHost, P->out);
+    if (e == cudaSuccess && h_pos)
+      e = cudaMemcpyAsync(h_pos + 3 * vtx[i], d_pos + 3 * vtx[i], 12 * (vtx[i + 1] - vtx[i]),
+                          cudaMemcpyDeviceToHost, P->out);
+  }
+  // join the internal streams back into the caller's stream (also on error,
+  // so that nothing of this call is left unordered)
+  cudaError_t j = cudaEventRecord(ev[2 * kHostChunks + 1], P->comp);
+  if (j == cudaSuccess) j = cudaStreamWaitEvent(s, ev[2 * kHostChunks + 1], 0);
+  if (j == cudaSuccess) j = cudaEventRecord(ev[2 * kHostChunks + 2], P->out);
+  if (j == cudaSuccess) j = cudaStreamWaitEvent(s, ev[2 * kHostChunks + 2], 0);
+  cudaEventRecord(ev[0], P->in);
+  cudaStreamWaitEvent(s, ev[0], 0);
+  if (st != MC_OK) return st;
+  if (e == cudaSuccess) e = j;
   return from_cuda(e);
 }

@@ -181,16 +181,23 @@ def test_graph_replay_and_autotune(mixed_batch):
     assert int(scratch.abs().sum()) == 0
 
 
-def test_host_buffer_decode_matches(mixed_batch):
-    """mc_decode_batch_host (copies in, decode, copies out) on a library blob."""
+@pytest.mark.parametrize("n_meshes,pinned", [(1, False), (1, True), (60, True)])
+def test_host_buffer_decode_matches(n_meshes, pinned):
+    """mc_decode_batch_host (copies in, decode, copies out) on a library blob;
+    60 tori give more than 8192 meshlets, so the call runs as several
+    overlapped chunks on the library's internal streams."""
     torch = _torch()
     rng = np.random.Generator(np.random.PCG64(12))
-    mesh = G.torus(20_000, rng)
-    m = mc.mc_meshletize(mesh.tris, mesh.n_verts, [(64, 126)])
-    blob = mc.mc_encode(m, mesh.pos, 16, 0)
-    ob = O.encode_mesh(mesh, (64, 126), 16, 0)
-    ref = O.decode(ob)
+    blobs = []
+    for i in range(n_meshes):
+        mesh = G.torus(20_000, rng)
+        m = mc.mc_meshletize(mesh.tris, mesh.n_verts, [(64, 126)])
+        blobs.append(mc.mc_encode(m, mesh.pos, 16, 0, mesh_id=i))
+    blob = blobs[0] if n_meshes == 1 else mc.mc_blob_concat(blobs)
+    a = blob.arrays()
+    ref = O.decode(O.Blob(a["desc"], a["payload"], a["grids"]))
     s = blob.stats()
+    assert (s["n_meshlets"] > 8192) == (n_meshes > 1)
     d_desc = torch.empty(32 * s["n_meshlets"], dtype=torch.uint8, device="cuda")
     d_pay = torch.empty(s["payload_bytes"], dtype=torch.uint8, device="cuda")
     d_grids = torch.empty(32 * s["n_grids"], dtype=torch.uint8, device="cuda")
@@ -200,12 +207,16 @@ def test_host_buffer_decode_matches(mixed_batch):
     d_pos = torch.empty(3 * V, dtype=torch.float32, device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     scratch = mc.new_scratch()
-    h_loc = torch.empty(3 * T, dtype=torch.uint8).pin_memory()
-    h_glob = torch.empty(3 * T, dtype=torch.int32).pin_memory()
-    h_pos = torch.empty(3 * V, dtype=torch.float32).pin_memory()
-    mc.mc_decode_batch_host(blob, d_desc, d_pay, d_grids, d_loc, d_glob, d_pos, st, scratch,
-                            h_loc, h_glob, h_pos)
-    torch.cuda.synchronize()
+    h_loc = torch.full((3 * T,), 0xEE, dtype=torch.uint8).pin_memory()
+    h_glob = torch.full((3 * T,), -1, dtype=torch.int32).pin_memory()
+    h_pos = torch.full((3 * V,), float("nan"), dtype=torch.float32).pin_memory()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        mc.mc_decode_batch_host(blob, d_desc, d_pay, d_grids, d_loc, d_glob, d_pos, st, scratch,
+                                h_loc, h_glob, h_pos, None, side,
+                                host_inputs=mc.pinned_inputs(blob) if pinned else None)
+    side.synchronize()  # the call is complete once its stream is
     res = {"local": h_loc.numpy(), "global": h_glob.numpy(), "pos": h_pos.numpy(),
            "status": st.cpu().numpy()}
     assert_same_decode(res, ref, "host-buffer decode")
+    assert int(scratch.abs().sum()) == 0
