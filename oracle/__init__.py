@@ -51,7 +51,7 @@ class _Blob(C.Structure):
                 ("degenerates", C.c_uint64), ("conn_bits", C.c_uint64),
                 ("reuse_entries", C.c_uint64), ("desc", C.POINTER(C.c_uint8)),
                 ("payload", C.POINTER(C.c_uint8)), ("grids", C.POINTER(C.c_uint8)),
-                ("vmap", C.POINTER(C.c_uint32))]
+                ("vmap", C.POINTER(C.c_uint32)), ("cones", C.POINTER(C.c_uint8))]
 
 
 def lib():
@@ -71,7 +71,9 @@ def lib():
             L.orc_dequant32.restype = C.c_float
             L.orc_decode_meshlet.argtypes = [P, P, u64, P, u32, P, P, P]
             L.orc_decode.argtypes = [P, u32, P, u64, P, u32, u32, u32, P, P, P, P]
-            L.orc_decode_cull.argtypes = [P, u32, P, u64, P, u32, u32, u32, P, P, P, P, P]
+            L.orc_decode_cull.argtypes = [P, u32, P, u64, P, u32, u32, u32, P, P, P, P, P, P]
+            L.orc_view_eye.argtypes = [P, P]
+            L.orc_cone_test.argtypes = [P, P]
             _lib = L
         return _lib
 
@@ -98,6 +100,7 @@ class Blob:
     payload: np.ndarray   # uint8 [bytes]
     grids: np.ndarray     # uint8 [G, 32]
     stats: dict = field(default_factory=dict)
+    cones: np.ndarray | None = None  # uint8 [M, 32] normal cones (format in oracle.h)
 
     @property
     def n_meshlets(self) -> int:
@@ -177,9 +180,11 @@ def encode(pos: np.ndarray, tris: np.ndarray, mtri: np.ndarray, mstart: np.ndarr
                                                   "degenerates", "conn_bits", "reuse_entries")}
         stats["vmap"] = np.ctypeslib.as_array(b.vmap, (b.total_verts,)).copy() \
             if b.total_verts else np.zeros(0, np.uint32)
+        cones = np.ctypeslib.as_array(b.cones, (b.n_meshlets * 32,)).copy().reshape(-1, 32) \
+            if b.n_meshlets else np.zeros((0, 32), np.uint8)
     finally:
         lib().orc_blob_free(out)
-    return Blob(desc, payload, grids, stats)
+    return Blob(desc, payload, grids, stats, cones)
 
 
 def encode_mesh(mesh, limits=(64, 126), bits=16, reuse_mode: int = 0, perm=None,
@@ -227,7 +232,9 @@ def concat(blobs: list[Blob]) -> Blob:
             vmaps.append(b.stats["vmap"])
     if len(vmaps) == len(blobs):
         stats["vmap_per_mesh"] = vmaps
-    return Blob(np.concatenate(descs), np.concatenate(pays), np.concatenate(grids), stats)
+    cones = np.concatenate([b.cones for b in blobs]) \
+        if all(b.cones is not None for b in blobs) else None
+    return Blob(np.concatenate(descs), np.concatenate(pays), np.concatenate(grids), stats, cones)
 
 
 def dequant32(g: int, G: float, D: float) -> float:
@@ -265,9 +272,25 @@ def decode(blob: Blob, first: int = 0, count: int | None = None, want_pos64: boo
             None if pos64 is None else pos64.reshape(-1, 3))
 
 
-def decode_cull(blob: Blob, vp: np.ndarray, first: int = 0, count: int | None = None):
+def view_eye(vp: np.ndarray):
+    """Camera position (float32 [3]) of a clip matrix, or None (orc_view_eye)."""
+    vp = np.ascontiguousarray(np.asarray(vp, np.float32).reshape(16))
+    eye = np.zeros(3, np.float32)
+    return eye if lib().orc_view_eye(_p(vp), _p(eye)) else None
+
+
+def cone_test(cone32: np.ndarray, eye: np.ndarray) -> bool:
+    """True when the normal-cone record rejects its meshlet seen from eye."""
+    c = np.ascontiguousarray(np.asarray(cone32, np.uint8).reshape(32))
+    e = np.ascontiguousarray(np.asarray(eye, np.float32).reshape(3))
+    return bool(lib().orc_cone_test(_p(c), _p(e)))
+
+
+def decode_cull(blob: Blob, vp: np.ndarray, first: int = 0, count: int | None = None,
+                cones: np.ndarray | None = None):
     """(survivor triples uint32 [n,3] in meshlet order, pos float32 [V_total,3],
-    frustum pass flags uint8 [M])."""
+    pass flags uint8 [M]).  cones (uint8 [M,32], e.g. blob.cones): also drop
+    meshlets the normal-cone test rejects."""
     if count is None:
         count = blob.n_meshlets - first
     T, V = blob.total_tris, blob.total_verts
@@ -276,8 +299,11 @@ def decode_cull(blob: Blob, vp: np.ndarray, first: int = 0, count: int | None = 
     passed = np.zeros(blob.n_meshlets, np.uint8)
     cnt = C.c_uint64(0)
     vp = np.ascontiguousarray(np.asarray(vp, np.float32).reshape(16))
+    cn = None if cones is None else np.ascontiguousarray(np.asarray(cones, np.uint8).reshape(-1, 32))
+    if cn is not None and cn.shape[0] != blob.n_meshlets:
+        raise ValueError("one cone record per meshlet expected")
     _check(lib().orc_decode_cull(_p(blob.desc), blob.n_meshlets, _p(blob.payload),
                                  blob.payload.size, _p(blob.grids), blob.n_grids, first, count,
-                                 _p(vp), _p(out), C.byref(cnt), _p(pos), _p(passed)),
+                                 _p(vp), _p(cn), _p(out), C.byref(cnt), _p(pos), _p(passed)),
            "orc_decode_cull")
     return out[: 3 * cnt.value].reshape(-1, 3), pos.reshape(-1, 3), passed

@@ -174,14 +174,55 @@ static float clip_row(const float *M, int r, float x, float y, float z) {
   return fmaf(M[4 * r + 2], z, fmaf(M[4 * r + 1], y, fmaf(M[4 * r + 0], x, M[4 * r + 3])));
 }
 
+int orc_view_eye(const float *vp, float eye[3]) {
+  double r0[3], r1[3], r3[3];
+  for (int c = 0; c < 3; c++) {
+    r0[c] = vp[c];
+    r1[c] = vp[4 + c];
+    r3[c] = vp[12 + c];
+  }
+  const double b0 = -(double)vp[3], b1 = -(double)vp[7], b3 = -(double)vp[15];
+  /* cross products r1 x r3, r3 x r0, r0 x r1 */
+  double k0[3] = {r1[1] * r3[2] - r1[2] * r3[1], r1[2] * r3[0] - r1[0] * r3[2],
+                  r1[0] * r3[1] - r1[1] * r3[0]};
+  double k1[3] = {r3[1] * r0[2] - r3[2] * r0[1], r3[2] * r0[0] - r3[0] * r0[2],
+                  r3[0] * r0[1] - r3[1] * r0[0]};
+  double k3[3] = {r0[1] * r1[2] - r0[2] * r1[1], r0[2] * r1[0] - r0[0] * r1[2],
+                  r0[0] * r1[1] - r0[1] * r1[0]};
+  double det = r0[0] * k0[0] + r0[1] * k0[1] + r0[2] * k0[2];
+  if (!(det != 0.0) || !isfinite(det)) return 0;
+  for (int c = 0; c < 3; c++) {
+    double e = (b0 * k0[c] + b1 * k1[c] + b3 * k3[c]) / det;
+    if (!isfinite(e)) return 0;
+    eye[c] = (float)e;
+  }
+  return 1;
+}
+
+int orc_cone_test(const uint8_t *cone32, const float eye[3]) {
+  float ctr[3], ax[3];
+  for (int c = 0; c < 3; c++) {
+    ctr[c] = get_f32(cone32 + 4 * c);
+    ax[c] = get_f32(cone32 + 16 + 4 * c);
+  }
+  float radius = get_f32(cone32 + 12), sn = get_f32(cone32 + 28);
+  if (!(sn < 1.0f)) return 0;
+  float vx = ctr[0] - eye[0], vy = ctr[1] - eye[1], vz = ctr[2] - eye[2];
+  float d = fmaf(ax[2], vz, fmaf(ax[1], vy, ax[0] * vx));
+  float l = sqrtf(fmaf(vz, vz, fmaf(vy, vy, vx * vx)));
+  return d >= fmaf(sn, l, radius);
+}
+
 int orc_decode_cull(const uint8_t *desc, uint32_t n_meshlets,
                     const uint8_t *payload, uint64_t payload_bytes,
                     const uint8_t *grids, uint32_t n_grids, uint32_t first,
-                    uint32_t count, const float *vp, uint32_t *tri_out,
-                    uint64_t *count_io, float *pos, uint8_t *pass_out) {
+                    uint32_t count, const float *vp, const uint8_t *cones,
+                    uint32_t *tri_out, uint64_t *count_io, float *pos, uint8_t *pass_out) {
   if (!desc || !payload || !grids || !vp || !tri_out || !count_io ||
       (uint64_t)first + count > n_meshlets)
     return ORC_ERR_ARG;
+  float eye[3];
+  const int use_cones = cones && orc_view_eye(vp, eye);
   uint8_t tl[3 * 256];
   float tp[3 * 256];
   float cx[256], cy[256], cw[256];
@@ -213,6 +254,7 @@ int orc_decode_cull(const uint8_t *desc, uint32_t n_meshlets,
       }
       if (all_out) culled = 1;
     }
+    if (!culled && use_cones && orc_cone_test(cones + 32 * (size_t)m, eye)) culled = 1;
     if (pass_out) pass_out[m] = (uint8_t)!culled;
     if (culled) continue;
     int rc = orc_decode_meshlet(desc + 32 * (size_t)m, payload, payload_bytes, grids, n_grids,

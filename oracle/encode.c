@@ -50,6 +50,85 @@ static void put_f32(uint8_t *p, float f) {
   put_u32(p, u);
 }
 
+/* Normal cone of one meshlet (record layout in oracle.h), from its decoded
+ * FP32 positions P[3 V] and its nt input triangles lt[3 nt] (local ids, input
+ * winding), all in FP64:
+ *   center = middle of the positions' bounding box, rounded to FP32;
+ *   radius = largest distance of a position from that center, times
+ *            1 + 2^-20, rounded up to FP32;
+ *   n_t    = normalised (p1 - p0) x (p2 - p0) of each non-degenerate triangle;
+ *   axis   = normalised sum of the n_t, rounded to FP32;
+ *   s      = sqrt(1 - c^2) + 2^-20 rounded up to FP32, c = min_t n_t . axis;
+ *            1 (no cone) when c <= 0, when no triangle has an area, or when s
+ *            would reach 1. */
+static void meshlet_cone(const float *P, uint32_t V, const uint32_t *lt, uint32_t nt,
+                         uint8_t *out) {
+  double lo[3], hi[3];
+  for (int c = 0; c < 3; c++) lo[c] = hi[c] = P[c];
+  for (uint32_t v = 1; v < V; v++)
+    for (int c = 0; c < 3; c++) {
+      double x = P[3 * v + c];
+      if (x < lo[c]) lo[c] = x;
+      if (x > hi[c]) hi[c] = x;
+    }
+  float cf[3];
+  for (int c = 0; c < 3; c++) cf[c] = (float)((lo[c] + hi[c]) * 0.5);
+  double r = 0.0;
+  for (uint32_t v = 0; v < V; v++) {
+    double dx = (double)P[3 * v] - (double)cf[0];
+    double dy = (double)P[3 * v + 1] - (double)cf[1];
+    double dz = (double)P[3 * v + 2] - (double)cf[2];
+    double d = sqrt(dx * dx + dy * dy + dz * dz);
+    if (d > r) r = d;
+  }
+  r = r * (1.0 + ldexp(1.0, -20));
+  float rf = (float)r;
+  if ((double)rf < r) rf = nextafterf(rf, INFINITY);
+  double n[256][3], S[3] = {0.0, 0.0, 0.0};
+  uint32_t k = 0;
+  for (uint32_t t = 0; t < nt; t++) {
+    const float *p0 = P + 3 * lt[3 * t], *p1 = P + 3 * lt[3 * t + 1], *p2 = P + 3 * lt[3 * t + 2];
+    double e1[3], e2[3];
+    for (int c = 0; c < 3; c++) {
+      e1[c] = (double)p1[c] - (double)p0[c];
+      e2[c] = (double)p2[c] - (double)p0[c];
+    }
+    double x = e1[1] * e2[2] - e1[2] * e2[1];
+    double y = e1[2] * e2[0] - e1[0] * e2[2];
+    double z = e1[0] * e2[1] - e1[1] * e2[0];
+    double len = sqrt(x * x + y * y + z * z);
+    if (!(len > 0.0)) continue;
+    n[k][0] = x / len;
+    n[k][1] = y / len;
+    n[k][2] = z / len;
+    for (int c = 0; c < 3; c++) S[c] += n[k][c];
+    k++;
+  }
+  float af[3] = {0.0f, 0.0f, 1.0f}, sf = 1.0f;
+  double sl = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+  if (k > 0 && sl > 0.0) {
+    double a[3] = {S[0] / sl, S[1] / sl, S[2] / sl};
+    double cmin = 1.0;
+    for (uint32_t t = 0; t < k; t++) {
+      double d = n[t][0] * a[0] + n[t][1] * a[1] + n[t][2] * a[2];
+      if (d < cmin) cmin = d;
+    }
+    for (int c = 0; c < 3; c++) af[c] = (float)a[c];
+    if (cmin > 0.0) {
+      double sn = sqrt(1.0 - cmin * cmin) + ldexp(1.0, -20);
+      if (sn < 1.0) {
+        sf = (float)sn;
+        if ((double)sf < sn) sf = nextafterf(sf, INFINITY);
+        if (sf > 1.0f) sf = 1.0f;
+      }
+    }
+  }
+  for (int c = 0; c < 3; c++) put_f32(out + 4 * c, cf[c]);
+  put_f32(out + 12, rf);
+  for (int c = 0; c < 3; c++) put_f32(out + 16 + 4 * c, af[c]);
+  put_f32(out + 28, sf);
+}
+
 static uint32_t ceil_log2(uint32_t v) {
   uint32_t w = 0;
   while ((1u << w) < v) w++;
@@ -205,8 +284,9 @@ int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
   uint64_t all_v = 0;
   for (uint32_t m = 0; m < n_meshlets; m++) all_v += ms[m].V;
   blob->vmap = (uint32_t *)calloc((size_t)all_v + 1, sizeof(uint32_t));
+  blob->cones = (uint8_t *)calloc((size_t)n_meshlets * 32 + 1, 1);
   uint32_t *words = (uint32_t *)calloc(1024, sizeof(uint32_t)); /* >= 2*8 + 64 + 768 + 3 */
-  if (!blob->desc || !blob->payload || !blob->grids || !blob->vmap || !words) {
+  if (!blob->desc || !blob->payload || !blob->grids || !blob->vmap || !blob->cones || !words) {
     free(words); free(ms); orc_blob_free(blob);
     return ORC_ERR_NOMEM;
   }
@@ -255,6 +335,31 @@ int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
     put_u16(d + 18, grid_of[x->b]);
     for (int c = 0; c < 3; c++) put_u32(d + 20 + 4 * c, x->L[c]);
     for (uint32_t i = 0; i < x->V; i++) blob->vmap[vbase + i] = x->gv[i];
+    {
+      /* decoded positions and local input triangles for the normal cone */
+      float P[3 * 256];
+      uint32_t lt[3 * 256];
+      const uint8_t *g = blob->grids + 32 * (size_t)grid_of[x->b];
+      for (uint32_t i = 0; i < x->V; i++)
+        for (int c = 0; c < 3; c++) {
+          float Gc, Dc;
+          uint32_t gu = (uint32_t)g[4 * c] | (uint32_t)g[4 * c + 1] << 8 |
+                        (uint32_t)g[4 * c + 2] << 16 | (uint32_t)g[4 * c + 3] << 24;
+          uint32_t du = (uint32_t)g[16 + 4 * c] | (uint32_t)g[17 + 4 * c] << 8 |
+                        (uint32_t)g[18 + 4 * c] << 16 | (uint32_t)g[19 + 4 * c] << 24;
+          memcpy(&Gc, &gu, 4);
+          memcpy(&Dc, &du, 4);
+          P[3 * i + c] = orc_dequant32(x->L[c] + x->q[i][c], Gc, Dc);
+        }
+      uint32_t nt = mstart[mi + 1] - mstart[mi];
+      for (uint32_t t = 0; t < nt; t++)
+        for (int c = 0; c < 3; c++) {
+          uint32_t gvid = tris[3 * (size_t)mtri[mstart[mi] + t] + c], li = 0;
+          while (li < x->V && x->gv[li] != gvid) li++;
+          lt[3 * t + c] = li;
+        }
+      meshlet_cone(P, x->V, lt, nt, blob->cones + 32 * (size_t)p);
+    }
     off_words += n;
     vbase += x->V;
     tbase += x->tp;
@@ -277,5 +382,6 @@ void orc_blob_free(orc_blob *b) {
   free(b->payload);
   free(b->grids);
   free(b->vmap);
+  free(b->cones);
   free(b);
 }

@@ -35,6 +35,12 @@
  *     ceil(R*w/32) reuse words, ceil(3*V*b/32) position words
  *     (vertex v channel c at bit (3v+c)*b).  Bit 0 of both flag words is 0.
  *   grid entry, 32 B: f32 G[3], u32 b, f32 Delta[3], u32 mesh id.
+ *   normal cone, 32 B per meshlet (blob order), the per-meshlet cull data
+ *   the paper keeps beside the offsets (Sec. 3, Sec. 5 "cull information"):
+ *     f32 center[3], f32 radius   a sphere holding the decoded vertices,
+ *     f32 axis[3], f32 s          unit axis of the cone holding every
+ *                                 triangle normal and s = sine of its half
+ *                                 angle plus 2^-20 (1 = no cone).
  */
 #ifndef ORACLE_H
 #define ORACLE_H
@@ -83,6 +89,7 @@ typedef struct {
   uint8_t *payload;
   uint8_t *grids;
   uint32_t *vmap; /* input vertex id of every decoded vertex (total_verts) */
+  uint8_t *cones; /* 32 B normal cone per meshlet (blob order) */
 } orc_blob;
 
 /* Encode the meshlets (mtri/mstart as produced by orc_meshletize) of one mesh.
@@ -117,12 +124,32 @@ int orc_decode(const uint8_t *desc, uint32_t n_meshlets, const uint8_t *payload,
 /* Decode + cull meshlets [first, first + count).  vp: row-major 4x4 clip
  * matrix.  Surviving triangles are appended to tri_out as global u32 triples
  * (meshlet order, then triangle order); *count_io is the running count in
- * triangles.  Positions are written only for meshlets that pass the frustum
- * test; pass_out[m] (may be NULL) receives 1 for those. */
+ * triangles.  cones (may be NULL: no cone test): the blob's cone records; a
+ * meshlet is then also dropped whole when the matrix has a camera position
+ * (orc_view_eye) and orc_cone_test rejects it.  Positions are written only
+ * for meshlets that pass both tests; pass_out[m] (may be NULL) receives 1
+ * for those. */
 int orc_decode_cull(const uint8_t *desc, uint32_t n_meshlets,
                     const uint8_t *payload, uint64_t payload_bytes,
                     const uint8_t *grids, uint32_t n_grids, uint32_t first,
-                    uint32_t count, const float *vp, uint32_t *tri_out,
-                    uint64_t *count_io, float *pos, uint8_t *pass_out);
+                    uint32_t count, const float *vp, const uint8_t *cones,
+                    uint32_t *tri_out, uint64_t *count_io, float *pos,
+                    uint8_t *pass_out);
+
+/* Camera position of a clip matrix: the point whose clip x, y and w are all
+ * zero (rows 0, 1, 3), solved in FP64 by the cross-product inverse
+ *   e = (b0 (r1 x r3) + b1 (r3 x r0) + b3 (r0 x r1)) / (r0 . (r1 x r3)),
+ * r_i = (M[i][0..2]), b_i = -M[i][3], and rounded to FP32.  Returns 0 (no
+ * camera position: an affine projection) when the determinant is 0 or not
+ * finite. */
+int orc_view_eye(const float *vp, float eye[3]);
+
+/* Normal-cone test of one meshlet (cone record cone32) for a camera at eye:
+ * 1 when every triangle is back-facing, by the sufficient condition
+ *   axis . (center - eye) >= s |center - eye| + radius,
+ * evaluated in FP32 as d = fma(a_z, v_z, fma(a_y, v_y, a_x v_x)),
+ * l = sqrt(fma(v_z, v_z, fma(v_y, v_y, v_x v_x))), reject iff s < 1 and
+ * d >= fma(s, l, radius), with v = center - eye componentwise. */
+int orc_cone_test(const uint8_t *cone32, const float eye[3]);
 
 #endif
