@@ -94,6 +94,31 @@ typedef struct {
   uint32_t mesh_id;
 } mc_grid;
 
+/* Normal cone of a meshlet, 32 bytes: the per-meshlet cull data kept beside
+ * the offsets (Sec. 3: the triangle normals of a meshlet form a cone, stored
+ * as an axis and an opening angle; Sec. 5: 16 B of cull information per
+ * meshlet in the paper's layout).  Here: a sphere holding the decoded
+ * vertices and a cone holding every triangle normal, computed by mc_encode
+ * in FP64 from the decoded FP32 positions:
+ *   center  middle of the positions' bounding box (FP32, nearest);
+ *   radius  largest distance of a position from center, times 1 + 2^-20,
+ *           rounded up to FP32;
+ *   axis    normalised sum of the unit normals (p1 - p0) x (p2 - p0) of the
+ *           triangles with an area (FP32, nearest);
+ *   s       sin of the cone's half angle + 2^-20, rounded up to FP32: with
+ *           c = the smallest normal . axis, s = sqrt(1 - c^2) + 2^-20; 1 (no
+ *           cone) when c <= 0, when no triangle has an area or when s >= 1.
+ * A meshlet is back-facing as a whole for a camera at e when
+ *   axis . (center - e) >= s |center - e| + radius
+ * (every normal n within the cone and every point p within the sphere then
+ * satisfy n . (p - e) >= 0). */
+typedef struct {
+  float center[3];
+  float radius;
+  float axis[3];
+  float s;
+} mc_cone;
+
 /* -------------------------------------------------------------------- host */
 
 typedef struct mc_meshlets mc_meshlets; /* opaque, library-owned */
@@ -171,6 +196,7 @@ typedef struct {
   uint64_t pos_bits_total;    /* sum of 3 V b */
   uint32_t max_block_words;   /* largest payload block, u32 words */
   uint32_t max_tris;          /* largest T' */
+  const mc_cone *cones;       /* normal cone per meshlet (n_meshlets) */
 } mc_blob_view_t;
 
 mc_status mc_blob_view(const mc_blob *b, mc_blob_view_t *v);
@@ -190,6 +216,9 @@ typedef struct {
   uint64_t total_verts; /* capacity of the outputs, vertices (sum of V) */
   uint32_t max_block_words; /* from mc_blob_view (sizes shared-memory staging) */
   uint32_t max_tris;        /* largest T' (from mc_blob_view); 0 = 256 */
+  const mc_cone *cones;     /* optional device copy of the normal cones
+                             * (n_meshlets, 16-byte aligned); NULL = the
+                             * fused cull uses no cone test */
 } mc_device_batch;
 
 /* Launch shape; zero fields take the library defaults or the autotuned
@@ -295,13 +324,22 @@ mc_status mc_decode_batch_noalloc(const mc_device_batch *b, uint8_t *d_local, ui
  *   d_tri_count  u32, receives the number of surviving triangles (the
  *                running count lives in d_scratch during the launch)
  *   d_pos        f32 [3 * total_verts], written for meshlets that pass the
- *                frustum test only
+ *                meshlet tests only
  * A meshlet is skipped when all 8 corners of its quantisation box
- * [L, L + 2^b - 1] lie outside one clip plane (-w <= x, y, z <= w); a
- * triangle is dropped when two of its indices coincide (restart
- * degenerates) or when all three clip w are positive and the determinant of
- * its (x, y, w) clip rows is not positive (back-facing, counter-clockwise
- * front faces).  Decoded indices never leave the chip except as survivors. */
+ * [L, L + 2^b - 1] lie outside one clip plane (-w <= x, y, z <= w), or --
+ * when b->cones is set and the matrix has a camera position -- when its
+ * normal cone faces away from that camera (mc_cone).  The camera position is
+ * the point whose clip x, y and w are zero: rows r_i = M[i][0..2] and
+ * b_i = -M[i][3] of rows 0, 1, 3 give, in FP64,
+ *   e = (b0 (r1 x r3) + b1 (r3 x r0) + b3 (r0 x r1)) / (r0 . (r1 x r3)),
+ * rounded to FP32 (none when the determinant is 0 or not finite); the cone
+ * test is evaluated in FP32 as v = center - e, d = fma(a_z, v_z, fma(a_y,
+ * v_y, a_x v_x)), l = sqrt(fma(v_z, v_z, fma(v_y, v_y, v_x v_x))), skip iff
+ * s < 1 and d >= fma(s, l, radius).  A triangle is dropped when two of its
+ * indices coincide (restart degenerates) or when all three clip w are
+ * positive and the determinant of its (x, y, w) clip rows is not positive
+ * (back-facing, counter-clockwise front faces).  Decoded indices never leave
+ * the chip except as survivors. */
 mc_status mc_decode_cull(const mc_device_batch *b, const float *d_view_proj,
                          uint32_t *d_tri_out, uint32_t *d_tri_count, float *d_pos,
                          uint32_t *d_status, void *d_scratch, const mc_tuning *t,

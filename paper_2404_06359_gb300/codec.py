@@ -39,13 +39,13 @@ class mc_blob_view_t(C.Structure):
                 ("n_meshes", u32), ("vertex_map", P), ("total_tris", u64), ("total_verts", u64),
                 ("input_tris", u64), ("restarts", u64), ("split_meshlets", u64),
                 ("conn_bits", u64), ("pos_bits_total", u64), ("max_block_words", u32),
-                ("max_tris", u32)]
+                ("max_tris", u32), ("cones", P)]
 
 
 class mc_device_batch(C.Structure):
     _fields_ = [("desc", P), ("payload", P), ("grids", P), ("n_meshlets", u32), ("n_grids", u32),
                 ("payload_bytes", u64), ("total_tris", u64), ("total_verts", u64),
-                ("max_block_words", u32), ("max_tris", u32)]
+                ("max_block_words", u32), ("max_tris", u32), ("cones", P)]
 
 
 class mc_request(C.Structure):
@@ -228,7 +228,8 @@ class Blob:
 
     def arrays(self) -> dict:
         """Copies of desc (uint8 [M,32]), payload, grids (uint8 [G,32]),
-        vertex_map and the per-mesh table."""
+        cones (uint8 [M,32], mc_cone records), vertex_map and the per-mesh
+        table."""
         v = self.view()
 
         def grab(ptr, n, dt):
@@ -242,6 +243,7 @@ class Blob:
             "desc": grab(v.desc, 32 * v.n_meshlets, np.uint8).reshape(-1, 32),
             "payload": grab(v.payload, v.payload_bytes, np.uint8),
             "grids": grab(v.grids, 32 * v.n_grids, np.uint8).reshape(-1, 32),
+            "cones": grab(v.cones, 32 * v.n_meshlets, np.uint8).reshape(-1, 32),
             "vertex_map": grab(v.vertex_map, v.total_verts, np.uint32),
             "meshes": meshes,
         }
@@ -286,38 +288,46 @@ class DeviceBatch:
     """A blob copied into device memory (torch uint8 tensors) plus the
     ``mc_device_batch`` that points at it."""
 
-    def __init__(self, blob: Blob, device="cuda"):
+    def __init__(self, blob: Blob, device="cuda", cones: bool = False):
+        """cones: also copy the normal cones (enables the cone test of the
+        fused cull)."""
         a = blob.arrays()
-        self._init(a["desc"], a["payload"], a["grids"], blob.stats(), device)
+        self._init(a["desc"], a["payload"], a["grids"], blob.stats(), device,
+                   a["cones"] if cones else None)
         self.meshes = a["meshes"]
 
     @classmethod
     def from_arrays(cls, desc, payload, grids, total_tris, total_verts, max_block_words,
-                    max_tris=256, device="cuda"):
+                    max_tris=256, device="cuda", cones=None):
         """Wrap blob arrays that did not come from ``mc_encode`` (e.g. a
-        hand-packed stream); sizes are the caller's."""
+        hand-packed stream); sizes are the caller's; cones (uint8 [M,32])
+        optional."""
         self = cls.__new__(cls)
         stats = {"n_meshlets": desc.shape[0], "n_grids": grids.shape[0],
                  "payload_bytes": payload.size, "total_tris": total_tris,
                  "total_verts": total_verts, "max_block_words": max_block_words,
                  "max_tris": max_tris}
         self._init(np.asarray(desc, np.uint8), np.asarray(payload, np.uint8),
-                   np.asarray(grids, np.uint8), stats, device)
+                   np.asarray(grids, np.uint8), stats, device,
+                   None if cones is None else np.asarray(cones, np.uint8))
         self.meshes = []
         return self
 
-    def _init(self, desc, payload, grids, stats, device):
+    def _init(self, desc, payload, grids, stats, device, cones=None):
         import torch
         self.stats = stats
         self.desc = torch.from_numpy(np.ascontiguousarray(desc).reshape(-1)).to(device)
         self.payload = torch.from_numpy(np.ascontiguousarray(payload) if payload.size
                                         else np.zeros(16, np.uint8)).to(device)
         self.grids = torch.from_numpy(np.ascontiguousarray(grids).reshape(-1)).to(device)
+        self.cones = None if cones is None or cones.size == 0 else \
+            torch.from_numpy(np.ascontiguousarray(cones).reshape(-1)).to(device)
         s = self.stats
         self.c = mc_device_batch(self.desc.data_ptr(), self.payload.data_ptr(), self.grids.data_ptr(),
                                  s["n_meshlets"], s["n_grids"], s["payload_bytes"], s["total_tris"],
                                  s["total_verts"], max(1, s["max_block_words"]),
-                                 s.get("max_tris", 256))
+                                 s.get("max_tris", 256),
+                                 None if self.cones is None else self.cones.data_ptr())
 
     def outputs(self, local=True, global_=True, device="cuda"):
         import torch

@@ -55,6 +55,7 @@ mc_status check_batch(const mc_device_batch *b) {
   if (b->n_grids == 0 || b->n_grids > 65536) return MC_ERR_INVALID_ARG;
   if (b->max_block_words == 0 || b->max_block_words > 2 * 8 + 64 + 768 + 4) return MC_ERR_INVALID_ARG;
   if (b->payload_bytes % 16) return MC_ERR_INVALID_ARG;
+  if (b->cones && !aligned(b->cones, 16)) return MC_ERR_INVALID_ARG;
   return MC_OK;
 }
 
@@ -231,8 +232,8 @@ mc_status launch_cull_checked(const mc_device_batch *b, const float *d_vp, uint3
   uint32_t per_sm = (t && t->ctas_per_sm) ? std::min<uint32_t>(t->ctas_per_sm, occ) : (uint32_t)occ;
   uint32_t ctas = per_sm * (uint32_t)sm_count();
   if (ctas == 0) return MC_ERR_CUDA;
-  cudaError_t e = launch_cull(a, d_vp, ctas, warps, grab, t && t->checked, d_tri_out, d_tri_count,
-                              d_pos, d_status, static_cast<uint32_t *>(d_scratch), s);
+  cudaError_t e = launch_cull(a, d_vp, b->cones, ctas, warps, grab, t && t->checked, d_tri_out,
+                              d_tri_count, d_pos, d_status, static_cast<uint32_t *>(d_scratch), s);
   if (e == cudaSuccess) g_launches++;
   return from_cuda(e);
 }

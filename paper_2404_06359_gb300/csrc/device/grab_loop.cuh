@@ -70,14 +70,17 @@ __host__ __device__ inline uint32_t grab_loop_bytes(uint32_t max_block_words, ui
   return 32 * (per_grab + 1) + 16 + 4 * (per_grab * ((max_block_words + 3) & ~3u) + kSlackWords);
 }
 
-// Runs the warp's share of the work queue.  Per grab, pre(sdesc, cnt) is
-// called by all lanes once the grab's cnt descriptors are in shared memory
-// (sdesc, 8 words each, not yet validated) and returns a warp-uniform word;
+// Runs the warp's share of the work queue.  Per grab, pre(m0, sdesc, cnt) is
+// called by all lanes once the descriptors of the grab's cnt meshlets
+// m0 .. m0 + cnt - 1 are in shared memory (sdesc, 8 words each, not yet
+// validated) and returns a warp-uniform word;
 // body(d, sw, j, word) is then called by all lanes for every meshlet j of the
 // grab whose header passes header_ok, with sw its payload block in shared
 // memory; a failed header sets MC_ERR_CORRUPT.
 struct NoPre {
-  __device__ __forceinline__ uint32_t operator()(const uint32_t *, uint32_t) const { return 0; }
+  __device__ __forceinline__ uint32_t operator()(uint32_t, const uint32_t *, uint32_t) const {
+    return 0;
+  }
 };
 template <class Pre, class Body>
 __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab, uint8_t *wbase,
@@ -128,7 +131,7 @@ __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab,
       }
       parity ^= 1u;
     }
-    const uint32_t word = pre(sdesc, cnt);
+    const uint32_t word = pre(m0, sdesc, cnt);
     for (uint32_t j = 0; j < cnt; j++) {
       const uint4 *sd = reinterpret_cast<const uint4 *>(sdesc) + 2 * j;
       const Desc d = unpack_desc(sd[0], sd[1]);

@@ -169,19 +169,72 @@ __device__ __forceinline__ float clip_row(const float *M, int r, float x, float 
   return __fmaf_rn(M[4 * r + 2], z, __fmaf_rn(M[4 * r + 1], y, __fmaf_rn(M[4 * r + 0], x, M[4 * r + 3])));
 }
 
-// Frustum test of a grab's meshlets: bit j of the result is set when all 8
-// corners of meshlet j's quantisation box [L, L + 2^b - 1] (dequantised like
-// the vertices) are outside one clip plane.  Lane 8 i + c takes corner c of
+// Camera position of a clip matrix M (row-major, in shared memory): the point
+// whose clip x, y and w are zero, from rows r0, r1, r3 and b_i = -M[i][3] by
+// the cross-product inverse in FP64,
+//   e = (b0 (r1 x r3) + b1 (r3 x r0) + b3 (r0 x r1)) / (r0 . (r1 x r3)),
+// rounded to FP32.  Returns false (no camera: affine projection) when the
+// determinant is 0 or not finite, or a coordinate is not finite.
+__device__ bool view_eye(const float *M, float *eye) {
+  double r0[3], r1[3], r3[3];
+  for (int c = 0; c < 3; c++) {
+    r0[c] = M[c];
+    r1[c] = M[4 + c];
+    r3[c] = M[12 + c];
+  }
+  const double b0 = -(double)M[3], b1 = -(double)M[7], b3 = -(double)M[15];
+  auto cross = [](const double *u, const double *v, double *w) {
+    w[0] = __dsub_rn(__dmul_rn(u[1], v[2]), __dmul_rn(u[2], v[1]));
+    w[1] = __dsub_rn(__dmul_rn(u[2], v[0]), __dmul_rn(u[0], v[2]));
+    w[2] = __dsub_rn(__dmul_rn(u[0], v[1]), __dmul_rn(u[1], v[0]));
+  };
+  double k0[3], k1[3], k3[3];
+  cross(r1, r3, k0);
+  cross(r3, r0, k1);
+  cross(r0, r1, k3);
+  const double det =
+      __dadd_rn(__dadd_rn(__dmul_rn(r0[0], k0[0]), __dmul_rn(r0[1], k0[1])), __dmul_rn(r0[2], k0[2]));
+  if (!(det != 0.0) || !isfinite(det)) return false;
+  for (int c = 0; c < 3; c++) {
+    const double num =
+        __dadd_rn(__dadd_rn(__dmul_rn(b0, k0[c]), __dmul_rn(b1, k1[c])), __dmul_rn(b3, k3[c]));
+    const double e = __ddiv_rn(num, det);
+    if (!isfinite(e)) return false;
+    eye[c] = __double2float_rn(e);
+  }
+  return true;
+}
+
+// Normal-cone test (mc_cone) of one meshlet for a camera at eye: true when
+// axis . v >= s |v| + radius with v = center - eye, in FP32 with a fixed
+// operation order.
+__device__ __forceinline__ bool cone_faces_away(const mc_cone *cone, const float *eye) {
+  const float4 *p = reinterpret_cast<const float4 *>(cone);
+  const float4 c0 = __ldg(p), c1 = __ldg(p + 1);  // center, radius / axis, s
+  const float vx = __fsub_rn(c0.x, eye[0]), vy = __fsub_rn(c0.y, eye[1]), vz = __fsub_rn(c0.z, eye[2]);
+  const float d = __fmaf_rn(c1.z, vz, __fmaf_rn(c1.y, vy, __fmul_rn(c1.x, vx)));
+  const float l = __fsqrt_rn(__fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx))));
+  return (c1.w < 1.0f) & (d >= __fmaf_rn(c1.w, l, c0.w));
+}
+
+// Meshlet tests of a grab: bit j of the result is set when all 8 corners of
+// meshlet j's quantisation box [L, L + 2^b - 1] (dequantised like the
+// vertices) are outside one clip plane, or when cones is set, eye_ok and the
+// meshlet's normal cone faces away from eye.  Lane 8 i + c takes corner c of
 // meshlet 4 p + i in pass p and collects the planes the corner is outside
-// of; the eight lanes of a meshlet AND their plane masks.  A descriptor with
-// an out-of-range grid index gets no bit (its header check rejects it).
-__device__ __forceinline__ uint32_t grab_outside(const BatchArgs &a, const uint32_t *sdesc,
-                                                 uint32_t cnt, const float *M, uint32_t lane) {
+// of; the eight lanes of a meshlet AND their plane masks; lane 8 i runs the
+// cone test.  A descriptor with an out-of-range grid index gets no bit (its
+// header check rejects it).
+__device__ __forceinline__ uint32_t grab_outside(const BatchArgs &a, uint32_t m0,
+                                                 const uint32_t *sdesc, uint32_t cnt,
+                                                 const float *M, const mc_cone *cones,
+                                                 const float *eye, bool eye_ok, uint32_t lane) {
   uint32_t out = 0;
   const uint32_t corner = lane & 7u;
   for (uint32_t p = 0; 4 * p < cnt; p++) {
     const uint32_t j = 4 * p + (lane >> 3);
     uint32_t mask = 0;
+    bool away = false;
     if (j < cnt) {
       const uint32_t *w = sdesc + 8 * j;
       const uint32_t b = (w[4] >> 8) & 0xFFu, grid = w[4] >> 16;
@@ -202,11 +255,12 @@ __device__ __forceinline__ uint32_t grab_outside(const BatchArgs &a, const uint3
           mask |= (__fsub_rn(cw, comp) < 0.0f ? 2u : 0u) << (2 * r);
         }
       }
+      if (cones && eye_ok && corner == 0) away = cone_faces_away(cones + m0 + j, eye);
     }
     mask &= __shfl_xor_sync(kFull, mask, 1);
     mask &= __shfl_xor_sync(kFull, mask, 2);
     mask &= __shfl_xor_sync(kFull, mask, 4);
-    const uint32_t bal = __ballot_sync(kFull, mask != 0 && corner == 0);
+    const uint32_t bal = __ballot_sync(kFull, (mask != 0 || away) && corner == 0);
     out |= ((bal & 1u) | ((bal >> 7) & 2u) | ((bal >> 14) & 4u) | ((bal >> 21) & 8u)) << (4 * p);
   }
   return out;
@@ -332,11 +386,13 @@ __device__ __forceinline__ void cull_flush(const uint32_t *surv, const uint32_t 
 // one atomicAdd.
 template <bool CHECKED, int MAX_THREADS>
 __global__ void __launch_bounds__(MAX_THREADS) decode_cull_kernel(BatchArgs a, const float *view_proj,
-                                                          uint32_t per_grab, uint32_t *tri_out,
-                                                          uint32_t *tri_count, float *out_pos,
-                                                          uint32_t *status, uint32_t *scratch) {
+                                                          const mc_cone *cones, uint32_t per_grab,
+                                                          uint32_t *tri_out, uint32_t *tri_count,
+                                                          float *out_pos, uint32_t *status,
+                                                          uint32_t *scratch) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ float s_M[16];
+  __shared__ float s_eye[4];  // camera position, [3] = 1 when there is one
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const CullLayout L = cull_layout(a.max_block_words, a.max_tris, per_grab);
   uint8_t *base = smem + warp * L.bytes;
@@ -348,9 +404,12 @@ __global__ void __launch_bounds__(MAX_THREADS) decode_cull_kernel(BatchArgs a, c
   uint32_t n_keep = 0, n_src = 0;  // buffered survivors, meshlets they reference
   if (threadIdx.x < 16) s_M[threadIdx.x] = view_proj[threadIdx.x];
   __syncthreads();
+  if (threadIdx.x == 0) s_eye[3] = cones && view_eye(s_M, s_eye) ? 1.0f : 0.0f;
+  __syncthreads();
+  const bool eye_ok = s_eye[3] != 0.0f;
   grab_loop(a, per_grab, base, lane, scratch + kQueue, status,
-                [&](const uint32_t *sdesc, uint32_t cnt) {
-                  return grab_outside(a, sdesc, cnt, s_M, lane);
+                [&](uint32_t m0, const uint32_t *sdesc, uint32_t cnt) {
+                  return grab_outside(a, m0, sdesc, cnt, s_M, cones, s_eye, eye_ok, lane);
                 },
                 [&](const Desc &d, const uint32_t *sw, uint32_t j, uint32_t outside) {
                   if ((outside >> j) & 1u) return;
@@ -490,30 +549,32 @@ namespace {
 // Small CTAs (up to 4 warps) get a build whose register budget needs no
 // spills; larger CTAs the 512-thread build.
 template <int MAX_THREADS>
-cudaError_t launch_cull_t(const BatchArgs &a, const float *view_proj, uint32_t ctas, uint32_t warps,
-                          uint32_t per_grab, bool checked, uint32_t *tri_out, uint32_t *tri_count,
-                          float *out_pos, uint32_t *status, uint32_t *scratch, cudaStream_t s) {
+cudaError_t launch_cull_t(const BatchArgs &a, const float *view_proj, const mc_cone *cones,
+                          uint32_t ctas, uint32_t warps, uint32_t per_grab, bool checked,
+                          uint32_t *tri_out, uint32_t *tri_count, float *out_pos, uint32_t *status,
+                          uint32_t *scratch, cudaStream_t s) {
   const uint32_t smem = cull_smem_per_warp(a.max_block_words, a.max_tris, per_grab) * warps;
   if (checked) {
     prepare(fn(decode_cull_kernel<true, MAX_THREADS>));
     decode_cull_kernel<true, MAX_THREADS><<<ctas, warps * 32, smem, s>>>(
-        a, view_proj, per_grab, tri_out, tri_count, out_pos, status, scratch);
+        a, view_proj, cones, per_grab, tri_out, tri_count, out_pos, status, scratch);
   } else {
     prepare(fn(decode_cull_kernel<false, MAX_THREADS>));
     decode_cull_kernel<false, MAX_THREADS><<<ctas, warps * 32, smem, s>>>(
-        a, view_proj, per_grab, tri_out, tri_count, out_pos, status, scratch);
+        a, view_proj, cones, per_grab, tri_out, tri_count, out_pos, status, scratch);
   }
   return cudaGetLastError();
 }
 }  // namespace
 
-cudaError_t launch_cull(const BatchArgs &a, const float *view_proj, uint32_t ctas, uint32_t warps,
-                        uint32_t per_grab, bool checked, uint32_t *tri_out, uint32_t *tri_count,
-                        float *out_pos, uint32_t *status, uint32_t *scratch, cudaStream_t s) {
+cudaError_t launch_cull(const BatchArgs &a, const float *view_proj, const mc_cone *cones,
+                        uint32_t ctas, uint32_t warps, uint32_t per_grab, bool checked,
+                        uint32_t *tri_out, uint32_t *tri_count, float *out_pos, uint32_t *status,
+                        uint32_t *scratch, cudaStream_t s) {
   if (warps <= 4)
-    return launch_cull_t<128>(a, view_proj, ctas, warps, per_grab, checked, tri_out, tri_count,
-                              out_pos, status, scratch, s);
-  return launch_cull_t<512>(a, view_proj, ctas, warps, per_grab, checked, tri_out, tri_count,
+    return launch_cull_t<128>(a, view_proj, cones, ctas, warps, per_grab, checked, tri_out,
+                              tri_count, out_pos, status, scratch, s);
+  return launch_cull_t<512>(a, view_proj, cones, ctas, warps, per_grab, checked, tri_out, tri_count,
                             out_pos, status, scratch, s);
 }
 

@@ -55,6 +55,72 @@ float round_up_float(double d) {
   return f;
 }
 
+// FP32 position of grid coordinate g (the dequantisation of Sec. 4.4, as the
+// decoder evaluates it)
+float grid_to_float(uint32_t g, float G, float D) {
+  if (g < (1u << 24)) return std::fma((float)g, D, G);
+  return std::fma((float)(g & 0xFFFu), D, std::fma((float)(g >> 12), D * 4096.0f, G));
+}
+
+// Normal cone of one meshlet (mc_cone) from its decoded positions P (V
+// vertices) and its triangles in local ids tl (nt of them, input winding).
+mc_cone meshlet_cone(const float *P, uint32_t V, const uint32_t *tl, uint32_t nt) {
+  mc_cone k{};
+  double lo[3], hi[3];
+  for (int c = 0; c < 3; c++) lo[c] = hi[c] = P[c];
+  for (uint32_t v = 1; v < V; v++)
+    for (int c = 0; c < 3; c++) {
+      const double x = P[3 * v + c];
+      lo[c] = x < lo[c] ? x : lo[c];
+      hi[c] = x > hi[c] ? x : hi[c];
+    }
+  for (int c = 0; c < 3; c++) k.center[c] = (float)((lo[c] + hi[c]) * 0.5);
+  double r = 0.0;
+  for (uint32_t v = 0; v < V; v++) {
+    const double dx = (double)P[3 * v] - (double)k.center[0];
+    const double dy = (double)P[3 * v + 1] - (double)k.center[1];
+    const double dz = (double)P[3 * v + 2] - (double)k.center[2];
+    const double d = std::sqrt(dx * dx + dy * dy + dz * dz);
+    if (d > r) r = d;
+  }
+  k.radius = round_up_float(r * (1.0 + std::ldexp(1.0, -20)));
+  double nrm[256][3], sum[3] = {0.0, 0.0, 0.0};
+  uint32_t cnt = 0;
+  for (uint32_t t = 0; t < nt; t++) {
+    const float *a = P + 3 * tl[3 * t], *b = P + 3 * tl[3 * t + 1], *c = P + 3 * tl[3 * t + 2];
+    const double u0 = (double)b[0] - (double)a[0], u1 = (double)b[1] - (double)a[1],
+                 u2 = (double)b[2] - (double)a[2];
+    const double w0 = (double)c[0] - (double)a[0], w1 = (double)c[1] - (double)a[1],
+                 w2 = (double)c[2] - (double)a[2];
+    const double x = u1 * w2 - u2 * w1, y = u2 * w0 - u0 * w2, z = u0 * w1 - u1 * w0;
+    const double len = std::sqrt(x * x + y * y + z * z);
+    if (!(len > 0.0)) continue;
+    nrm[cnt][0] = x / len;
+    nrm[cnt][1] = y / len;
+    nrm[cnt][2] = z / len;
+    for (int i = 0; i < 3; i++) sum[i] += nrm[cnt][i];
+    cnt++;
+  }
+  k.axis[0] = 0.0f;
+  k.axis[1] = 0.0f;
+  k.axis[2] = 1.0f;
+  k.s = 1.0f;
+  const double sl = std::sqrt(sum[0] * sum[0] + sum[1] * sum[1] + sum[2] * sum[2]);
+  if (cnt == 0 || !(sl > 0.0)) return k;
+  const double ax[3] = {sum[0] / sl, sum[1] / sl, sum[2] / sl};
+  double cmin = 1.0;
+  for (uint32_t t = 0; t < cnt; t++) {
+    const double d = nrm[t][0] * ax[0] + nrm[t][1] * ax[1] + nrm[t][2] * ax[2];
+    cmin = d < cmin ? d : cmin;
+  }
+  for (int i = 0; i < 3; i++) k.axis[i] = (float)ax[i];
+  if (cmin > 0.0) {
+    const double sn = std::sqrt(1.0 - cmin * cmin) + std::ldexp(1.0, -20);
+    if (sn < 1.0) k.s = std::min(1.0f, round_up_float(sn));
+  }
+  return k;
+}
+
 }  // namespace
 
 extern "C" mc_status mc_encode(const mc_meshlets *m, const float *pos, uint32_t n_verts,
@@ -212,6 +278,7 @@ extern "C" mc_status mc_encode(const mc_meshlets *m, const float *pos, uint32_t 
     }
     blob->payload.assign(off[nm] * 4, 0);
     blob->vmap.resize(vb[nm]);
+    blob->cones.resize(nm);
     uint32_t *words = reinterpret_cast<uint32_t *>(blob->payload.data());
     parallel_for(
         nm, threads,
@@ -226,13 +293,26 @@ extern "C" mc_status mc_encode(const mc_meshlets *m, const float *pos, uint32_t 
           uint32_t *rw = w + 2 * nw;
           for (uint32_t r = 0; r < x.R; r++) put_bits(rw, (uint64_t)r * x.w, x.w, x.reuse[r]);
           uint32_t *pw = rw + (x.R * x.w + 31) / 32;
+          float P[3 * 256];  // decoded positions, for the normal cone
           for (uint32_t v = 0; v < x.V; v++)
             for (int c = 0; c < 3; c++) {
               double y = ((double)pos[3 * (size_t)x.gv[v] + c] - (double)G[c]) /
                          (double)delta[x.b][c];
               uint32_t q = (uint32_t)(std::floor(y + 0.5) - (double)x.L[c]);
               put_bits(pw, (3 * (uint64_t)v + c) * x.b, x.b, q);
+              P[3 * v + c] = grid_to_float(x.L[c] + q, G[c], delta[x.b][c]);
             }
+          {
+            // the meshlet's input triangles in local ids (vertex -> local id
+            // through a per-thread table over the mesh's vertices)
+            thread_local std::vector<uint16_t> local_of;
+            if (local_of.size() < n_verts) local_of.resize(n_verts);
+            for (uint32_t v = 0; v < x.V; v++) local_of[x.gv[v]] = (uint16_t)v;
+            const uint32_t mi = slot[s], t0 = m->start[mi], nt = m->start[mi + 1] - t0;
+            uint32_t tl[3 * 256];
+            for (uint32_t i = 0; i < 3 * nt; i++) tl[i] = local_of[m->corners[3 * (size_t)t0 + i]];
+            blob->cones[s] = meshlet_cone(P, x.V, tl, nt);
+          }
           mc_desc &d = blob->desc[s];
           d.payload_off16 = (uint32_t)(off[s] / 4);
           d.vertex_base = (uint32_t)vb[s];
@@ -310,6 +390,7 @@ extern "C" mc_status mc_blob_concat(const mc_blob *const *blobs, uint32_t n, mc_
     b->payload.reserve(pay);
     b->grids.reserve(ng);
     b->vmap.reserve(nv);
+    b->cones.reserve(nm);
     uint64_t o16 = 0, vb = 0, tb = 0, gb = 0, mb = 0;
     for (uint32_t i = 0; i < n; i++) {
       const mc_blob *s = blobs[i];
@@ -332,6 +413,7 @@ extern "C" mc_status mc_blob_concat(const mc_blob *const *blobs, uint32_t n, mc_
         b->meshes.push_back(mi);
       }
       b->vmap.insert(b->vmap.end(), s->vmap.begin(), s->vmap.end());
+      b->cones.insert(b->cones.end(), s->cones.begin(), s->cones.end());
       o16 += s->payload.size() / 16;
       vb += s->total_verts;
       tb += s->total_tris;
@@ -376,6 +458,7 @@ extern "C" mc_status mc_blob_view(const mc_blob *b, mc_blob_view_t *v) {
   v->pos_bits_total = b->pos_bits_total;
   v->max_block_words = b->max_block_words;
   v->max_tris = b->max_tris;
+  v->cones = b->cones.data();
   return MC_OK;
 }
 

@@ -44,6 +44,7 @@ struct mc_meshlets {
   uint32_t n_tris = 0, n_verts = 0;
   uint32_t n_grown = 0;
   std::vector<uint32_t> tri;          // triangle ids grouped by meshlet
+  std::vector<uint32_t> corners;      // their 3 vertex ids each (input winding), same order
   std::vector<uint32_t> start;        // meshlet offsets into tri (count + 1)
   std::vector<uint64_t> stream_start; // meshlet offsets into stream (count + 1)
   std::vector<uint32_t> stream;       // strip entries (global vertex ids)
@@ -58,6 +59,7 @@ struct mc_blob {
   std::vector<mc_grid> grids;
   std::vector<mc_mesh_info> meshes;
   std::vector<uint32_t> vmap;
+  std::vector<mc_cone> cones;
   uint64_t total_tris = 0, total_verts = 0, input_tris = 0;
   uint64_t restarts = 0, split_meshlets = 0, conn_bits = 0, pos_bits_total = 0;
   uint32_t max_block_words = 0, max_tris = 0;

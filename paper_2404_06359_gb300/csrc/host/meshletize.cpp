@@ -309,6 +309,9 @@ extern "C" mc_status mc_meshletize(const uint32_t *tri_idx, uint32_t n_tris, uin
       }
     m->start.push_back((uint32_t)m->tri.size());
     m->stream_start.push_back(m->stream.size());
+    m->corners.resize(3 * (size_t)m->tri.size());
+    for (size_t i = 0; i < m->tri.size(); i++)
+      for (int c = 0; c < 3; c++) m->corners[3 * i + c] = tri_idx[3 * (size_t)m->tri[i] + c];
   } catch (const std::bad_alloc &) {
     delete m;
     return MC_ERR_OOM;

@@ -24,10 +24,10 @@ def max_tris(desc: np.ndarray) -> int:
     return int((w[:, 3] >> 16).max()) if w.shape[0] else 1
 
 
-def device_batch_from_oracle(blob: O.Blob) -> mc.DeviceBatch:
+def device_batch_from_oracle(blob: O.Blob, cones: bool = False) -> mc.DeviceBatch:
     return mc.DeviceBatch.from_arrays(blob.desc, blob.payload, blob.grids, blob.total_tris,
                                       blob.total_verts, block_words_max(blob.desc),
-                                      max_tris(blob.desc))
+                                      max_tris(blob.desc), cones=blob.cones if cones else None)
 
 
 def run_decode(db: mc.DeviceBatch, mode="batch", tuning=None, local=True, global_=True):

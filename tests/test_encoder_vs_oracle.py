@@ -59,6 +59,7 @@ def test_blob_bytes_identical(both):
     assert a["payload"].size == ob.payload.size
     assert np.array_equal(a["payload"], ob.payload)
     assert np.array_equal(a["vertex_map"], ob.stats["vmap"])
+    assert np.array_equal(a["cones"], ob.cones)
     s = blob.stats()
     assert s["restarts"] == ob.stats["restarts"]
     assert s["conn_bits"] == ob.stats["conn_bits"]
@@ -81,6 +82,7 @@ def test_concat_matches_oracle_concat():
     assert np.array_equal(a["desc"], ocat.desc)
     assert np.array_equal(a["payload"], ocat.payload)
     assert np.array_equal(a["grids"], ocat.grids)
+    assert np.array_equal(a["cones"], ocat.cones)
     meshes_t = a["meshes"]
     assert [x["n_meshlets"] for x in meshes_t] == [b.n_meshlets for b in oblobs]
     assert meshes_t[1]["first_meshlet"] == oblobs[0].n_meshlets

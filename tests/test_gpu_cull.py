@@ -1,7 +1,8 @@
 """GPU parity of the fused decode + cull + compaction kernel against the
-oracle's sequential decode_cull: the surviving triangles are the same
-multiset (their order across warps is not fixed), the count is exact and the
-positions of meshlets that pass the frustum test match to 0 ulp."""
+oracle's sequential decode_cull, without and with the normal-cone meshlet
+test: the surviving triangles are the same multiset (their order across
+warps is not fixed), the count is exact and the positions of meshlets that
+pass the meshlet tests match to 0 ulp."""
 import numpy as np
 import pytest
 
@@ -113,3 +114,78 @@ def test_cull_small_meshlets_generic_path(tuning):
         vm = np.repeat(passed, f["V"].astype(np.int64)).astype(bool)
         assert np.array_equal(pos.reshape(-1, 3)[vm].view(np.uint32), ref_pos[vm].view(np.uint32))
     torch.cuda.synchronize()
+
+
+@pytest.fixture(scope="module")
+def smooth_scene():
+    """Noise-free spheres and tori: narrow normal cones, so the cone test
+    drops a large share of the meshlets."""
+    rng = np.random.Generator(np.random.PCG64(31))
+    meshes = []
+    for i in range(12):
+        c = (3.0 * (i % 3), 3.0 * ((i // 3) % 2), 3.0 * (i // 6))
+        t = int(rng.integers(5_000, 40_000))
+        meshes.append(G.uv_sphere(t, rng, noise=0.0, center=c) if i % 2 == 0
+                      else G.torus(t, rng, noise=0.0, center=c))
+    blob = O.concat([O.encode_mesh(m, (64, 126), 16, 0, mesh_id=i) for i, m in enumerate(meshes)])
+    pts = np.concatenate([m.pos for m in meshes])
+    c = 0.5 * (pts.min(0) + pts.max(0))
+    r = float(np.linalg.norm(pts - c, axis=1).max())
+    return blob, G.camera_poses(5, c, r, seed=32, distance=2.0)
+
+
+@pytest.mark.parametrize("tuning", [None, {"warps_per_cta": 8, "meshlets_per_grab": 16},
+                                    {"warps_per_cta": 4, "meshlets_per_grab": 3, "checked": 1}])
+@pytest.mark.parametrize("which", ["scene", "smooth_scene"])
+def test_cull_with_cones_vs_oracle(request, which, tuning):
+    blob, vps = request.getfixturevalue(which)
+    db = device_batch_from_oracle(blob, cones=True)
+    f = blob.fields()
+    rejected = 0
+    for vp in vps:
+        ref_tri, ref_pos, passed = O.decode_cull(blob, vp, cones=blob.cones)
+        _, _, passed_plain = O.decode_cull(blob, vp)
+        tri, pos, st = _run(db, vp, tuning)
+        assert st == 0
+        assert np.array_equal(_sorted_rows(tri), _sorted_rows(ref_tri))
+        vm = np.repeat(passed, f["V"].astype(np.int64)).astype(bool)
+        assert np.array_equal(pos.reshape(-1, 3)[vm].view(np.uint32), ref_pos[vm].view(np.uint32))
+        rejected += int((passed_plain.astype(bool) & ~passed.astype(bool)).sum())
+    if which == "smooth_scene":  # the cone test did drop meshlets here
+        assert rejected > 0.2 * blob.n_meshlets * len(vps)
+
+
+def test_cull_cones_ignored_without_a_camera(smooth_scene):
+    """An affine projection has no camera position: the cone test is off and
+    the result equals the cone-free cull."""
+    blob, _ = smooth_scene
+    pts_lo = blob.grids.view(np.float32).reshape(-1, 8)[:, :3].min(0)
+    vp = np.eye(4, dtype=np.float32) * np.float32(0.02)
+    vp[3, 3] = 1.0
+    vp[:3, 3] = -0.02 * (pts_lo + 4.0)
+    assert O.view_eye(vp) is None
+    db = device_batch_from_oracle(blob, cones=True)
+    ref_tri, _, _ = O.decode_cull(blob, vp)
+    tri, _, st = _run(db, vp)
+    assert st == 0 and np.array_equal(_sorted_rows(tri), _sorted_rows(ref_tri))
+
+
+def test_cull_graph_many_views_with_cones(smooth_scene):
+    import torch
+    blob, vps = smooth_scene
+    db = device_batch_from_oracle(blob, cones=True)
+    T, V = db.stats["total_tris"], db.stats["total_verts"]
+    tri = torch.zeros(3 * T + 3, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(len(vps), dtype=torch.int32, device="cuda")
+    pos = torch.zeros(3 * V, dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    scratch = mc.new_scratch()
+    d_vps = torch.from_numpy(np.ascontiguousarray(vps, np.float32)).cuda()
+    g = mc.mc_graph_capture_cull(db, d_vps, len(vps), tri, cnt, pos, st, scratch)
+    g.launch()
+    torch.cuda.synchronize()
+    counts = cnt.cpu().numpy()
+    for i, vp in enumerate(vps):
+        ref_tri, _, _ = O.decode_cull(blob, vp, cones=blob.cones)
+        assert counts[i] == ref_tri.shape[0]
+    assert int(st.item()) == 0 and int(scratch.abs().sum()) == 0
