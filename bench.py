@@ -35,7 +35,7 @@ WORKLOADS = {
        "64/126, b=16, w=8, u8 local + u32 global + f32 positions, one persistent launch (CUDA graph)",
     3: "cfg3: 50M-triangle disc height field, 3 sectors at 64/126, 128/128, 256/256, w=ceil(log2 V), "
        "b in {12,16,20} per meshlet, shuffled, u8 + u32 + f32, one persistent launch (CUDA graph)",
-    4: "cfg4: cfg2 generator grown to >=50M triangles, fused decode + frustum/back-face cull + "
+    4: "cfg4: cfg2 generator grown to >=50M triangles, fused decode + frustum/normal-cone/back-face cull + "
        "compaction, 64 camera poses, one CUDA graph",
     5: "cfg5: serving loop, Poisson arrivals (2000 meshes/s) over a resident pool of seeded "
        "spheres/tori/height fields (1k-2M triangles, mixed meshlet limits), 8 GB output budget, "
@@ -192,9 +192,9 @@ def build_workload(cfg: int, rank: int):
 
 def cpu_oracle_baseline(blob, budget_s: float = 10.0, vp=None):
     """The oracle's sequential C decode (or, given a view-projection matrix,
-    its fused decode + cull for that view) in one call over a prefix of the
-    batch, sized from a short probe to take about ``budget_s``, on one host
-    core."""
+    its fused decode + normal-cone/frustum/back-face cull for that view) in
+    one call over a prefix of the batch, sized from a short probe to take
+    about ``budget_s``, on one host core."""
     import oracle as O
     a = blob.arrays()
     ob = O.Blob(a["desc"], a["payload"], a["grids"])
@@ -203,7 +203,7 @@ def cpu_oracle_baseline(blob, budget_s: float = 10.0, vp=None):
     def run(count):
         if vp is None:
             return O.decode(ob, 0, count, want_pos64=False)
-        return O.decode_cull(ob, vp, 0, count)
+        return O.decode_cull(ob, vp, 0, count, cones=a["cones"])
 
     t0 = time.perf_counter()
     run(min(n, 2000))
@@ -218,7 +218,8 @@ def cpu_oracle_baseline(blob, budget_s: float = 10.0, vp=None):
     end = int(f["tri_base"][count - 1]) + int(f["Tp"][count - 1])
     t = loc[:end].astype(np.int16)
     tris = int(((t[:, 0] != t[:, 1]) & (t[:, 1] != t[:, 2]) & (t[:, 0] != t[:, 2])).sum())
-    what = "decode + FP32 dequant" if vp is None else "decode + frustum/back-face cull + compaction, one view"
+    what = "decode + FP32 dequant" if vp is None else \
+        "decode + frustum/normal-cone/back-face cull + compaction, one view"
     return {"value": tris / dt / 1e9, "unit": "Gtps", "cores": 1, "kind": "oracle",
             "sample": f"first {count} of {n} meshlets ({tris} input triangles) of the same batch, "
                       f"sequential C {what} in one call, {dt:.2f} s, 1 thread"}
@@ -319,7 +320,7 @@ def main():
     blob, meshes, vps = build_workload(args.config, rank)
     t_build = time.time() - t_build
     stats = blob.stats()
-    db = mc.DeviceBatch(blob, "cuda")
+    db = mc.DeviceBatch(blob, "cuda", cones=args.config == 4)  # cfg4: normal-cone meshlet test on
     arrays = blob.arrays()
     input_tris = stats["input_tris"]
     stream = torch.cuda.Stream()
@@ -449,7 +450,30 @@ def main():
     bytes_per_launch = nbytes["total"] if not cull else None
     if cull:
         counts_np = counts.cpu().numpy().astype(np.int64)
-        bytes_per_launch = W.cull_bytes(stats, arrays, vps, counts_np)
+        bytes_per_launch = W.cull_bytes(stats, arrays, vps, counts_np, cones=True)
+        # the same step without the normal-cone test (frustum + per-triangle only)
+        db_nc = mc.DeviceBatch(blob, "cuda")
+        with torch.cuda.stream(stream):
+            g_nc = mc.mc_graph_capture_cull(db_nc, d_vps, len(vps), tri, counts, out["pos"],
+                                            out["status"], scratch, tune, stream)
+            nc_t = []
+            for i in range(3 + max(3, args.steps // 10)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g_nc.launch(stream)
+                e1.record(stream)
+                flush.zero_()
+                if i >= 3:
+                    nc_t.append((e0, e1))
+            torch.cuda.synchronize()
+        nc_ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in nc_t]))
+        assert int(out["status"].item()) == 0
+        counts_nc = counts.cpu().numpy().astype(np.int64)
+        extra["cull_without_cones"] = {
+            "value": round(input_tris * len(vps) / (nc_ms * 1e-3) / 1e9, 3), "unit": "Gtps",
+            "ms_per_step": round(nc_ms, 5),
+            "kept_fraction_mean": float(counts_nc.mean() / input_tris),
+            "algorithmic_bytes_per_launch": W.cull_bytes(stats, arrays, vps, counts_nc)}
     roof = None
     if bytes_per_launch:
         ach = bytes_per_launch / per_launch_s / 1e9

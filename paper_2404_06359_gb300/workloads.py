@@ -10,8 +10,9 @@
         w = ceil(log2 V); b drawn from {12, 16, 20} per meshlet; meshlets
         shuffled; one persistent launch.
   cfg4  cfg2's generator grown to >= 50 M triangles on a 3-D lattice, fused
-        decode + frustum/back-face cull + compaction under 64 camera poses
-        (60 degree FOV), one CUDA graph.
+        decode + per-meshlet frustum / normal-cone and per-triangle back-face
+        cull + compaction under 64 camera poses (60 degree FOV), one CUDA
+        graph.
 All inputs are seeded; see meshgen for the recipes.
 """
 from __future__ import annotations
@@ -91,11 +92,23 @@ def algorithmic_bytes(stats: dict, desc: np.ndarray, local=True, global_=True) -
             "padding": 4 * int(((words + 3) // 4 * 4 - words).sum())}
 
 
-def cull_bytes(stats: dict, arrays: dict, vps: np.ndarray, counts: np.ndarray) -> int:
+def _eye64(vp: np.ndarray):
+    """Camera position of a clip matrix (the point with clip x = y = w = 0),
+    FP64, or None for an affine projection."""
+    m = np.asarray(vp, np.float64).reshape(4, 4)
+    a = m[[0, 1, 3], :3]
+    if abs(np.linalg.det(a)) == 0.0:
+        return None
+    return np.linalg.solve(a, -m[[0, 1, 3], 3])
+
+
+def cull_bytes(stats: dict, arrays: dict, vps: np.ndarray, counts: np.ndarray,
+               cones: bool = False) -> int:
     """Mean algorithmic bytes of one fused decode+cull launch: every descriptor
-    and grid entry, the payload and positions of the meshlets whose
-    quantisation box is not wholly outside one clip plane (box test in FP64 --
-    exact decisions near a plane do not matter for a byte count), and the
+    and grid entry (and cone record, with cones), the payload and positions of
+    the meshlets that pass the meshlet tests -- quantisation box not wholly
+    outside one clip plane, normal cone not facing away (both in FP64: exact
+    decisions near a boundary do not matter for a byte count) -- and the
     surviving triangles (12 B each)."""
     w = arrays["desc"].view(np.uint32).reshape(-1, 8)
     V = (w[:, 3] & 0xFFFF).astype(np.int64)
@@ -111,6 +124,8 @@ def cull_bytes(stats: dict, arrays: dict, vps: np.ndarray, counts: np.ndarray) -
     corners = np.stack([np.where(np.array([(k >> c) & 1 for c in range(3)], bool), hi, lo)
                         for k in range(8)], 1)                      # [M, 8, 3]
     ch = np.concatenate([corners, np.ones(corners.shape[:2] + (1,))], 2)
+    if cones:
+        cn = arrays["cones"].view(np.float32).reshape(-1, 8).astype(np.float64)
     total = 0.0
     for vp, cnt in zip(vps, counts):
         clip = ch @ vp.reshape(4, 4).astype(np.float64).T           # [M, 8, 4]
@@ -118,6 +133,12 @@ def cull_bytes(stats: dict, arrays: dict, vps: np.ndarray, counts: np.ndarray) -
         out = np.zeros(w.shape[0], bool)
         for c in range(3):
             out |= (clip[..., c] > wv).all(1) | (clip[..., c] < -wv).all(1)
+        eye = _eye64(vp) if cones else None
+        if eye is not None:
+            v = cn[:, 0:3] - eye
+            d = (cn[:, 4:7] * v).sum(1)
+            out |= (cn[:, 7] < 1) & (d >= cn[:, 7] * np.linalg.norm(v, axis=1) + cn[:, 3])
         keep = ~out
         total += (4 * words[keep].sum() + 12 * V[keep].sum() + 12 * int(cnt))
-    return int(32 * w.shape[0] + 32 * stats["n_grids"] + total / len(vps))
+    per_meshlet = 64 if cones else 32
+    return int(per_meshlet * w.shape[0] + 32 * stats["n_grids"] + total / len(vps))

@@ -138,12 +138,18 @@ def test_cfg3_fullsize():
     print(f"cfg3: {s['n_meshlets']} meshlets ({s['split_meshlets']} from splits), {n} sampled")
 
 
-def test_cfg4_fullsize_cull():
+@pytest.fixture(scope="module")
+def cfg4_data():
+    return W.cfg4()
+
+
+@pytest.mark.parametrize("cones", [False, True])
+def test_cfg4_fullsize_cull(cfg4_data, cones):
     import torch
-    blob, meshes, vps = W.cfg4()
+    blob, meshes, vps = cfg4_data
     s = blob.stats()
     assert s["input_tris"] >= 50_000_000
-    db = mc.DeviceBatch(blob)
+    db = mc.DeviceBatch(blob, cones=cones)
     T, V = s["total_tris"], s["total_verts"]
     tri = torch.empty(3 * T + 3, dtype=torch.int32, device="cuda")
     counts = torch.zeros(len(vps), dtype=torch.int32, device="cuda")
@@ -161,7 +167,7 @@ def test_cfg4_fullsize_cull():
     # the last view's survivors, in full, against the oracle's
     a = blob.arrays()
     ob = O.Blob(a["desc"], a["payload"], a["grids"])
-    ref, ref_pos, passed = O.decode_cull(ob, vps[-1])
+    ref, ref_pos, passed = O.decode_cull(ob, vps[-1], cones=a["cones"] if cones else None)
     assert int(c[-1]) == ref.shape[0]
     got = tri[: 3 * int(c[-1])].cpu().numpy().view(np.uint32).reshape(-1, 3)
     order_g = np.lexsort(got.T[::-1])
@@ -170,4 +176,5 @@ def test_cfg4_fullsize_cull():
     f = ob.fields()
     vm = np.repeat(passed, f["V"].astype(np.int64)).astype(bool)
     assert np.array_equal(pos.cpu().numpy().reshape(-1, 3)[vm].view(np.uint32), ref_pos[vm].view(np.uint32))
-    print(f"cfg4: {s['input_tris']} triangles, kept fraction per view {frac.min():.3f}..{frac.max():.3f}")
+    print(f"cfg4 (cones={cones}): {s['input_tris']} triangles, kept fraction per view "
+          f"{frac.min():.3f}..{frac.max():.3f}, meshlets decoded in the last view {passed.mean():.3f}")
