@@ -85,27 +85,32 @@ int orc_decode_meshlet(const uint8_t *desc32, const uint8_t *payload,
                        double *pos64) {
   desc_t d;
   parse_desc(desc32, &d);
-  if (d.V < 3 || d.V > 256 || d.tp < 1 || d.tp > 256 || d.w < 1 || d.w > 8 || d.b < 1 ||
+  if (d.V < 3 || d.V > 256 || d.tp < 1 || d.tp > 256 || d.w > 8 || d.b < 1 ||
       d.b > 32 || d.grid >= n_grids || d.V > d.tp + 2)
     return ORC_ERR_CORRUPT;
+  const int gts = d.w == 0; /* plain GTS: one stored 8-bit entry per triangle */
   uint32_t R = d.tp + 2 - d.V;
   uint64_t nw = (d.tp + 31) / 32;
-  uint64_t rw = ((uint64_t)R * d.w + 31) / 32;
+  uint64_t cw = gts ? nw + ((uint64_t)d.tp - 1 + 3) / 4 : 2 * nw + ((uint64_t)R * d.w + 31) / 32;
   uint64_t pw = (3 * (uint64_t)d.V * d.b + 31) / 32;
   uint64_t start = 16 * (uint64_t)d.off16;
-  if (start + 4 * (2 * nw + rw + pw) > payload_bytes) return ORC_ERR_CORRUPT;
+  if (start + 4 * (cw + pw) > payload_bytes) return ORC_ERR_CORRUPT;
   const uint8_t *F = payload + start;
-  const uint8_t *INC = F + 4 * nw;
+  const uint8_t *INC = F + 4 * nw; /* plain GTS: the entry bytes */
   const uint8_t *RB = INC + 4 * nw;
-  const uint8_t *PB = RB + 4 * rw;
-  if (get_bits(F, 0, 1) || get_bits(INC, 0, 1)) return ORC_ERR_CORRUPT;
+  const uint8_t *PB = F + 4 * cw;
+  if (get_bits(F, 0, 1) || (!gts && get_bits(INC, 0, 1))) return ORC_ERR_CORRUPT;
 
   /* strip walk */
   uint32_t a = 0, b = 1, c = 2, next_new = 3, slot = 0;
   if (local) { local[0] = 0; local[1] = 1; local[2] = 2; }
   for (uint32_t k = 1; k < d.tp; k++) {
     uint32_t x;
-    if (get_bits(INC, k, 1)) {
+    if (gts) {
+      x = get_bits(INC, 8 * (uint64_t)(k - 1), 8);
+      if (x > next_new || x >= d.V) return ORC_ERR_CORRUPT;
+      if (x == next_new) next_new++;
+    } else if (get_bits(INC, k, 1)) {
       if (next_new >= d.V) return ORC_ERR_CORRUPT;
       x = next_new++;
     } else {
@@ -126,7 +131,7 @@ int orc_decode_meshlet(const uint8_t *desc32, const uint8_t *payload,
       local[3 * k + 2] = (uint8_t)c;
     }
   }
-  if (next_new != d.V || slot != R) return ORC_ERR_CORRUPT;
+  if (next_new != d.V || (!gts && slot != R)) return ORC_ERR_CORRUPT;
 
   /* positions */
   const uint8_t *g = grids + 32 * (size_t)d.grid;

@@ -30,6 +30,7 @@ typedef struct {
   uint32_t tp, V, R, w, b, strips;
   uint8_t f[256], inc[256]; /* per triangle */
   uint8_t reuse[256];       /* reuse buffer values */
+  uint8_t ent[256];         /* plain GTS: stream entry n_k of triangle k */
   uint32_t gv[256];         /* global vertex id of local vertex */
   uint32_t L[3];
   uint32_t q[256][3];
@@ -129,6 +130,15 @@ static void meshlet_cone(const float *P, uint32_t V, const uint32_t *lt, uint32_
   put_f32(out + 28, sf);
 }
 
+/* u32 words of a meshlet's connectivity section: GTS-Reuse (w >= 1): L/R
+ * words, increment words, reuse words; plain GTS (w = 0): L/R words and one
+ * byte per triangle k >= 1 holding its stream entry. */
+static uint64_t conn_words(const meshlet_t *x) {
+  uint64_t nw = (x->tp + 31) / 32;
+  if (x->w == 0) return nw + ((uint64_t)x->tp - 1 + 3) / 4;
+  return 2 * nw + ((uint64_t)x->R * x->w + 31) / 32;
+}
+
 static uint32_t ceil_log2(uint32_t v) {
   uint32_t w = 0;
   while ((1u << w) < v) w++;
@@ -164,9 +174,11 @@ static int build_meshlet(const uint32_t *tris, const uint32_t *ids, uint32_t T,
   uint32_t R = 0, seen = 3;
   m->f[0] = 0;
   m->inc[0] = 0;
+  m->ent[0] = 2;
   for (uint32_t k = 1; k < tp; k++) {
     m->f[k] = flags[k];
     uint32_t n = local[k + 2];
+    m->ent[k] = (uint8_t)n;
     if (n == seen) {
       m->inc[k] = 1;
       seen++;
@@ -176,7 +188,7 @@ static int build_meshlet(const uint32_t *tris, const uint32_t *ids, uint32_t T,
     }
   }
   m->R = R;
-  m->w = reuse_mode == 0 ? 8u : ceil_log2(V);
+  m->w = reuse_mode == 0 ? 8u : reuse_mode == 1 ? ceil_log2(V) : 0u;
   return ORC_OK;
 }
 
@@ -184,7 +196,7 @@ int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
                const uint32_t *mtri, const uint32_t *mstart,
                uint32_t n_meshlets, const uint8_t *bits, uint32_t reuse_mode,
                const uint32_t *perm, uint32_t mesh_id, orc_blob **out) {
-  if (!pos || !tris || !mtri || !mstart || !bits || !out || n_verts == 0 || reuse_mode > 1)
+  if (!pos || !tris || !mtri || !mstart || !bits || !out || n_verts == 0 || reuse_mode > 2)
     return ORC_ERR_ARG;
   *out = NULL;
   for (uint32_t m = 0; m < n_meshlets; m++)
@@ -271,8 +283,7 @@ int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
   uint64_t total_words = 0;
   for (uint32_t m = 0; m < n_meshlets; m++) {
     meshlet_t *x = &ms[m];
-    uint64_t words = 2 * (uint64_t)((x->tp + 31) / 32) + ((uint64_t)x->R * x->w + 31) / 32 +
-                     (3 * (uint64_t)x->V * x->b + 31) / 32;
+    uint64_t words = conn_words(x) + (3 * (uint64_t)x->V * x->b + 31) / 32;
     total_words += (words + 3) / 4 * 4;
   }
   blob->n_meshlets = n_meshlets;
@@ -306,18 +317,20 @@ int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
     if (mi >= n_meshlets) { free(words); free(ms); orc_blob_free(blob); return ORC_ERR_ARG; }
     meshlet_t *x = &ms[mi];
     uint32_t nw = (x->tp + 31) / 32;
-    uint64_t rw = ((uint64_t)x->R * x->w + 31) / 32;
+    uint64_t cw = conn_words(x);
     uint64_t pw = (3 * (uint64_t)x->V * x->b + 31) / 32;
-    uint64_t n = (2 * nw + rw + pw + 3) / 4 * 4;
+    uint64_t n = (cw + pw + 3) / 4 * 4;
     memset(words, 0, n * 4);
-    for (uint32_t k = 0; k < x->tp; k++) {
-      put_bits(words, k, 1, x->f[k]);
-      put_bits(words + nw, k, 1, x->inc[k]);
+    for (uint32_t k = 0; k < x->tp; k++) put_bits(words, k, 1, x->f[k]);
+    if (x->w == 0) {
+      for (uint32_t k = 1; k < x->tp; k++) put_bits(words + nw, 8 * (uint64_t)(k - 1), 8, x->ent[k]);
+    } else {
+      for (uint32_t k = 0; k < x->tp; k++) put_bits(words + nw, k, 1, x->inc[k]);
+      for (uint32_t r = 0; r < x->R; r++) put_bits(words + 2 * nw, (uint64_t)r * x->w, x->w, x->reuse[r]);
     }
-    for (uint32_t r = 0; r < x->R; r++) put_bits(words + 2 * nw, (uint64_t)r * x->w, x->w, x->reuse[r]);
     for (uint32_t v = 0; v < x->V; v++)
       for (int c = 0; c < 3; c++)
-        put_bits(words + 2 * nw + rw, (3 * (uint64_t)v + c) * x->b, x->b, x->q[v][c]);
+        put_bits(words + cw, (3 * (uint64_t)v + c) * x->b, x->b, x->q[v][c]);
     for (uint64_t i = 0; i < n; i++) put_u32(blob->payload + 4 * (off_words + i), words[i]);
     uint8_t *d = blob->desc + 32 * (size_t)p;
     if (vbase + x->V > 0xFFFFFFFFull || tbase + x->tp > 0xFFFFFFFFull ||
@@ -365,7 +378,8 @@ int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
     tbase += x->tp;
     blob->restarts += x->strips - 1;
     blob->degenerates += 4 * (uint64_t)(x->strips - 1);
-    blob->conn_bits += 2 * (uint64_t)x->tp + (uint64_t)x->w * x->R;
+    blob->conn_bits += x->w ? 2 * (uint64_t)x->tp + (uint64_t)x->w * x->R
+                            : (uint64_t)x->tp + 8 * (uint64_t)(x->tp - 1);
     blob->reuse_entries += x->R;
   }
   blob->total_tris = tbase;

@@ -27,13 +27,17 @@
  * Blob format (little-endian):
  *   descriptor, 32 B per meshlet:
  *     u32 payload offset in 16-byte units, u32 vertex_base, u32 tri_base,
- *     u16 V, u16 T' (triangles incl. degenerates), u8 reuse width w,
+ *     u16 V, u16 T' (triangles incl. degenerates), u8 reuse width w
+ *     (0 = plain GTS, below),
  *     u8 position bits b, u16 grid id, u32 L[3] (meshlet minimum on the grid)
  *   payload block per meshlet, u32 words, bits LSB-first, padded to 16 B:
  *     ceil(T'/32) L/R words (bit k = 1: triangle k entered across the right
  *     edge), ceil(T'/32) increment words (bit k = 1: new vertex),
  *     ceil(R*w/32) reuse words, ceil(3*V*b/32) position words
  *     (vertex v channel c at bit (3v+c)*b).  Bit 0 of both flag words is 0.
+ *     Plain GTS (Sec. 4.2, w = 0): the L/R words, then one byte per
+ *     triangle k >= 1 holding its stream entry I[k+2] (ceil((T'-1)/4)
+ *     words), then the position words.
  *   grid entry, 32 B: f32 G[3], u32 b, f32 Delta[3], u32 mesh id.
  *   normal cone, 32 B per meshlet (blob order), the per-meshlet cull data
  *   the paper keeps beside the offsets (Sec. 3, Sec. 5 "cull information"):
@@ -94,7 +98,8 @@ typedef struct {
 
 /* Encode the meshlets (mtri/mstart as produced by orc_meshletize) of one mesh.
  * bits[m]: position bits of meshlet m (1..32).  reuse_mode 0: w = 8,
- * reuse_mode 1: w = ceil(log2 V).  perm (may be NULL): blob slot p holds
+ * reuse_mode 1: w = ceil(log2 V), reuse_mode 2: plain GTS (every stream
+ * entry stored at 8 bits, no increment flags).  perm (may be NULL): blob slot p holds
  * meshlet perm[p].  mesh_id is written into the grid entries. */
 int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
                const uint32_t *mtri, const uint32_t *mstart,
