@@ -37,8 +37,13 @@
  *                               a vertex not seen before (Sec. 4.3); bit 0 is 0
  *     ceil(R*w/32) reuse words  R = T' - V + 2 entries of w bits (Sec. 4.3)
  *     ceil(3*V*b/32) position words  vertex v channel c at bit (3v+c)*b
+ *   plain GTS block (descriptor w = 0, Sec. 4.2 before the reuse packing):
+ *     the L/R words, then ceil((T'-1)/4) words holding one byte per triangle
+ *     k >= 1, its strip entry I[k+2] (byte k-1), then the position words
  *   grid entry, 32 bytes (mc_grid below): FP32 origin G and step Delta of
  *     the global quantisation grid of one mesh at one bit width (Sec. 4.4).
+ *   normal cone, 32 bytes per meshlet (mc_cone below), optional input of the
+ *     fused cull.
  */
 #ifndef MESHLET_CODEC_H
 #define MESHLET_CODEC_H
@@ -77,7 +82,7 @@ typedef struct {
   uint32_t tri_base;      /* first decoded triangle (T' slots incl. degenerates) */
   uint16_t n_verts;       /* V, 3..256 */
   uint16_t n_tris;        /* T' = triangles incl. restart degenerates, 1..256 */
-  uint8_t reuse_bits;     /* w, 1..8, 2^w >= V */
+  uint8_t reuse_bits;     /* w, 1..8, 2^w >= V; 0 = plain GTS block */
   uint8_t pos_bits;       /* b, 1..32 */
   uint16_t grid;          /* index of the mc_grid entry */
   uint32_t L[3];          /* meshlet minimum on the global grid (Sec. 4.4) */
@@ -152,7 +157,9 @@ void mc_meshlets_free(mc_meshlets *m);
 typedef struct {
   uint32_t pos_bits;              /* b for every meshlet (1..32) ... */
   const uint8_t *pos_bits_per_meshlet; /* ... or one b per meshlet (may be NULL) */
-  uint32_t reuse_mode;            /* 0: w = 8 (Sec. 3), 1: w = ceil(log2 V) */
+  uint32_t reuse_mode;            /* 0: w = 8 (Sec. 3), 1: w = ceil(log2 V),
+                                   * 2: plain GTS (Sec. 4.2: every stream entry
+                                   * stored at 8 bits; descriptor w = 0) */
   const uint32_t *order;          /* optional: blob slot p holds meshlet order[p] */
   uint32_t mesh_id;               /* written into the grid entries */
   uint32_t n_threads;             /* 0 = hardware concurrency */

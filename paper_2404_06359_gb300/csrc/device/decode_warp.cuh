@@ -76,11 +76,21 @@ __device__ __forceinline__ Grid load_grid(const mc_grid *g) {
   return r;
 }
 
+// Connectivity encodings of a meshlet: GTS-Reuse with w-bit reuse entries
+// (funnel-shift extraction) or with byte entries (w = 8: byte loads), and
+// plain GTS (w = 0: every stream entry stored as a byte, Sec. 4.2).
+enum : int { kReuseBits = 0, kReuseBytes = 1, kPlainGts = 2 };
+
+// u32 words of the connectivity section: L/R words plus increment and reuse
+// words (GTS-Reuse), or plus one byte per triangle k >= 1 (plain GTS).
+__device__ __forceinline__ uint32_t conn_words(const Desc &d) {
+  const uint32_t nw = (d.T + 31) >> 5;
+  return d.w ? 2 * nw + ((d.T + 2 - d.V) * d.w + 31) / 32 : nw + (d.T + 2) / 4;
+}
+
 // Payload block size in u32 words (unpadded) of a meshlet.
 __device__ __forceinline__ uint32_t block_words(const Desc &d) {
-  uint32_t nw = (d.T + 31) >> 5;
-  uint32_t R = d.T + 2 - d.V;
-  return 2 * nw + (R * d.w + 31) / 32 + (3 * d.V * d.b + 31) / 32;
+  return conn_words(d) + (3 * d.V * d.b + 31) / 32;
 }
 
 struct BatchArgs {
@@ -98,7 +108,7 @@ struct BatchArgs {
 __device__ __forceinline__ bool header_ok(const Desc &d, const BatchArgs &a) {
   // evaluated without short-circuit branches (all terms are cheap)
   const bool shape = (d.V - 3u <= 253u) & (d.T - 1u <= 255u) & (d.V <= d.T + 2) &
-                     (d.w - 1u <= 7u) & (d.b - 1u <= 31u) & (d.grid < a.n_grids) &
+                     (d.w <= 8u) & (d.b - 1u <= 31u) & (d.grid < a.n_grids) &
                      (d.T <= a.max_tris);
   const uint32_t padded = (block_words(d) + 3) & ~3u;
   return shape & (padded <= a.max_block_words) &
@@ -187,9 +197,24 @@ __device__ __forceinline__ void stg3_u32_if(uint32_t *g, uint32_t x, uint32_t y,
 }
 
 // Stream-level consistency checks of the checked build: bit 0 of both flag
-// words clear, no flag bit past T', and V = 3 + (number of increment flags).
+// words clear, no flag bit past T', and V = 3 + (number of increment flags);
+// plain GTS: every stored entry is a vertex already seen or the next new
+// one, and V vertices are introduced in all (a short sequential scan, run by
+// every lane alike).
 __device__ __forceinline__ bool stream_header_ok(const Desc &d, const uint32_t *sw) {
   const uint32_t nw = (d.T + 31) >> 5;
+  if (d.w == 0) {
+    const uint32_t tail = d.T & 31u;
+    bool ok = !(sw[0] & 1u) && !(tail && (sw[nw - 1] >> tail));
+    const uint8_t *e = reinterpret_cast<const uint8_t *>(sw + nw);
+    uint32_t next = 3;
+    for (uint32_t k = 1; k < d.T; k++) {
+      const uint32_t x = e[k - 1];
+      ok = ok & (x <= next) & (x < d.V);
+      next += x == next ? 1u : 0u;
+    }
+    return ok && next == d.V;
+  }
   uint32_t incs = 0;
   for (uint32_t i = 0; i < nw; i++) incs += __popc(sw[nw + i]);
   const uint32_t tail = d.T & 31u;
@@ -209,12 +234,13 @@ __device__ __forceinline__ bool stream_header_ok(const Desc &d, const uint32_t *
 // running "last transition" register when the run starts in an earlier word.
 // CHECKED: returns false (warp-uniform) if a reuse entry names a vertex not
 // yet seen.
-template <bool CHECKED, bool W8, class Emit>
+template <bool CHECKED, int RM, class Emit>
 __device__ __forceinline__ bool walk_triangles(const Desc &d, const uint32_t *sw, uint8_t *sI,
                                                uint32_t lane, Emit &&emit) {
   const uint32_t nw = (d.T + 31) >> 5;
   const uint32_t a_sw = smem_addr(sw);
   const uint32_t a_rb = a_sw + 8 * nw;
+  const uint32_t a_eb = a_sw + 4 * nw;  // plain GTS: byte k-1 = entry of triangle k
   const uint32_t a_sI = smem_addr(sI);
   if (lane < 2) sts_u8(a_sI + lane, lane);
   const uint32_t le = (2u << lane) - 1u;
@@ -223,14 +249,21 @@ __device__ __forceinline__ bool walk_triangles(const Desc &d, const uint32_t *sw
   uint32_t k = lane;
   for (uint32_t i = 0; i < nw; i++, k += 32) {
     const uint32_t f = lds_u32(a_sw + 4 * i);
-    const uint32_t inc = lds_u32(a_sw + 4 * (nw + i)) | (i == 0 ? 1u : 0u);
-    const uint32_t s = base + __popc(inc & le);
-    const bool is_new = (inc & (1u << lane)) != 0;
-    const uint32_t slot = is_new ? 0u : k + 1 - s;
-    const uint32_t r = W8 ? lds_u8(a_rb + slot) : extract(sw + 2 * nw, slot * d.w, d.w);
-    const uint32_t n = is_new ? s : r;
+    uint32_t n;
+    if (RM == kPlainGts) {
+      const uint32_t e = lds_u8(a_eb + (k ? k - 1 : 0u));
+      n = k ? e : 2u;
+    } else {
+      const uint32_t inc = lds_u32(a_sw + 4 * (nw + i)) | (i == 0 ? 1u : 0u);
+      const uint32_t s = base + __popc(inc & le);
+      const bool is_new = (inc & (1u << lane)) != 0;
+      const uint32_t slot = is_new ? 0u : k + 1 - s;
+      const uint32_t r = RM == kReuseBytes ? lds_u8(a_rb + slot) : extract(sw + 2 * nw, slot * d.w, d.w);
+      n = is_new ? s : r;
+      if (CHECKED && k < d.T && !is_new && r > s) bad = true;
+      base += __popc(inc);
+    }
     const bool live = k < d.T;
-    if (CHECKED && live && !is_new && r > s) bad = true;
     sts_u8_if(a_sI + k + 2, n, live);
     uint32_t prev = __shfl_up_sync(kFull, n, 1);
     if (lane == 0) prev = carry;
@@ -244,7 +277,6 @@ __device__ __forceinline__ bool walk_triangles(const Desc &d, const uint32_t *sw
     const bool fk = (f >> lane) & 1u;
     emit(k, fk ? prev : old, fk ? old : prev, n, live);
     if (D) lastT = 32 * i + msb(D);
-    base += __popc(inc);
   }
   if (CHECKED) bad = __any_sync(kFull, bad);
   __syncwarp();
@@ -285,7 +317,7 @@ __device__ __forceinline__ void stg3_f32_if(float *g, float x, float y, float z,
 // of walk_triangles (same arithmetic) written out flat, with predicated
 // stores and per-lane output pointers advanced by one word of triangles per
 // pass.
-template <bool CHECKED, bool B16, bool W8>
+template <bool CHECKED, bool B16, int RM>
 __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, const uint32_t *sw,
                                               uint8_t *sI, uint32_t lane, uint8_t *out_local,
                                               uint32_t *out_global, float *out_pos) {
@@ -293,6 +325,7 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
   const uint32_t nw = (d.T + 31) >> 5;
   const uint32_t a_sw = smem_addr(sw);
   const uint32_t a_rb = a_sw + 8 * nw;  // reuse section (bytes)
+  const uint32_t a_eb = a_sw + 4 * nw;  // plain GTS entries (byte k-1 = triangle k)
   const uint32_t a_sI = smem_addr(sI);
   if (lane < 2) sts_u8(a_sI + lane, lane);  // I[0], I[1]; I[2] is triangle 0's entry
   const uint32_t le = (2u << lane) - 1u;
@@ -305,14 +338,21 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
   uint32_t k = lane;
   for (uint32_t i = 0; i < nw; i++, k += 32) {
     const uint32_t f = lds_u32(a_sw + 4 * i);
-    const uint32_t inc = lds_u32(a_sw + 4 * (nw + i)) | (i == 0 ? 1u : 0u);
-    const uint32_t s = base + __popc(inc & le);
-    const bool is_new = (inc & (1u << lane)) != 0;
-    const uint32_t slot = is_new ? 0u : k + 1 - s;
-    const uint32_t r = W8 ? lds_u8(a_rb + slot) : extract(sw + 2 * nw, slot * d.w, d.w);
-    const uint32_t n = is_new ? s : r;
+    uint32_t n;
+    if (RM == kPlainGts) {
+      const uint32_t e = lds_u8(a_eb + (k ? k - 1 : 0u));
+      n = k ? e : 2u;
+    } else {
+      const uint32_t inc = lds_u32(a_sw + 4 * (nw + i)) | (i == 0 ? 1u : 0u);
+      const uint32_t s = base + __popc(inc & le);
+      const bool is_new = (inc & (1u << lane)) != 0;
+      const uint32_t slot = is_new ? 0u : k + 1 - s;
+      const uint32_t r = RM == kReuseBytes ? lds_u8(a_rb + slot) : extract(sw + 2 * nw, slot * d.w, d.w);
+      n = is_new ? s : r;
+      if (CHECKED && k < d.T && !is_new && r > s) bad = true;  // entries seen so far: 0..s
+      base += __popc(inc);
+    }
     const bool live = k < d.T;
-    if (CHECKED && live && !is_new && r > s) bad = true;  // entries seen so far: 0..s
     sts_u8_if(a_sI + k + 2, n, live);
     uint32_t prev = __shfl_up_sync(kFull, n, 1);
     if (lane == 0) prev = carry;
@@ -330,11 +370,10 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
     pl += 96;
     pg += 96;
     if (D) lastT = 32 * i + msb(D);
-    base += __popc(inc);
   }
   if (CHECKED && __any_sync(kFull, bad)) return false;
   // positions
-  const uint32_t *pw = sw + 2 * nw + ((d.T + 2 - d.V) * d.w + 31) / 32;
+  const uint32_t *pw = sw + conn_words(d);
   float *op = out_pos + 3ull * (d.vbase + lane);
   const uint32_t vpasses = (d.V + 31) >> 5;
   if (B16 && small_coords(d)) {
@@ -364,11 +403,17 @@ __device__ __forceinline__ bool decode_dispatch(const Desc &d, const Grid &g, co
                                                 uint8_t *sI, uint32_t lane, uint8_t *out_local,
                                                 uint32_t *out_global, float *out_pos) {
   if (d.b == 16) {
-    if (d.w == 8) return decode_staged<CHECKED, true, true>(d, g, sw, sI, lane, out_local, out_global, out_pos);
-    return decode_staged<CHECKED, true, false>(d, g, sw, sI, lane, out_local, out_global, out_pos);
+    if (d.w == 8)
+      return decode_staged<CHECKED, true, kReuseBytes>(d, g, sw, sI, lane, out_local, out_global, out_pos);
+    if (d.w == 0)
+      return decode_staged<CHECKED, true, kPlainGts>(d, g, sw, sI, lane, out_local, out_global, out_pos);
+    return decode_staged<CHECKED, true, kReuseBits>(d, g, sw, sI, lane, out_local, out_global, out_pos);
   }
-  if (d.w == 8) return decode_staged<CHECKED, false, true>(d, g, sw, sI, lane, out_local, out_global, out_pos);
-  return decode_staged<CHECKED, false, false>(d, g, sw, sI, lane, out_local, out_global, out_pos);
+  if (d.w == 8)
+    return decode_staged<CHECKED, false, kReuseBytes>(d, g, sw, sI, lane, out_local, out_global, out_pos);
+  if (d.w == 0)
+    return decode_staged<CHECKED, false, kPlainGts>(d, g, sw, sI, lane, out_local, out_global, out_pos);
+  return decode_staged<CHECKED, false, kReuseBits>(d, g, sw, sI, lane, out_local, out_global, out_pos);
 }
 
 }  // namespace mcdev

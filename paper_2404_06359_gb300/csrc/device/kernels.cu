@@ -303,14 +303,13 @@ __device__ __forceinline__ void sts_u32_if(uint32_t a, uint32_t x, bool p) {
 // position n_keep as x | y << 8 | z << 16 | tag (tag = source slot << 24).
 // Returns the new count, or 0xFFFFFFFF for a corrupt stream (checked build).
 // Clip x, y of vertex v sit in cxy[v] (float2), clip w in cw[v].
-template <bool CHECKED, bool B16, bool W8>
+template <bool CHECKED, bool B16, int RM>
 __device__ __forceinline__ uint32_t cull_staged(const Desc &d, const Grid &g, const float *M,
                                                 const uint32_t *sw, uint8_t *sI, float2 *cxy,
                                                 float *cw, uint32_t *surv, uint32_t n_keep,
                                                 uint32_t tag, uint32_t lane, float *out_pos) {
   if (CHECKED && !stream_header_ok(d, sw)) return 0xFFFFFFFFu;
-  const uint32_t nw = (d.T + 31) >> 5;
-  const uint32_t *pw = sw + 2 * nw + ((d.T + 2 - d.V) * d.w + 31) / 32;
+  const uint32_t *pw = sw + conn_words(d);
   const bool small = small_coords(d);
   float *op = out_pos + 3ull * (d.vbase + lane);
   const uint32_t vpasses = (d.V + 31) >> 5;
@@ -329,7 +328,7 @@ __device__ __forceinline__ uint32_t cull_staged(const Desc &d, const Grid &g, co
   }
   __syncwarp();
   const uint32_t a_surv = smem_addr(surv);
-  const bool ok = walk_triangles<CHECKED, W8>(
+  const bool ok = walk_triangles<CHECKED, RM>(
       d, sw, sI, lane, [&](uint32_t k, uint32_t x, uint32_t y, uint32_t z, bool live) {
         // evaluated on every lane without branches; dead lanes read vertex 0
         const uint32_t xi = live ? x : 0u, yi = live ? y : 0u, zi = live ? z : 0u;
@@ -354,12 +353,16 @@ __device__ __forceinline__ uint32_t cull_dispatch(const Desc &d, const Grid &g, 
                                                   const uint32_t *sw, uint8_t *sI, float2 *cxy,
                                                   float *cw, uint32_t *surv, uint32_t n_keep,
                                                   uint32_t tag, uint32_t lane, float *out_pos) {
+#define MC_CULL(B, R) cull_staged<CHECKED, B, R>(d, g, M, sw, sI, cxy, cw, surv, n_keep, tag, lane, out_pos)
   if (d.b == 16) {
-    if (d.w == 8) return cull_staged<CHECKED, true, true>(d, g, M, sw, sI, cxy, cw, surv, n_keep, tag, lane, out_pos);
-    return cull_staged<CHECKED, true, false>(d, g, M, sw, sI, cxy, cw, surv, n_keep, tag, lane, out_pos);
+    if (d.w == 8) return MC_CULL(true, kReuseBytes);
+    if (d.w == 0) return MC_CULL(true, kPlainGts);
+    return MC_CULL(true, kReuseBits);
   }
-  if (d.w == 8) return cull_staged<CHECKED, false, true>(d, g, M, sw, sI, cxy, cw, surv, n_keep, tag, lane, out_pos);
-  return cull_staged<CHECKED, false, false>(d, g, M, sw, sI, cxy, cw, surv, n_keep, tag, lane, out_pos);
+  if (d.w == 8) return MC_CULL(false, kReuseBytes);
+  if (d.w == 0) return MC_CULL(false, kPlainGts);
+  return MC_CULL(false, kReuseBits);
+#undef MC_CULL
 }
 
 // Writes a warp's buffered survivors as global index triples: one atomicAdd

@@ -32,6 +32,7 @@ struct Packed {
   uint32_t words = 0;  // padded block size in u32 words
   std::vector<uint32_t> gv;     // global vertex id per local id
   std::vector<uint8_t> reuse;   // reuse entries
+  std::vector<uint8_t> ent;     // plain GTS (w = 0): stream entry of triangles 1..T'-1
   uint32_t flag_words[8], inc_words[8];
   uint32_t L[3];
 };
@@ -127,7 +128,7 @@ extern "C" mc_status mc_encode(const mc_meshlets *m, const float *pos, uint32_t 
                                const mc_encode_params *p, mc_blob **out) {
   if (!out) return MC_ERR_INVALID_ARG;
   *out = nullptr;
-  if (!m || !pos || !p || n_verts != m->n_verts || p->reuse_mode > 1) return MC_ERR_INVALID_ARG;
+  if (!m || !pos || !p || n_verts != m->n_verts || p->reuse_mode > 2) return MC_ERR_INVALID_ARG;
   const uint32_t nm = mc_meshlets_count(m);
   if (!p->pos_bits_per_meshlet && (p->pos_bits < 1 || p->pos_bits > 32)) return MC_ERR_INVALID_ARG;
   if (p->pos_bits_per_meshlet)
@@ -183,8 +184,10 @@ extern "C" mc_status mc_encode(const mc_meshlets *m, const float *pos, uint32_t 
           }
           x.V = (uint32_t)x.gv.size();
           uint32_t seen = 3;
+          x.ent.clear();
           for (uint32_t k = 1; k < tp; k++) {
             if (fl[k]) x.flag_words[k >> 5] |= 1u << (k & 31);
+            x.ent.push_back(local[k + 2]);
             if (local[k + 2] == seen) {
               x.inc_words[k >> 5] |= 1u << (k & 31);
               seen++;
@@ -193,8 +196,12 @@ extern "C" mc_status mc_encode(const mc_meshlets *m, const float *pos, uint32_t 
             }
           }
           x.R = (uint32_t)x.reuse.size();
-          x.w = p->reuse_mode == 0 ? 8u : ceil_log2(x.V);
-          uint32_t words = 2 * ((tp + 31) / 32) + (x.R * x.w + 31) / 32 + (3 * x.V * x.b + 31) / 32;
+          x.w = p->reuse_mode == 0 ? 8u : p->reuse_mode == 1 ? ceil_log2(x.V) : 0u;
+          // connectivity words: GTS-Reuse = L/R + increment + reuse words;
+          // plain GTS (w = 0) = L/R words + one byte per triangle k >= 1
+          const uint32_t conn = x.w ? 2 * ((tp + 31) / 32) + (x.R * x.w + 31) / 32
+                                    : (tp + 31) / 32 + (tp + 2) / 4;
+          const uint32_t words = conn + (3 * x.V * x.b + 31) / 32;
           x.words = (words + 3) / 4 * 4;
         },
         256);
@@ -286,13 +293,21 @@ extern "C" mc_status mc_encode(const mc_meshlets *m, const float *pos, uint32_t 
           const Packed &x = pk[slot[s]];
           uint32_t *w = words + off[s];
           const uint32_t nw = (x.tp + 31) / 32;
-          for (uint32_t i = 0; i < nw; i++) {
-            w[i] = x.flag_words[i];
-            w[nw + i] = x.inc_words[i];
+          uint32_t *pw;
+          if (x.w == 0) {
+            for (uint32_t i = 0; i < nw; i++) w[i] = x.flag_words[i];
+            uint8_t *eb = reinterpret_cast<uint8_t *>(w + nw);  // little-endian byte k-1
+            for (uint32_t k = 1; k < x.tp; k++) eb[k - 1] = x.ent[k - 1];
+            pw = w + nw + (x.tp + 2) / 4;
+          } else {
+            for (uint32_t i = 0; i < nw; i++) {
+              w[i] = x.flag_words[i];
+              w[nw + i] = x.inc_words[i];
+            }
+            uint32_t *rw = w + 2 * nw;
+            for (uint32_t r = 0; r < x.R; r++) put_bits(rw, (uint64_t)r * x.w, x.w, x.reuse[r]);
+            pw = rw + (x.R * x.w + 31) / 32;
           }
-          uint32_t *rw = w + 2 * nw;
-          for (uint32_t r = 0; r < x.R; r++) put_bits(rw, (uint64_t)r * x.w, x.w, x.reuse[r]);
-          uint32_t *pw = rw + (x.R * x.w + 31) / 32;
           float P[3 * 256];  // decoded positions, for the normal cone
           for (uint32_t v = 0; v < x.V; v++)
             for (int c = 0; c < 3; c++) {
@@ -354,7 +369,7 @@ extern "C" mc_status mc_encode(const mc_meshlets *m, const float *pos, uint32_t 
     for (uint32_t i = 0; i < nm; i++) {
       const Packed &x = pk[i];
       blob->restarts += x.strips - 1;
-      blob->conn_bits += 2ull * x.tp + (uint64_t)x.w * x.R;
+      blob->conn_bits += x.w ? 2ull * x.tp + (uint64_t)x.w * x.R : x.tp + 8ull * (x.tp - 1);
       blob->pos_bits_total += 3ull * x.V * x.b;
       blob->max_block_words = std::max(blob->max_block_words, x.words);
       blob->max_tris = std::max(blob->max_tris, x.tp);

@@ -15,7 +15,9 @@ def block_words_max(desc: np.ndarray) -> int:
     rw = (w[:, 4] & 0xFF).astype(np.int64)
     b = ((w[:, 4] >> 8) & 0xFF).astype(np.int64)
     R = T + 2 - V
-    words = 2 * ((T + 31) // 32) + (R * rw + 31) // 32 + (3 * V * b + 31) // 32
+    nw = (T + 31) // 32
+    conn = np.where(rw == 0, nw + (T + 2) // 4, 2 * nw + (R * rw + 31) // 32)  # w = 0: plain GTS
+    words = conn + (3 * V * b + 31) // 32
     return int(((words + 3) // 4 * 4).max()) if words.size else 4
 
 

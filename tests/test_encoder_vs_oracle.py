@@ -24,6 +24,9 @@ def _cases():
         "sphere_256_256_log2": (G.uv_sphere(30_000, rng), [(256, 256)], 12, 1, False),
         "torus_3_8_b7": (G.torus(3_000, rng), [(8, 3)], 7, 1, False),
         "hf_mixed": (G.height_field_disc(40_000, seed=5), list(G.SECTOR_LIMITS), "mixed", 1, True),
+        "torus_64_126_plain_gts": (G.torus(10_000, rng), [(64, 126)], 16, 2, False),
+        "hf_mixed_plain_gts": (G.height_field_disc(20_000, seed=6), list(G.SECTOR_LIMITS), "mixed",
+                               2, True),
     }
 
 

@@ -189,3 +189,24 @@ def test_cull_graph_many_views_with_cones(smooth_scene):
         ref_tri, _, _ = O.decode_cull(blob, vp, cones=blob.cones)
         assert counts[i] == ref_tri.shape[0]
     assert int(st.item()) == 0 and int(scratch.abs().sum()) == 0
+
+
+def test_cull_plain_gts_vs_oracle(smooth_scene):
+    """The fused cull on plain GTS blocks (with cones) against the oracle."""
+    _, vps = smooth_scene
+    rng = np.random.Generator(np.random.PCG64(61))
+    meshes = [G.uv_sphere(15_000, rng, noise=0.0), G.torus(12_000, rng, center=(2.5, 0, 0))]
+    blob = O.concat([O.encode_mesh(m, (64, 126), 16, 2, mesh_id=i) for i, m in enumerate(meshes)])
+    pts = np.concatenate([m.pos for m in meshes])
+    c = 0.5 * (pts.min(0) + pts.max(0))
+    r = float(np.linalg.norm(pts - c, axis=1).max())
+    db = device_batch_from_oracle(blob, cones=True)
+    f = blob.fields()
+    for vp in G.camera_poses(4, c, r, seed=62, distance=2.0):
+        ref_tri, ref_pos, passed = O.decode_cull(blob, vp, cones=blob.cones)
+        for tuning in (None, {"warps_per_cta": 8, "checked": 1}):
+            tri, pos, st = _run(db, vp, tuning)
+            assert st == 0
+            assert np.array_equal(_sorted_rows(tri), _sorted_rows(ref_tri))
+            vm = np.repeat(passed, f["V"].astype(np.int64)).astype(bool)
+            assert np.array_equal(pos.reshape(-1, 3)[vm].view(np.uint32), ref_pos[vm].view(np.uint32))

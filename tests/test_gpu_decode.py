@@ -220,3 +220,54 @@ def test_host_buffer_decode_matches(n_meshes, pinned):
            "status": st.cpu().numpy()}
     assert_same_decode(res, ref, "host-buffer decode")
     assert int(scratch.abs().sum()) == 0
+
+
+@pytest.fixture(scope="module")
+def gts_batches():
+    """Plain GTS blocks (w = 0): a batch of them alone and one mixing them with
+    GTS-Reuse blocks of both reuse widths, all three limits, several b."""
+    rng = np.random.Generator(np.random.PCG64(45))
+    hf = G.height_field_disc(20_000, seed=8)
+    gts = [
+        O.encode_mesh(G.uv_sphere(9_000, rng), (64, 126), 16, 2),
+        O.encode_mesh(G.torus(7_000, rng), (128, 128), lambda n: G.meshlet_bits(n, 1), 2,
+                      perm=lambda n: G.meshlet_permutation(n, 2)),
+        O.encode_mesh(hf, np.array(G.SECTOR_LIMITS).reshape(-1), 20, 2),
+        O.encode_mesh(G.grid_mesh(5), (8, 5), 7, 2),
+    ]
+    reuse = [O.encode_mesh(G.torus(5_000, rng), (64, 126), 16, 0),
+             O.encode_mesh(G.uv_sphere(6_000, rng), (256, 256), 12, 1)]
+    return O.concat(gts), O.concat([gts[0], reuse[0], gts[1], reuse[1], gts[3]])
+
+
+@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("tuning", [None, {"warps_per_cta": 4, "meshlets_per_grab": 1},
+                                    {"warps_per_cta": 16, "meshlets_per_grab": 8},
+                                    {"warps_per_cta": 8, "checked": 1}])
+def test_plain_gts_batch_vs_oracle(gts_batches, which, tuning):
+    blob = gts_batches[which]
+    ref = O.decode(blob)
+    db = device_batch_from_oracle(blob)
+    assert_same_decode(run_decode(db, "batch", tuning), ref, f"gts batch {which} {tuning}")
+    if tuning is None:
+        assert_same_decode(run_decode(db, "plain", {"checked": 1}), ref, f"gts plain {which}")
+
+
+def test_plain_gts_corrupt_entry_flagged(gts_batches):
+    """An entry naming a vertex that was never introduced: the checked kernels
+    report MC_ERR_CORRUPT, the unchecked ones still finish."""
+    blob = gts_batches[0]
+    f = blob.fields()
+    m = int(np.argmax(f["Tp"]))
+    tp = int(f["Tp"][m])
+    start = 16 * int(f["off16"][m]) + 4 * ((tp + 31) // 32)
+    bad = blob.payload.copy()
+    ent = bad[start:start + tp - 1]
+    bad[start + int(np.argmax(ent == ent.max()))] = min(255, int(ent.max()) + 1)
+    broken = O.Blob(blob.desc, bad, blob.grids)
+    db = device_batch_from_oracle(broken)
+    for mode in ("batch", "plain"):
+        res = run_decode(db, mode, {"checked": 1})
+        assert int(res["status"][0]) & (1 << 3), mode
+    res = run_decode(db, "batch")
+    assert int(res["status"][0]) == 0
