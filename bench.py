@@ -174,16 +174,16 @@ def _barrier(ws):
         dist.barrier()
 
 
-def build_workload(cfg: int, rank: int):
+def build_workload(cfg: int, rank: int, codec: str = "reuse"):
     from paper_2404_06359_gb300 import workloads as W
     if cfg == 1:
         blob, meshes = W.cfg1()
         return blob, meshes, None
     if cfg == 2:
-        blob, meshes = W.cfg2(rank)
+        blob, meshes = W.cfg2(rank, plain_gts=codec == "gts")
         return blob, meshes, None
     if cfg == 3:
-        blob, meshes = W.cfg3(rank)
+        blob, meshes = W.cfg3(rank, plain_gts=codec == "gts")
         return blob, meshes, None
     if cfg == 4:
         return W.cfg4(rank)
@@ -299,6 +299,9 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--pool-meshes", type=int, default=128)
+    ap.add_argument("--codec", choices=("reuse", "gts"), default="reuse",
+                    help="connectivity encoding of configs 2/3: GTS-Reuse (default) or plain GTS "
+                         "(one stored 8-bit entry per triangle)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
@@ -317,7 +320,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     t_build = time.time()
-    blob, meshes, vps = build_workload(args.config, rank)
+    if args.codec == "gts" and args.config not in (2, 3):
+        raise SystemExit("--codec gts applies to configs 2 and 3")
+    blob, meshes, vps = build_workload(args.config, rank, args.codec)
     t_build = time.time() - t_build
     stats = blob.stats()
     db = mc.DeviceBatch(blob, "cuda", cones=args.config == 4)  # cfg4: normal-cone meshlet test on
@@ -493,7 +498,10 @@ def main():
         "metric": METRIC, "value": round(value, 3), "unit": "Gtps", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.config], "input_triangles": input_tris,
+        "config": {"workload": WORKLOADS[args.config] + (" [plain GTS connectivity]"
+                                                          if args.codec == "gts" else ""),
+                   "connectivity_bits_per_triangle": round(stats["conn_bits"] / input_tris, 3),
+                   "input_triangles": input_tris,
                    "decoded_triangle_slots": stats["total_tris"], "vertices": stats["total_verts"],
                    "meshlets": stats["n_meshlets"], "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"{ws} independent replica(s), no collective"},

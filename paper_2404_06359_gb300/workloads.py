@@ -49,19 +49,21 @@ def cfg1():
     return mc.mc_encode(ml, mesh.pos, 16, 0), [mesh]
 
 
-def cfg2(rank: int = 0):
+def cfg2(rank: int = 0, plain_gts: bool = False):
+    """plain_gts: store every strip entry at 8 bits (Sec. 4.2) instead of the
+    GTS-Reuse packing."""
     meshes = G.surface_batch(256, 10_000, 200_000, SEEDS[2] + 1000 * rank)
-    return encode_meshes(meshes), meshes
+    return encode_meshes(meshes, reuse_mode=2 if plain_gts else 0), meshes
 
 
-def cfg3(rank: int = 0, total_tris: int = 50_000_000):
+def cfg3(rank: int = 0, total_tris: int = 50_000_000, plain_gts: bool = False):
     seed = SEEDS[3] + 1000 * rank
     mesh = G.height_field_disc(total_tris, seed)
     ml = mc.mc_meshletize(mesh.tris, mesh.n_verts, list(G.SECTOR_LIMITS), mesh.tri_class)
     n = ml.count
     bits = G.meshlet_bits(n, seed + 1)
     order = G.meshlet_permutation(n, seed + 2)
-    return mc.mc_encode(ml, mesh.pos, bits, 1, order), [mesh]
+    return mc.mc_encode(ml, mesh.pos, bits, 2 if plain_gts else 1, order), [mesh]
 
 
 def cfg4(rank: int = 0, min_tris: int = 50_000_000, n_views: int = 64):
@@ -75,6 +77,15 @@ def cfg4(rank: int = 0, min_tris: int = 50_000_000, n_views: int = 64):
     return blob, meshes, vps
 
 
+def _block_words(T, V, w, b):
+    """Unpadded payload words per meshlet: L/R words, then increment and
+    reuse words (GTS-Reuse) or one byte per triangle k >= 1 (plain GTS,
+    w = 0), then the position words."""
+    nw = (T + 31) // 32
+    conn = np.where(w == 0, nw + (T + 2) // 4, 2 * nw + ((T + 2 - V) * w + 31) // 32)
+    return conn + (3 * V * b + 31) // 32
+
+
 def algorithmic_bytes(stats: dict, desc: np.ndarray, local=True, global_=True) -> dict:
     """Bytes one decode must move: compressed input read (descriptors, payload
     without block padding, grids) and decoded output written."""
@@ -83,8 +94,7 @@ def algorithmic_bytes(stats: dict, desc: np.ndarray, local=True, global_=True) -
     T = (w[:, 3] >> 16).astype(np.int64)
     rw = (w[:, 4] & 0xFF).astype(np.int64)
     b = ((w[:, 4] >> 8) & 0xFF).astype(np.int64)
-    R = T + 2 - V
-    words = 2 * ((T + 31) // 32) + (R * rw + 31) // 32 + (3 * V * b + 31) // 32
+    words = _block_words(T, V, rw, b)
     read = 32 * w.shape[0] + 4 * int(words.sum()) + 32 * stats["n_grids"]
     Tt, Vt = int(T.sum()), int(V.sum())
     write = (3 * Tt if local else 0) + (12 * Tt if global_ else 0) + 12 * Vt
@@ -115,7 +125,7 @@ def cull_bytes(stats: dict, arrays: dict, vps: np.ndarray, counts: np.ndarray,
     T = (w[:, 3] >> 16).astype(np.int64)
     rw = (w[:, 4] & 0xFF).astype(np.int64)
     b = ((w[:, 4] >> 8) & 0xFF).astype(np.int64)
-    words = 2 * ((T + 31) // 32) + ((T + 2 - V) * rw + 31) // 32 + (3 * V * b + 31) // 32
+    words = _block_words(T, V, rw, b)
     g = arrays["grids"].view(np.float32).reshape(-1, 8).astype(np.float64)
     gid = (w[:, 4] >> 16).astype(np.int64)
     L = w[:, 5:8].astype(np.float64)
