@@ -51,7 +51,9 @@ class _Blob(C.Structure):
                 ("degenerates", C.c_uint64), ("conn_bits", C.c_uint64),
                 ("reuse_entries", C.c_uint64), ("desc", C.POINTER(C.c_uint8)),
                 ("payload", C.POINTER(C.c_uint8)), ("grids", C.POINTER(C.c_uint8)),
-                ("vmap", C.POINTER(C.c_uint32)), ("cones", C.POINTER(C.c_uint8))]
+                ("vmap", C.POINTER(C.c_uint32)), ("cones", C.POINTER(C.c_uint8)),
+                ("n_attr", C.c_uint32), ("attr_bits", C.c_uint32),
+                ("adesc", C.POINTER(C.c_uint8)), ("agrids", C.POINTER(C.c_uint8))]
 
 
 def lib():
@@ -64,7 +66,9 @@ def lib():
             u32, u64 = C.c_uint32, C.c_uint64
             L.orc_meshletize.argtypes = [u32, P, u32, P, P, u32, P, P, P, P]
             L.orc_stripify.argtypes = [P, P, u32, P, P, P, P, P]
-            L.orc_encode.argtypes = [P, u32, P, P, P, u32, P, u32, P, u32, C.POINTER(C.POINTER(_Blob))]
+            L.orc_encode.argtypes = [P, u32, P, P, P, u32, P, u32, P, u32, P, u32, u32,
+                                     C.POINTER(C.POINTER(_Blob))]
+            L.orc_decode_attrs.argtypes = [P, P, u32, P, u64, P, u32, u32, u32, u32, u32, P]
             L.orc_blob_free.argtypes = [C.POINTER(_Blob)]
             L.orc_blob_free.restype = None
             L.orc_dequant32.argtypes = [u32, C.c_float, C.c_float]
@@ -101,6 +105,8 @@ class Blob:
     grids: np.ndarray     # uint8 [G, 32]
     stats: dict = field(default_factory=dict)
     cones: np.ndarray | None = None  # uint8 [M, 32] normal cones (format in oracle.h)
+    # extra attribute channels: {"n_attr", "attr_bits", "adesc" uint8 [M,32], "agrids" uint8 [A,48]}
+    attrs: dict | None = None
 
     @property
     def n_meshlets(self) -> int:
@@ -158,8 +164,12 @@ def stripify(tris: np.ndarray, ids: np.ndarray):
 
 
 def encode(pos: np.ndarray, tris: np.ndarray, mtri: np.ndarray, mstart: np.ndarray,
-           bits, reuse_mode: int = 0, perm: np.ndarray | None = None, mesh_id: int = 0) -> Blob:
+           bits, reuse_mode: int = 0, perm: np.ndarray | None = None, mesh_id: int = 0,
+           attrs: np.ndarray | None = None, attr_bits: int = 16) -> Blob:
+    """attrs: optional float32 [n_verts, n_attr] extra attribute channels (n_attr <= 5)."""
     pos = np.ascontiguousarray(pos, np.float32)
+    at = None if attrs is None else np.ascontiguousarray(attrs, np.float32).reshape(pos.shape[0], -1)
+    n_attr = 0 if at is None else at.shape[1]
     tris = np.ascontiguousarray(tris, np.uint32)
     nm = mstart.size - 1
     bits = np.ascontiguousarray(np.broadcast_to(np.asarray(bits, np.uint8), (nm,)))
@@ -167,7 +177,8 @@ def encode(pos: np.ndarray, tris: np.ndarray, mtri: np.ndarray, mstart: np.ndarr
     out = C.POINTER(_Blob)()
     _check(lib().orc_encode(_p(pos), pos.shape[0], _p(tris), _p(np.ascontiguousarray(mtri, np.uint32)),
                             _p(np.ascontiguousarray(mstart, np.uint32)), nm, _p(bits), reuse_mode,
-                            _p(perm), mesh_id, C.byref(out)), "orc_encode")
+                            _p(perm), mesh_id, _p(at), n_attr, attr_bits if n_attr else 0,
+                            C.byref(out)), "orc_encode")
     b = out.contents
     try:
         desc = np.ctypeslib.as_array(b.desc, (b.n_meshlets * 32,)).copy().reshape(-1, 32) \
@@ -182,20 +193,25 @@ def encode(pos: np.ndarray, tris: np.ndarray, mtri: np.ndarray, mstart: np.ndarr
             if b.total_verts else np.zeros(0, np.uint32)
         cones = np.ctypeslib.as_array(b.cones, (b.n_meshlets * 32,)).copy().reshape(-1, 32) \
             if b.n_meshlets else np.zeros((0, 32), np.uint8)
+        attr = None
+        if b.n_attr:
+            attr = {"n_attr": int(b.n_attr), "attr_bits": int(b.attr_bits),
+                    "adesc": np.ctypeslib.as_array(b.adesc, (b.n_meshlets * 32,)).copy().reshape(-1, 32),
+                    "agrids": np.ctypeslib.as_array(b.agrids, (48,)).copy().reshape(1, 48)}
     finally:
         lib().orc_blob_free(out)
-    return Blob(desc, payload, grids, stats, cones)
+    return Blob(desc, payload, grids, stats, cones, attr)
 
 
 def encode_mesh(mesh, limits=(64, 126), bits=16, reuse_mode: int = 0, perm=None,
-                mesh_id: int = 0) -> Blob:
+                mesh_id: int = 0, attrs: np.ndarray | None = None, attr_bits: int = 16) -> Blob:
     """meshletize + encode of a ``meshgen.Mesh``; ``bits`` scalar or callable(n)->array."""
     lim = np.asarray(limits, np.uint32).reshape(-1)
     mtri, mstart, ng = meshletize(mesh.tris, mesh.n_verts, lim, mesh.tri_class)
     nm = mstart.size - 1
     b = bits(nm) if callable(bits) else np.full(nm, bits, np.uint8)
     p = perm(nm) if callable(perm) else perm
-    blob = encode(mesh.pos, mesh.tris, mtri, mstart, b, reuse_mode, p, mesh_id)
+    blob = encode(mesh.pos, mesh.tris, mtri, mstart, b, reuse_mode, p, mesh_id, attrs, attr_bits)
     blob.stats["grown_meshlets"] = ng
     blob.stats["input_tris"] = mesh.n_tris
     blob.stats["mtri"], blob.stats["mstart"] = mtri, mstart
@@ -234,7 +250,23 @@ def concat(blobs: list[Blob]) -> Blob:
         stats["vmap_per_mesh"] = vmaps
     cones = np.concatenate([b.cones for b in blobs]) \
         if all(b.cones is not None for b in blobs) else None
-    return Blob(np.concatenate(descs), np.concatenate(pays), np.concatenate(grids), stats, cones)
+    attr = None
+    if all(b.attrs is not None for b in blobs) and \
+            len({(b.attrs["n_attr"], b.attrs["attr_bits"]) for b in blobs}) == 1:
+        adescs, agrids, ag = [], [], 0
+        for i, b in enumerate(blobs):
+            a = b.attrs["adesc"].copy()
+            gid = a[:, 20].astype(np.uint32) | (a[:, 21].astype(np.uint32) << 8)
+            gid += ag
+            a[:, 20], a[:, 21] = gid & 0xFF, gid >> 8
+            g = b.attrs["agrids"].copy()
+            g.view(np.uint32).reshape(-1, 12)[:, 11] = i
+            adescs.append(a)
+            agrids.append(g)
+            ag += g.shape[0]
+        attr = {"n_attr": blobs[0].attrs["n_attr"], "attr_bits": blobs[0].attrs["attr_bits"],
+                "adesc": np.concatenate(adescs), "agrids": np.concatenate(agrids)}
+    return Blob(np.concatenate(descs), np.concatenate(pays), np.concatenate(grids), stats, cones, attr)
 
 
 def dequant32(g: int, G: float, D: float) -> float:
@@ -270,6 +302,20 @@ def decode(blob: Blob, first: int = 0, count: int | None = None, want_pos64: boo
                             _p(pos), _p(pos64)), "orc_decode")
     return (loc.reshape(-1, 3), glob.reshape(-1, 3), pos.reshape(-1, 3),
             None if pos64 is None else pos64.reshape(-1, 3))
+
+
+def decode_attrs(blob: Blob, first: int = 0, count: int | None = None) -> np.ndarray:
+    """float32 [V_total, n_attr] decoded attribute channels (meshlets outside
+    the range left zero)."""
+    a = blob.attrs
+    if count is None:
+        count = blob.n_meshlets - first
+    out = np.zeros(blob.total_verts * a["n_attr"], np.float32)
+    _check(lib().orc_decode_attrs(_p(blob.desc), _p(a["adesc"]), blob.n_meshlets, _p(blob.payload),
+                                  blob.payload.size, _p(a["agrids"]), a["agrids"].shape[0],
+                                  a["n_attr"], a["attr_bits"], first, count, _p(out)),
+           "orc_decode_attrs")
+    return out.reshape(-1, a["n_attr"])
 
 
 def view_eye(vp: np.ndarray):

@@ -179,6 +179,44 @@ static float clip_row(const float *M, int r, float x, float y, float z) {
   return fmaf(M[4 * r + 2], z, fmaf(M[4 * r + 1], y, fmaf(M[4 * r + 0], x, M[4 * r + 3])));
 }
 
+int orc_decode_attrs(const uint8_t *desc, const uint8_t *adesc, uint32_t n_meshlets,
+                     const uint8_t *payload, uint64_t payload_bytes, const uint8_t *agrids,
+                     uint32_t n_agrids, uint32_t n_attr, uint32_t attr_bits, uint32_t first,
+                     uint32_t count, float *attr) {
+  if (!desc || !adesc || !payload || !agrids || !attr || n_attr < 1 || n_attr > 5 ||
+      attr_bits < 1 || attr_bits > 32 || (uint64_t)first + count > n_meshlets)
+    return ORC_ERR_ARG;
+  for (uint32_t m = first; m < first + count; m++) {
+    desc_t d;
+    parse_desc(desc + 32 * (size_t)m, &d);
+    if (d.V < 3 || d.V > 256 || d.tp < 1 || d.tp > 256 || d.w > 8 || d.b < 1 || d.b > 32 ||
+        d.V > d.tp + 2)
+      return ORC_ERR_CORRUPT;
+    const uint8_t *ar = adesc + 32 * (size_t)m;
+    uint32_t ag = get_u16(ar + 20);
+    if (ag >= n_agrids) return ORC_ERR_CORRUPT;
+    const uint8_t *g = agrids + 48 * (size_t)ag;
+    if (get_u32(g + 40) != attr_bits) return ORC_ERR_CORRUPT;
+    uint64_t nw = (d.tp + 31) / 32;
+    uint64_t cw = d.w == 0 ? nw + ((uint64_t)d.tp - 1 + 3) / 4
+                           : 2 * nw + ((uint64_t)(d.tp + 2 - d.V) * d.w + 31) / 32;
+    uint64_t pw = (3 * (uint64_t)d.V * d.b + 31) / 32;
+    uint64_t aw = ((uint64_t)n_attr * d.V * attr_bits + 31) / 32;
+    uint64_t start = 16 * (uint64_t)d.off16;
+    if (start + 4 * (cw + pw + aw) > payload_bytes) return ORC_ERR_CORRUPT;
+    const uint8_t *AB = payload + start + 4 * (cw + pw);
+    for (uint32_t v = 0; v < d.V; v++)
+      for (uint32_t c = 0; c < n_attr; c++) {
+        uint64_t gg = (uint64_t)get_u32(ar + 4 * c) +
+                      get_bits(AB, ((uint64_t)n_attr * v + c) * attr_bits, attr_bits);
+        if (gg > 0xFFFFFFFFull) return ORC_ERR_CORRUPT;
+        attr[(size_t)n_attr * ((size_t)d.vbase + v) + c] =
+            orc_dequant32((uint32_t)gg, get_f32(g + 4 * c), get_f32(g + 20 + 4 * c));
+      }
+  }
+  return ORC_OK;
+}
+
 int orc_view_eye(const float *vp, float eye[3]) {
   double r0[3], r1[3], r3[3];
   for (int c = 0; c < 3; c++) {

@@ -34,6 +34,8 @@ typedef struct {
   uint32_t gv[256];         /* global vertex id of local vertex */
   uint32_t L[3];
   uint32_t q[256][3];
+  uint32_t La[5];           /* attribute channels: meshlet minimum on their grid */
+  uint32_t qa[256][5];
 } meshlet_t;
 
 static void put_bits(uint32_t *words, uint64_t bit, uint32_t nbits, uint64_t value) {
@@ -192,11 +194,71 @@ static int build_meshlet(const uint32_t *tris, const uint32_t *ids, uint32_t T,
   return ORC_OK;
 }
 
+/* Crack-free quantisation of n_ch extra attribute channels (Sec. 4.4, the
+ * attribute vector beyond the position) at `bits` bits, one grid for the
+ * mesh, by the same rules as the positions:
+ *   G_c = smallest value of channel c over the mesh's vertices (FP32);
+ *   Delta_c = largest meshlet extent of channel c / (2^bits - 1), in FP64,
+ *             rounded up to FP32 (1 when 0), raised one FP32 step at a time
+ *             while a meshlet still needs more than `bits` bits;
+ *   grid coordinate floor((a - G_c) / Delta_c + 1/2), La_c = meshlet minimum. */
+static int quantise_attrs(const float *attrs, uint32_t n_verts, uint32_t n_ch, uint32_t bits,
+                          meshlet_t *ms, uint32_t n_meshlets, float *G, float *D) {
+  double qmax = ldexp(1.0, (int)bits) - 1.0;
+  for (uint32_t c = 0; c < n_ch; c++) {
+    G[c] = attrs[c];
+    for (uint32_t v = 1; v < n_verts; v++)
+      if (attrs[(size_t)n_ch * v + c] < G[c]) G[c] = attrs[(size_t)n_ch * v + c];
+    double wmax = 0.0;
+    for (uint32_t m = 0; m < n_meshlets; m++) {
+      float lo = attrs[(size_t)n_ch * ms[m].gv[0] + c], hi = lo;
+      for (uint32_t i = 1; i < ms[m].V; i++) {
+        float x = attrs[(size_t)n_ch * ms[m].gv[i] + c];
+        if (x < lo) lo = x;
+        if (x > hi) hi = x;
+      }
+      if ((double)hi - (double)lo > wmax) wmax = (double)hi - (double)lo;
+    }
+    float Df = 1.0f;
+    if (wmax > 0.0) {
+      double d = wmax / qmax;
+      Df = (float)d;
+      if ((double)Df < d) Df = nextafterf(Df, INFINITY);
+    }
+    for (;;) {
+      int ok = 1;
+      for (uint32_t m = 0; m < n_meshlets && ok; m++) {
+        double lo = 0, hi = 0;
+        for (uint32_t i = 0; i < ms[m].V; i++) {
+          double y = ((double)attrs[(size_t)n_ch * ms[m].gv[i] + c] - (double)G[c]) / (double)Df;
+          double g = floor(y + 0.5);
+          if (g > 4294967295.0) return ORC_ERR_LIMIT;
+          if (i == 0 || g < lo) lo = g;
+          if (i == 0 || g > hi) hi = g;
+        }
+        if (hi - lo > qmax) { ok = 0; break; }
+        if (lo + qmax > 4294967295.0) return ORC_ERR_LIMIT;
+        ms[m].La[c] = (uint32_t)lo;
+        for (uint32_t i = 0; i < ms[m].V; i++) {
+          double y = ((double)attrs[(size_t)n_ch * ms[m].gv[i] + c] - (double)G[c]) / (double)Df;
+          ms[m].qa[i][c] = (uint32_t)(floor(y + 0.5) - lo);
+        }
+      }
+      if (ok) break;
+      Df = nextafterf(Df, INFINITY);
+    }
+    D[c] = Df;
+  }
+  return ORC_OK;
+}
+
 int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
                const uint32_t *mtri, const uint32_t *mstart,
                uint32_t n_meshlets, const uint8_t *bits, uint32_t reuse_mode,
-               const uint32_t *perm, uint32_t mesh_id, orc_blob **out) {
-  if (!pos || !tris || !mtri || !mstart || !bits || !out || n_verts == 0 || reuse_mode > 2)
+               const uint32_t *perm, uint32_t mesh_id, const float *attrs, uint32_t n_attr,
+               uint32_t attr_bits, orc_blob **out) {
+  if (!pos || !tris || !mtri || !mstart || !bits || !out || n_verts == 0 || reuse_mode > 2 ||
+      n_attr > 5 || (n_attr && (!attrs || attr_bits < 1 || attr_bits > 32)))
     return ORC_ERR_ARG;
   *out = NULL;
   for (uint32_t m = 0; m < n_meshlets; m++)
@@ -272,6 +334,9 @@ int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
     }
   }
   if (rc != ORC_OK) { free(ms); return rc; }
+  float GA[5] = {0}, DA[5] = {0};
+  if (n_attr) rc = quantise_attrs(attrs, n_verts, n_attr, attr_bits, ms, n_meshlets, GA, DA);
+  if (rc != ORC_OK) { free(ms); return rc; }
 
   /* ---- grids: one per bit width in use, ascending b ---- */
   uint32_t grid_of[33], n_grids = 0;
@@ -283,7 +348,8 @@ int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
   uint64_t total_words = 0;
   for (uint32_t m = 0; m < n_meshlets; m++) {
     meshlet_t *x = &ms[m];
-    uint64_t words = conn_words(x) + (3 * (uint64_t)x->V * x->b + 31) / 32;
+    uint64_t words = conn_words(x) + (3 * (uint64_t)x->V * x->b + 31) / 32 +
+                     ((uint64_t)n_attr * x->V * attr_bits + 31) / 32;
     total_words += (words + 3) / 4 * 4;
   }
   blob->n_meshlets = n_meshlets;
@@ -296,10 +362,24 @@ int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
   for (uint32_t m = 0; m < n_meshlets; m++) all_v += ms[m].V;
   blob->vmap = (uint32_t *)calloc((size_t)all_v + 1, sizeof(uint32_t));
   blob->cones = (uint8_t *)calloc((size_t)n_meshlets * 32 + 1, 1);
-  uint32_t *words = (uint32_t *)calloc(1024, sizeof(uint32_t)); /* >= 2*8 + 64 + 768 + 3 */
-  if (!blob->desc || !blob->payload || !blob->grids || !blob->vmap || !blob->cones || !words) {
+  blob->n_attr = n_attr;
+  blob->attr_bits = n_attr ? attr_bits : 0;
+  blob->adesc = (uint8_t *)calloc((size_t)n_meshlets * 32 + 1, 1);
+  blob->agrids = (uint8_t *)calloc(48, 1);
+  /* >= 2*8 + 64 + 768 + 5*256*32/32 + 3 words */
+  uint32_t *words = (uint32_t *)calloc(2304, sizeof(uint32_t));
+  if (!blob->desc || !blob->payload || !blob->grids || !blob->vmap || !blob->cones ||
+      !blob->adesc || !blob->agrids || !words) {
     free(words); free(ms); orc_blob_free(blob);
     return ORC_ERR_NOMEM;
+  }
+  if (n_attr) {
+    for (uint32_t c = 0; c < n_attr; c++) {
+      put_f32(blob->agrids + 4 * c, GA[c]);
+      put_f32(blob->agrids + 20 + 4 * c, DA[c]);
+    }
+    put_u32(blob->agrids + 40, attr_bits);
+    put_u32(blob->agrids + 44, mesh_id);
   }
   for (uint32_t b = 1; b <= 32; b++) {
     if (!present[b]) continue;
@@ -319,7 +399,8 @@ int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
     uint32_t nw = (x->tp + 31) / 32;
     uint64_t cw = conn_words(x);
     uint64_t pw = (3 * (uint64_t)x->V * x->b + 31) / 32;
-    uint64_t n = (cw + pw + 3) / 4 * 4;
+    uint64_t aw = ((uint64_t)n_attr * x->V * attr_bits + 31) / 32;
+    uint64_t n = (cw + pw + aw + 3) / 4 * 4;
     memset(words, 0, n * 4);
     for (uint32_t k = 0; k < x->tp; k++) put_bits(words, k, 1, x->f[k]);
     if (x->w == 0) {
@@ -331,6 +412,10 @@ int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
     for (uint32_t v = 0; v < x->V; v++)
       for (int c = 0; c < 3; c++)
         put_bits(words + cw, (3 * (uint64_t)v + c) * x->b, x->b, x->q[v][c]);
+    for (uint32_t v = 0; v < x->V; v++)
+      for (uint32_t c = 0; c < n_attr; c++)
+        put_bits(words + cw + pw, ((uint64_t)n_attr * v + c) * attr_bits, attr_bits, x->qa[v][c]);
+    for (uint32_t c = 0; c < n_attr; c++) put_u32(blob->adesc + 32 * (size_t)p + 4 * c, x->La[c]);
     for (uint64_t i = 0; i < n; i++) put_u32(blob->payload + 4 * (off_words + i), words[i]);
     uint8_t *d = blob->desc + 32 * (size_t)p;
     if (vbase + x->V > 0xFFFFFFFFull || tbase + x->tp > 0xFFFFFFFFull ||
@@ -397,5 +482,7 @@ void orc_blob_free(orc_blob *b) {
   free(b->grids);
   free(b->vmap);
   free(b->cones);
+  free(b->adesc);
+  free(b->agrids);
   free(b);
 }

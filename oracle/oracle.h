@@ -39,6 +39,11 @@
  *     triangle k >= 1 holding its stream entry I[k+2] (ceil((T'-1)/4)
  *     words), then the position words.
  *   grid entry, 32 B: f32 G[3], u32 b, f32 Delta[3], u32 mesh id.
+ *   attribute words (blobs with n_attr extra channels): after the position
+ *     words, ceil(n_attr*V*attr_bits/32) words, vertex v channel c at bit
+ *     (n_attr*v + c)*attr_bits; attribute record, 32 B per meshlet: u32 La[5]
+ *     (meshlet minimum on the attribute grid), u16 attribute grid id;
+ *     attribute grid, 48 B: f32 G[5], f32 Delta[5], u32 attr_bits, u32 mesh id.
  *   normal cone, 32 B per meshlet (blob order), the per-meshlet cull data
  *   the paper keeps beside the offsets (Sec. 3, Sec. 5 "cull information"):
  *     f32 center[3], f32 radius   a sphere holding the decoded vertices,
@@ -94,17 +99,24 @@ typedef struct {
   uint8_t *grids;
   uint32_t *vmap; /* input vertex id of every decoded vertex (total_verts) */
   uint8_t *cones; /* 32 B normal cone per meshlet (blob order) */
+  uint32_t n_attr, attr_bits; /* extra attribute channels (0..5) and their bits */
+  uint8_t *adesc; /* 32 B attribute record per meshlet (blob order) */
+  uint8_t *agrids; /* one 48 B attribute grid */
 } orc_blob;
 
 /* Encode the meshlets (mtri/mstart as produced by orc_meshletize) of one mesh.
  * bits[m]: position bits of meshlet m (1..32).  reuse_mode 0: w = 8,
  * reuse_mode 1: w = ceil(log2 V), reuse_mode 2: plain GTS (every stream
  * entry stored at 8 bits, no increment flags).  perm (may be NULL): blob slot p holds
- * meshlet perm[p].  mesh_id is written into the grid entries. */
+ * meshlet perm[p].  mesh_id is written into the grid entries.  attrs (may be
+ * NULL with n_attr = 0): n_attr (<= 5) extra attribute channels per input
+ * vertex (attrs[n_attr v + c]), quantised crack-free at attr_bits bits on one
+ * grid for the mesh, by the rules of the positions (Sec. 4.4). */
 int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
                const uint32_t *mtri, const uint32_t *mstart,
                uint32_t n_meshlets, const uint8_t *bits, uint32_t reuse_mode,
-               const uint32_t *perm, uint32_t mesh_id, orc_blob **out);
+               const uint32_t *perm, uint32_t mesh_id, const float *attrs,
+               uint32_t n_attr, uint32_t attr_bits, orc_blob **out);
 void orc_blob_free(orc_blob *b);
 
 /* FP32 dequantisation of a grid coordinate g (Sec. 4.4):
@@ -140,6 +152,15 @@ int orc_decode_cull(const uint8_t *desc, uint32_t n_meshlets,
                     uint32_t count, const float *vp, const uint8_t *cones,
                     uint32_t *tri_out, uint64_t *count_io, float *pos,
                     uint8_t *pass_out);
+
+/* Decode the attribute channels of meshlets [first, first + count) of a blob
+ * with n_attr channels at attr_bits bits (adesc / agrids: its attribute
+ * records and grids): attr[n_attr * (vertex_base + v) + c] = FP32
+ * dequantisation of La_c + q (the position formula, Sec. 4.4). */
+int orc_decode_attrs(const uint8_t *desc, const uint8_t *adesc, uint32_t n_meshlets,
+                     const uint8_t *payload, uint64_t payload_bytes, const uint8_t *agrids,
+                     uint32_t n_agrids, uint32_t n_attr, uint32_t attr_bits, uint32_t first,
+                     uint32_t count, float *attr);
 
 /* Camera position of a clip matrix: the point whose clip x, y and w are all
  * zero (rows 0, 1, 3), solved in FP64 by the cross-product inverse

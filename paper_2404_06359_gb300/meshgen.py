@@ -18,6 +18,8 @@ height-field scans, Sec. 5):
                            along its shorter diagonal, heights from 4-octave
                            value noise, triangles tagged with one of three
                            120-degree sectors (meshlet-limit classes).
+* ``vertex_attributes``    normals and texture coordinates (the rest of an
+                           8-channel attribute vector).
 * ``camera_poses``         row-major float32 view-projection matrices (OpenGL
                            clip conventions, 60 degree vertical FOV).
 * ``poisson_arrivals``     request arrival times and mesh choices.
@@ -298,6 +300,31 @@ def height_field_disc(total_tris: int = 50_000_000, seed: int = SEED_BASE + 3,
     tri_class = np.repeat(sector, 2)
     return Mesh(pos, tris, tri_class, "height_field",
                 {"radius": radius, "seed": seed, "limits": SECTOR_LIMITS})
+
+
+def vertex_attributes(mesh: Mesh) -> np.ndarray:
+    """float32 [V, 5] per-vertex attributes beyond the position, the rest of
+    an 8-channel attribute vector (position, normal, texture coordinate):
+    unit normal (area-weighted sum of the incident triangle normals) and a
+    texture coordinate -- spherical about the mesh's bounding-box centre for
+    spheres and tori, planar (x, y scaled to [0, 1]) otherwise."""
+    p = mesh.pos.astype(np.float64)
+    t = mesh.tris.astype(np.int64)
+    fn = np.cross(p[t[:, 1]] - p[t[:, 0]], p[t[:, 2]] - p[t[:, 0]])
+    n = np.zeros_like(p)
+    for c in range(3):
+        np.add.at(n, t[:, c], fn)
+    ln = np.linalg.norm(n, axis=1)
+    n = np.where(ln[:, None] > 0, n / np.maximum(ln, 1e-300)[:, None], np.array([0.0, 0.0, 1.0]))
+    lo, hi = p.min(0), p.max(0)
+    if mesh.kind in ("sphere", "torus"):
+        d = p - 0.5 * (lo + hi)
+        u = np.arctan2(d[:, 1], d[:, 0]) / (2 * np.pi) + 0.5
+        v = np.arccos(np.clip(d[:, 2] / np.maximum(np.linalg.norm(d, axis=1), 1e-300), -1, 1)) / np.pi
+    else:
+        ext = np.maximum(hi - lo, 1e-300)
+        u, v = (p[:, 0] - lo[0]) / ext[0], (p[:, 1] - lo[1]) / ext[1]
+    return np.concatenate([n, u[:, None], v[:, None]], 1).astype(np.float32)
 
 
 def meshlet_bits(n: int, seed: int, choices=(12, 16, 20)) -> np.ndarray:
