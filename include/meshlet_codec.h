@@ -99,6 +99,32 @@ typedef struct {
   uint32_t mesh_id;
 } mc_grid;
 
+/* Attribute channels beyond the position (Sec. 4.4: the attribute vector of
+ * a vertex; every channel is quantised uniformly at attr_bits bits on its
+ * own crack-free global grid, by the rules of the positions).  A blob with
+ * n_attr channels stores, after the position words of each payload block,
+ * ceil(n_attr * V * attr_bits / 32) attribute words (vertex v channel c at
+ * bit (n_attr v + c) attr_bits), plus one record per meshlet and one grid
+ * per mesh:
+ *   mc_attr_desc (32 B): La[c] = the meshlet's minimum on the attribute grid
+ *                        of channel c; grid = index of its mc_attr_grid;
+ *   mc_attr_grid (48 B): origin G[c] and step delta[c] per channel, decoded
+ *                        like the positions: a = fma((float)g, delta, G) for
+ *                        g = La + q < 2^24, else the split form of mc_grid. */
+typedef struct {
+  uint32_t La[5];
+  uint16_t grid;
+  uint16_t reserved0;
+  uint32_t reserved1[2];
+} mc_attr_desc;
+
+typedef struct {
+  float G[5];
+  float delta[5];
+  uint32_t attr_bits;
+  uint32_t mesh_id;
+} mc_attr_grid;
+
 /* Normal cone of a meshlet, 32 bytes: the per-meshlet cull data kept beside
  * the offsets (Sec. 3: the triangle normals of a meshlet form a cone, stored
  * as an axis and an opening angle; Sec. 5: 16 B of cull information per
@@ -163,6 +189,11 @@ typedef struct {
   const uint32_t *order;          /* optional: blob slot p holds meshlet order[p] */
   uint32_t mesh_id;               /* written into the grid entries */
   uint32_t n_threads;             /* 0 = hardware concurrency */
+  const float *attrs;             /* optional: n_verts x n_attr extra attribute
+                                   * channels per input vertex (e.g. normal,
+                                   * texture coordinate; Sec. 4.4) */
+  uint32_t n_attr;                /* 0..5 */
+  uint32_t attr_bits;             /* b of every attribute channel (1..32) */
 } mc_encode_params;
 
 /* Encode the meshlets of one mesh (Sec. 4.2-4.4) into a blob.
@@ -204,6 +235,10 @@ typedef struct {
   uint32_t max_block_words;   /* largest payload block, u32 words */
   uint32_t max_tris;          /* largest T' */
   const mc_cone *cones;       /* normal cone per meshlet (n_meshlets) */
+  uint32_t n_attr, attr_bits; /* extra attribute channels (0 = none) */
+  const mc_attr_desc *attr_desc;  /* n_meshlets records (n_attr > 0) */
+  const mc_attr_grid *attr_grids; /* n_attr_grids entries */
+  uint32_t n_attr_grids;
 } mc_blob_view_t;
 
 mc_status mc_blob_view(const mc_blob *b, mc_blob_view_t *v);
@@ -226,6 +261,11 @@ typedef struct {
   const mc_cone *cones;     /* optional device copy of the normal cones
                              * (n_meshlets, 16-byte aligned); NULL = the
                              * fused cull uses no cone test */
+  uint32_t n_attr, attr_bits; /* the blob's attribute channels (0 = none);
+                               * they size every payload block */
+  const mc_attr_desc *attr_desc;  /* device copies (16-byte aligned), needed by */
+  const mc_attr_grid *attr_grids; /* mc_decode_batch_vertices only */
+  uint32_t n_attr_grids;
 } mc_device_batch;
 
 /* Launch shape; zero fields take the library defaults or the autotuned
@@ -272,6 +312,16 @@ mc_status mc_decode_plain(const mc_device_batch *b, uint32_t first, uint32_t cou
 mc_status mc_decode_batch(const mc_device_batch *b, uint8_t *d_local, uint32_t *d_global,
                           float *d_pos, uint32_t *d_status, void *d_scratch,
                           const mc_tuning *t, void *stream);
+
+/* Batched decode into full vertices: as mc_decode_batch, but each decoded
+ * vertex is written as 8 FP32 (32 bytes, the vertex layout of Sec. 5):
+ * x, y, z, the n_attr attribute channels (b->attr_desc / attr_grids), and
+ * zeros up to 8.  d_vertex: f32 [8 * total_verts], 16-byte aligned.
+ * MC_ERR_INVALID_ARG if the batch has no attribute channels or their
+ * records / grids are missing. */
+mc_status mc_decode_batch_vertices(const mc_device_batch *b, uint8_t *d_local,
+                                   uint32_t *d_global, float *d_vertex, uint32_t *d_status,
+                                   void *d_scratch, const mc_tuning *t, void *stream);
 
 /* One decode request of a serving batch: a range of meshlets of a resident
  * pool batch (e.g. one mesh of it) and the request's own output buffers.

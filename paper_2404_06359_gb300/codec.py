@@ -25,7 +25,8 @@ class mc_limits(C.Structure):
 
 class mc_encode_params(C.Structure):
     _fields_ = [("pos_bits", u32), ("pos_bits_per_meshlet", P), ("reuse_mode", u32),
-                ("order", P), ("mesh_id", u32), ("n_threads", u32)]
+                ("order", P), ("mesh_id", u32), ("n_threads", u32), ("attrs", P),
+                ("n_attr", u32), ("attr_bits", u32)]
 
 
 class mc_mesh_info(C.Structure):
@@ -39,13 +40,16 @@ class mc_blob_view_t(C.Structure):
                 ("n_meshes", u32), ("vertex_map", P), ("total_tris", u64), ("total_verts", u64),
                 ("input_tris", u64), ("restarts", u64), ("split_meshlets", u64),
                 ("conn_bits", u64), ("pos_bits_total", u64), ("max_block_words", u32),
-                ("max_tris", u32), ("cones", P)]
+                ("max_tris", u32), ("cones", P), ("n_attr", u32), ("attr_bits", u32),
+                ("attr_desc", P), ("attr_grids", P), ("n_attr_grids", u32)]
 
 
 class mc_device_batch(C.Structure):
     _fields_ = [("desc", P), ("payload", P), ("grids", P), ("n_meshlets", u32), ("n_grids", u32),
                 ("payload_bytes", u64), ("total_tris", u64), ("total_verts", u64),
-                ("max_block_words", u32), ("max_tris", u32), ("cones", P)]
+                ("max_block_words", u32), ("max_tris", u32), ("cones", P),
+                ("n_attr", u32), ("attr_bits", u32), ("attr_desc", P), ("attr_grids", P),
+                ("n_attr_grids", u32)]
 
 
 class mc_request(C.Structure):
@@ -82,6 +86,8 @@ _SIGS = [
                                   C.POINTER(mc_tuning), P]),
     ("mc_decode_batch", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P,
                                   C.POINTER(mc_tuning), P]),
+    ("mc_decode_batch_vertices", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P,
+                                           C.POINTER(mc_tuning), P]),
     ("mc_decode_batch_noalloc", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P,
                                           C.POINTER(mc_tuning), P]),
     ("mc_decode_cull", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P, P,
@@ -244,6 +250,9 @@ class Blob:
             "payload": grab(v.payload, v.payload_bytes, np.uint8),
             "grids": grab(v.grids, 32 * v.n_grids, np.uint8).reshape(-1, 32),
             "cones": grab(v.cones, 32 * v.n_meshlets, np.uint8).reshape(-1, 32),
+            "attr_desc": grab(v.attr_desc, 32 * v.n_meshlets if v.n_attr else 0,
+                              np.uint8).reshape(-1, 32),
+            "attr_grids": grab(v.attr_grids, 48 * v.n_attr_grids, np.uint8).reshape(-1, 48),
             "vertex_map": grab(v.vertex_map, v.total_verts, np.uint32),
             "meshes": meshes,
         }
@@ -252,7 +261,7 @@ class Blob:
         v = self.view()
         keys = ("n_meshlets", "payload_bytes", "n_grids", "n_meshes", "total_tris", "total_verts",
                 "input_tris", "restarts", "split_meshlets", "conn_bits", "pos_bits_total",
-                "max_block_words", "max_tris")
+                "max_block_words", "max_tris", "n_attr", "attr_bits")
         return {k: int(getattr(v, k)) for k in keys}
 
     def __del__(self):
@@ -262,14 +271,19 @@ class Blob:
 
 
 def mc_encode(meshlets: Meshlets, pos: np.ndarray, pos_bits=16, reuse_mode: int = 0, order=None,
-              mesh_id: int = 0, n_threads: int = 0) -> Blob:
+              mesh_id: int = 0, n_threads: int = 0, attrs: np.ndarray | None = None,
+              attr_bits: int = 16) -> Blob:
+    """attrs: optional float32 [n_verts, n_attr] extra attribute channels (n_attr <= 5)."""
     pos = np.ascontiguousarray(pos, np.float32)
     per = None
     if np.ndim(pos_bits) > 0:
         per = np.ascontiguousarray(pos_bits, np.uint8)
     order = None if order is None else np.ascontiguousarray(order, np.uint32)
+    at = None if attrs is None else np.ascontiguousarray(attrs, np.float32).reshape(pos.shape[0], -1)
+    n_attr = 0 if at is None else at.shape[1]
     p = mc_encode_params(int(pos_bits) if per is None else 0, _np_ptr(per), reuse_mode,
-                         _np_ptr(order), mesh_id, n_threads)
+                         _np_ptr(order), mesh_id, n_threads, _np_ptr(at), n_attr,
+                         attr_bits if n_attr else 0)
     h = P()
     _check(lib().mc_encode(meshlets._h, _np_ptr(pos), pos.shape[0], C.byref(p), C.byref(h)),
            "mc_encode")
@@ -288,32 +302,37 @@ class DeviceBatch:
     """A blob copied into device memory (torch uint8 tensors) plus the
     ``mc_device_batch`` that points at it."""
 
-    def __init__(self, blob: Blob, device="cuda", cones: bool = False):
+    def __init__(self, blob: Blob, device="cuda", cones: bool = False, attrs: bool = False):
         """cones: also copy the normal cones (enables the cone test of the
-        fused cull)."""
+        fused cull); attrs: also copy the attribute records and grids (for
+        mc_decode_batch_vertices)."""
         a = blob.arrays()
         self._init(a["desc"], a["payload"], a["grids"], blob.stats(), device,
-                   a["cones"] if cones else None)
+                   a["cones"] if cones else None,
+                   (a["attr_desc"], a["attr_grids"]) if attrs else None)
         self.meshes = a["meshes"]
 
     @classmethod
     def from_arrays(cls, desc, payload, grids, total_tris, total_verts, max_block_words,
-                    max_tris=256, device="cuda", cones=None):
+                    max_tris=256, device="cuda", cones=None, attrs: dict | None = None):
         """Wrap blob arrays that did not come from ``mc_encode`` (e.g. a
         hand-packed stream); sizes are the caller's; cones (uint8 [M,32])
-        optional."""
+        optional; attrs: {"n_attr", "attr_bits", "adesc", "agrids"} of a blob
+        with attribute channels (optional)."""
         self = cls.__new__(cls)
         stats = {"n_meshlets": desc.shape[0], "n_grids": grids.shape[0],
                  "payload_bytes": payload.size, "total_tris": total_tris,
                  "total_verts": total_verts, "max_block_words": max_block_words,
-                 "max_tris": max_tris}
+                 "max_tris": max_tris, "n_attr": attrs["n_attr"] if attrs else 0,
+                 "attr_bits": attrs["attr_bits"] if attrs else 0}
         self._init(np.asarray(desc, np.uint8), np.asarray(payload, np.uint8),
                    np.asarray(grids, np.uint8), stats, device,
-                   None if cones is None else np.asarray(cones, np.uint8))
+                   None if cones is None else np.asarray(cones, np.uint8),
+                   (attrs["adesc"], attrs["agrids"]) if attrs else None)
         self.meshes = []
         return self
 
-    def _init(self, desc, payload, grids, stats, device, cones=None):
+    def _init(self, desc, payload, grids, stats, device, cones=None, attr_arrays=None):
         import torch
         self.stats = stats
         self.desc = torch.from_numpy(np.ascontiguousarray(desc).reshape(-1)).to(device)
@@ -322,12 +341,20 @@ class DeviceBatch:
         self.grids = torch.from_numpy(np.ascontiguousarray(grids).reshape(-1)).to(device)
         self.cones = None if cones is None or cones.size == 0 else \
             torch.from_numpy(np.ascontiguousarray(cones).reshape(-1)).to(device)
+        self.attr_desc = self.attr_grids = None
+        if attr_arrays is not None and attr_arrays[0].size:
+            self.attr_desc = torch.from_numpy(np.ascontiguousarray(attr_arrays[0]).reshape(-1)).to(device)
+            self.attr_grids = torch.from_numpy(np.ascontiguousarray(attr_arrays[1]).reshape(-1)).to(device)
         s = self.stats
         self.c = mc_device_batch(self.desc.data_ptr(), self.payload.data_ptr(), self.grids.data_ptr(),
                                  s["n_meshlets"], s["n_grids"], s["payload_bytes"], s["total_tris"],
                                  s["total_verts"], max(1, s["max_block_words"]),
                                  s.get("max_tris", 256),
-                                 None if self.cones is None else self.cones.data_ptr())
+                                 None if self.cones is None else self.cones.data_ptr(),
+                                 s.get("n_attr", 0), s.get("attr_bits", 0),
+                                 None if self.attr_desc is None else self.attr_desc.data_ptr(),
+                                 None if self.attr_grids is None else self.attr_grids.data_ptr(),
+                                 0 if self.attr_grids is None else self.attr_grids.numel() // 48)
 
     def outputs(self, local=True, global_=True, device="cuda"):
         import torch
@@ -357,6 +384,16 @@ def mc_decode_batch(db: DeviceBatch, d_local, d_global, d_pos, d_status, d_scrat
     _check(lib().mc_decode_batch(C.byref(db.c), _tptr(d_local), _tptr(d_global), _tptr(d_pos),
                                  _tptr(d_status), _tptr(d_scratch), _tuning(tuning), _stream(stream)),
            "mc_decode_batch")
+
+
+def mc_decode_batch_vertices(db: DeviceBatch, d_local, d_global, d_vertex, d_status, d_scratch,
+                             tuning=None, stream=None):
+    """Batched decode writing full 32-byte vertices (x, y, z, attribute
+    channels, zero padding) into d_vertex (float32 [8 * total_verts])."""
+    _check(lib().mc_decode_batch_vertices(C.byref(db.c), _tptr(d_local), _tptr(d_global),
+                                          _tptr(d_vertex), _tptr(d_status), _tptr(d_scratch),
+                                          _tuning(tuning), _stream(stream)),
+           "mc_decode_batch_vertices")
 
 
 def mc_decode_batch_noalloc(db: DeviceBatch, d_local, d_global, d_pos, d_status, tuning=None,

@@ -53,9 +53,14 @@ mc_status check_batch(const mc_device_batch *b) {
   if (!aligned(b->desc, 16) || !aligned(b->payload, 16) || !aligned(b->grids, 16))
     return MC_ERR_INVALID_ARG;
   if (b->n_grids == 0 || b->n_grids > 65536) return MC_ERR_INVALID_ARG;
-  if (b->max_block_words == 0 || b->max_block_words > 2 * 8 + 64 + 768 + 4) return MC_ERR_INVALID_ARG;
+  // largest block: 2 x 8 flag words, 64 reuse words, 768 position words and
+  // 1280 attribute words (5 channels x 256 vertices x 32 bits), padded
+  if (b->max_block_words == 0 || b->max_block_words > 2 * 8 + 64 + 768 + 1280 + 4)
+    return MC_ERR_INVALID_ARG;
   if (b->payload_bytes % 16) return MC_ERR_INVALID_ARG;
   if (b->cones && !aligned(b->cones, 16)) return MC_ERR_INVALID_ARG;
+  if (b->n_attr > 5 || (b->n_attr && (b->attr_bits < 1 || b->attr_bits > 32)))
+    return MC_ERR_INVALID_ARG;
   return MC_OK;
 }
 
@@ -71,6 +76,11 @@ BatchArgs args_of(const mc_device_batch *b) {
   a.total_verts = b->total_verts;
   a.max_block_words = b->max_block_words;
   a.max_tris = (b->max_tris == 0 || b->max_tris > 256) ? 256 : b->max_tris;
+  a.n_attr = b->n_attr;
+  a.attr_bits = b->n_attr ? b->attr_bits : 0;
+  a.attr_desc = b->attr_desc;
+  a.attr_grids = b->attr_grids;
+  a.n_attr_grids = b->n_attr_grids;
   return a;
 }
 
@@ -101,22 +111,23 @@ mc_tuning resolve_batch(const mc_device_batch *b, const mc_tuning *t) {
 
 mc_status launch_batch_checked(const mc_device_batch *b, uint8_t *d_local, uint32_t *d_global,
                                float *d_pos, uint32_t *d_status, void *d_scratch,
-                               const mc_tuning &r, cudaStream_t s) {
+                               const mc_tuning &r, cudaStream_t s, bool vertices = false) {
   if (r.warps_per_cta < 1 || r.warps_per_cta > 32 || r.meshlets_per_grab < 1 ||
       r.meshlets_per_grab > 16)
     return MC_ERR_INVALID_ARG;
   // a grab's two pipeline buffers live in shared memory: shrink the grab
   // until the requested number of warps fits on an SM
   uint32_t grab = r.meshlets_per_grab;
-  int occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, grab);
-  while (occ <= 0 && grab > 1) occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, --grab);
+  int occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, grab, vertices);
+  while (occ <= 0 && grab > 1)
+    occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, --grab, vertices);
   if (occ <= 0) return MC_ERR_INVALID_ARG;
   uint32_t per_sm = std::min<uint32_t>(r.ctas_per_sm, (uint32_t)occ);
   uint32_t ctas = per_sm * (uint32_t)sm_count();
   if (ctas == 0) return MC_ERR_CUDA;
-  cudaError_t e = launch_batch(args_of(b), ctas, r.warps_per_cta, grab,
-                               b->max_block_words, r.checked != 0, d_local, d_global, d_pos,
-                               d_status, static_cast<uint32_t *>(d_scratch), s);
+  cudaError_t e = launch_batch(args_of(b), ctas, r.warps_per_cta, grab, b->max_block_words,
+                               r.checked != 0, vertices, d_local, d_global, d_pos, d_status,
+                               static_cast<uint32_t *>(d_scratch), s);
   if (e == cudaSuccess) g_launches++;
   return from_cuda(e);
 }
@@ -213,6 +224,25 @@ extern "C" mc_status mc_decode_batch(const mc_device_batch *b, uint8_t *d_local,
   mc_tuning r = resolve_batch(b, t);
   return launch_batch_checked(b, d_local, d_global, d_pos, d_status, d_scratch, r,
                               static_cast<cudaStream_t>(stream));
+}
+
+extern "C" mc_status mc_decode_batch_vertices(const mc_device_batch *b, uint8_t *d_local,
+                                              uint32_t *d_global, float *d_vertex,
+                                              uint32_t *d_status, void *d_scratch,
+                                              const mc_tuning *t, void *stream) {
+  if (!b) return MC_ERR_INVALID_ARG;
+  mc_status st = check_batch(b);
+  if (st != MC_OK) return st;
+  if (b->n_attr == 0 || !b->attr_desc || !b->attr_grids || b->n_attr_grids == 0 ||
+      !aligned(b->attr_desc, 16) || !aligned(b->attr_grids, 16))
+    return MC_ERR_INVALID_ARG;
+  if (b->n_meshlets == 0) return MC_OK;
+  if (!d_vertex || !aligned(d_vertex, 16) || !d_scratch || !aligned(d_scratch, 16) ||
+      !aligned(d_local, 16) || !aligned(d_global, 16))
+    return MC_ERR_INVALID_ARG;
+  mc_tuning r = resolve_batch(b, t);
+  return launch_batch_checked(b, d_local, d_global, d_vertex, d_status, d_scratch, r,
+                              static_cast<cudaStream_t>(stream), true);
 }
 
 namespace {

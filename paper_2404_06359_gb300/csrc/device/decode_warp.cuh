@@ -36,6 +36,7 @@ constexpr uint32_t kStreamBytes = 272;
 
 struct Desc {
   uint32_t off16, vbase, tbase, V, T, w, b, grid, L[3];
+  uint32_t aw;  // attribute words after the position words (0 without attribute channels)
 };
 
 __device__ __forceinline__ Desc unpack_desc(uint4 a, uint4 c) {
@@ -51,6 +52,7 @@ __device__ __forceinline__ Desc unpack_desc(uint4 a, uint4 c) {
   r.L[0] = c.y;
   r.L[1] = c.z;
   r.L[2] = c.w;
+  r.aw = 0;
   return r;
 }
 
@@ -90,7 +92,7 @@ __device__ __forceinline__ uint32_t conn_words(const Desc &d) {
 
 // Payload block size in u32 words (unpadded) of a meshlet.
 __device__ __forceinline__ uint32_t block_words(const Desc &d) {
-  return conn_words(d) + (3 * d.V * d.b + 31) / 32;
+  return conn_words(d) + (3 * d.V * d.b + 31) / 32 + d.aw;
 }
 
 struct BatchArgs {
@@ -101,7 +103,17 @@ struct BatchArgs {
   uint64_t payload_bytes, total_tris, total_verts;
   uint32_t max_block_words;  // capacity of one meshlet's shared-memory slot
   uint32_t max_tris;         // largest T' of the batch (sizes per-warp output buffers)
+  uint32_t n_attr, attr_bits;  // attribute channels after the positions (0 = none)
+  const mc_attr_desc *attr_desc;
+  const mc_attr_grid *attr_grids;
+  uint32_t n_attr_grids;
 };
+
+// The attribute words of a meshlet follow its position words.
+__device__ __forceinline__ Desc with_attrs(Desc d, const BatchArgs &a) {
+  d.aw = (a.n_attr * d.V * a.attr_bits + 31) / 32;
+  return d;
+}
 
 // Header sanity (all builds): a descriptor that passes cannot make the decode
 // read or write outside its buffers.
@@ -313,14 +325,60 @@ __device__ __forceinline__ void stg3_f32_if(float *g, float x, float y, float z,
       : "memory");
 }
 
+__device__ __forceinline__ void stg4_f32_if(float *g, float x, float y, float z, float w, bool p) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %5, 0;\n @q st.global.v4.f32 [%0], {%1, %2, %3, %4};\n}" ::"l"(g),
+      "f"(x), "f"(y), "f"(z), "f"(w), "r"((uint32_t)p)
+      : "memory");
+}
+
+// Full vertices of one staged meshlet: 8 FP32 per vertex -- x, y, z, then
+// the n_attr attribute channels (q at bit (n_attr v + c) attr_bits of the
+// attribute words that follow the position words; La_c + q dequantised with
+// the channel's G_c and D_c like a position), then zeros -- written as two
+// 16-byte stores.  sa holds La[0..4], G[5..9] and D[10..14] (float bits) of
+// the meshlet in shared memory (a 64-byte slot).
+template <bool B16>
+__device__ __forceinline__ void vertex_stage_full(const Desc &d, const Grid &g, const uint32_t *sw,
+                                                  const uint32_t *sa, uint32_t n_attr,
+                                                  uint32_t attr_bits, uint32_t lane,
+                                                  float *out_vertex) {
+  const uint32_t *pw = sw + conn_words(d);
+  const uint32_t *aw = pw + (3 * d.V * d.b + 31) / 32;
+  float *ov = out_vertex + 8ull * (d.vbase + lane);
+  const uint32_t vpasses = (d.V + 31) >> 5;
+  uint32_t v = lane;
+  for (uint32_t i = 0; i < vpasses; i++, v += 32, ov += 256) {
+    const uint32_t vv = min(v, d.V - 1);  // idle lanes recompute the last vertex
+    uint32_t q[3];
+    vertex_q<B16>(pw, vv, d.b, q);
+    float a[5];
+#pragma unroll
+    for (uint32_t c = 0; c < 5; c++) {
+      a[c] = 0.0f;
+      if (c < n_attr) {
+        const uint32_t qa = extract(aw, (n_attr * vv + c) * attr_bits, attr_bits);
+        a[c] = dequant(sa[c] + qa, __uint_as_float(sa[5 + c]), __uint_as_float(sa[10 + c]));
+      }
+    }
+    const bool live = v < d.V;
+    stg4_f32_if(ov, dequant(d.L[0] + q[0], g.G[0], g.D[0]), dequant(d.L[1] + q[1], g.G[1], g.D[1]),
+                dequant(d.L[2] + q[2], g.G[2], g.D[2]), a[0], live);
+    stg4_f32_if(ov + 4, a[1], a[2], a[3], a[4], live);
+  }
+  __syncwarp();
+}
+
 // Full decode of one staged meshlet into the batch outputs: the strip walk
 // of walk_triangles (same arithmetic) written out flat, with predicated
 // stores and per-lane output pointers advanced by one word of triangles per
 // pass.
-template <bool CHECKED, bool B16, int RM>
+template <bool CHECKED, bool B16, int RM, bool VTX>
 __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, const uint32_t *sw,
                                               uint8_t *sI, uint32_t lane, uint8_t *out_local,
-                                              uint32_t *out_global, float *out_pos) {
+                                              uint32_t *out_global, float *out_pos,
+                                              const uint32_t *sa, uint32_t n_attr,
+                                              uint32_t attr_bits) {
   if (CHECKED && !stream_header_ok(d, sw)) return false;
   const uint32_t nw = (d.T + 31) >> 5;
   const uint32_t a_sw = smem_addr(sw);
@@ -372,6 +430,10 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
     if (D) lastT = 32 * i + msb(D);
   }
   if (CHECKED && __any_sync(kFull, bad)) return false;
+  if (VTX) {
+    vertex_stage_full<B16>(d, g, sw, sa, n_attr, attr_bits, lane, out_pos);
+    return true;
+  }
   // positions
   const uint32_t *pw = sw + conn_words(d);
   float *op = out_pos + 3ull * (d.vbase + lane);
@@ -398,22 +460,25 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
   return true;
 }
 
-template <bool CHECKED>
+// out_pos: positions (3 FP32 per vertex) or, VTX, full vertices (8 FP32 per
+// vertex, sa / n_attr / attr_bits as for vertex_stage_full).
+template <bool CHECKED, bool VTX = false>
 __device__ __forceinline__ bool decode_dispatch(const Desc &d, const Grid &g, const uint32_t *sw,
                                                 uint8_t *sI, uint32_t lane, uint8_t *out_local,
-                                                uint32_t *out_global, float *out_pos) {
+                                                uint32_t *out_global, float *out_pos,
+                                                const uint32_t *sa = nullptr, uint32_t n_attr = 0,
+                                                uint32_t attr_bits = 0) {
+#define MC_DEC(B, R) \
+  decode_staged<CHECKED, B, R, VTX>(d, g, sw, sI, lane, out_local, out_global, out_pos, sa, n_attr, attr_bits)
   if (d.b == 16) {
-    if (d.w == 8)
-      return decode_staged<CHECKED, true, kReuseBytes>(d, g, sw, sI, lane, out_local, out_global, out_pos);
-    if (d.w == 0)
-      return decode_staged<CHECKED, true, kPlainGts>(d, g, sw, sI, lane, out_local, out_global, out_pos);
-    return decode_staged<CHECKED, true, kReuseBits>(d, g, sw, sI, lane, out_local, out_global, out_pos);
+    if (d.w == 8) return MC_DEC(true, kReuseBytes);
+    if (d.w == 0) return MC_DEC(true, kPlainGts);
+    return MC_DEC(true, kReuseBits);
   }
-  if (d.w == 8)
-    return decode_staged<CHECKED, false, kReuseBytes>(d, g, sw, sI, lane, out_local, out_global, out_pos);
-  if (d.w == 0)
-    return decode_staged<CHECKED, false, kPlainGts>(d, g, sw, sI, lane, out_local, out_global, out_pos);
-  return decode_staged<CHECKED, false, kReuseBits>(d, g, sw, sI, lane, out_local, out_global, out_pos);
+  if (d.w == 8) return MC_DEC(false, kReuseBytes);
+  if (d.w == 0) return MC_DEC(false, kPlainGts);
+  return MC_DEC(false, kReuseBits);
+#undef MC_DEC
 }
 
 }  // namespace mcdev

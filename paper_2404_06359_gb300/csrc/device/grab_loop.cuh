@@ -74,7 +74,8 @@ __host__ __device__ inline uint32_t grab_loop_bytes(uint32_t max_block_words, ui
 // called by all lanes once the descriptors of the grab's cnt meshlets
 // m0 .. m0 + cnt - 1 are in shared memory (sdesc, 8 words each, not yet
 // validated) and returns a warp-uniform word;
-// body(d, sw, j, word) is then called by all lanes for every meshlet j of the
+// body(d, sw, j, word) is then called by all lanes for every meshlet j (batch
+// index m0 + j) of the
 // grab whose header passes header_ok, with sw its payload block in shared
 // memory; a failed header sets MC_ERR_CORRUPT.
 struct NoPre {
@@ -134,7 +135,7 @@ __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab,
     const uint32_t word = pre(m0, sdesc, cnt);
     for (uint32_t j = 0; j < cnt; j++) {
       const uint4 *sd = reinterpret_cast<const uint4 *>(sdesc) + 2 * j;
-      const Desc d = unpack_desc(sd[0], sd[1]);
+      const Desc d = with_attrs(unpack_desc(sd[0], sd[1]), a);
       if (!header_ok(d, a)) {
         if (lane == 0) set_status(status, MC_ERR_CORRUPT);
         continue;
@@ -150,7 +151,7 @@ __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab,
         __syncwarp();
         sw = spay;
       }
-      body(d, sw, j, word);
+      body(d, sw, j, word, m0 + j);
     }
     __syncwarp();
   }

@@ -18,9 +18,10 @@ __host__ __device__ inline uint32_t warp_smem_bytes(uint32_t max_block_words) {
   return 4 * warp_words(max_block_words) + kStreamBytes;
 }
 uint32_t decode_smem_per_warp(uint32_t max_block_words) { return warp_smem_bytes(max_block_words); }
-// Batched kernel: the grab loop's buffers, then the strip stream.
+// Batched kernel: the grab loop's buffers, a 64-byte attribute slot, then the
+// strip stream.
 uint32_t batch_smem_per_warp(uint32_t max_block_words, uint32_t per_grab) {
-  return grab_loop_bytes(max_block_words, per_grab) + kStreamBytes;
+  return grab_loop_bytes(max_block_words, per_grab) + 64 + kStreamBytes;
 }
 
 template <bool CHECKED>
@@ -28,7 +29,7 @@ __device__ __forceinline__ void decode_one(const BatchArgs &a, uint32_t m, uint3
                                            uint8_t *sI, uint32_t lane, uint8_t *out_local,
                                            uint32_t *out_global, float *out_pos,
                                            uint32_t *status) {
-  const Desc d = load_desc(a.desc + m);
+  const Desc d = with_attrs(load_desc(a.desc + m), a);
   if (!header_ok(d, a)) {
     if (lane == 0) set_status(status, MC_ERR_CORRUPT);
     return;
@@ -59,8 +60,11 @@ __global__ void decode_plain_kernel(BatchArgs a, uint32_t first, uint32_t count,
 enum { kQueue = 0, kDone = 1, kCount = 2 };
 
 // Persistent batched decode: each warp runs the grab loop and decodes the
-// staged meshlets one after another from shared memory.
-template <bool CHECKED>
+// staged meshlets one after another from shared memory.  VTX: out_pos
+// receives full 8-float vertices (positions + attribute channels); the
+// meshlet's attribute minima and grid are first copied into the warp's
+// 64-byte slot in front of the strip stream.
+template <bool CHECKED, bool VTX>
 __global__ void __launch_bounds__(512) decode_batch_kernel(BatchArgs a, uint32_t per_grab,
                                                            uint32_t smem_per_warp, uint8_t *out_local,
                                                            uint32_t *out_global, float *out_pos,
@@ -69,10 +73,32 @@ __global__ void __launch_bounds__(512) decode_batch_kernel(BatchArgs a, uint32_t
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   uint8_t *base = smem + warp * smem_per_warp;
   uint8_t *sI = base + smem_per_warp - kStreamBytes;
+  uint32_t *sa = reinterpret_cast<uint32_t *>(sI - 64);
   grab_loop(a, per_grab, base, lane, scratch + kQueue, status, NoPre{},
-            [&](const Desc &d, const uint32_t *sw, uint32_t, uint32_t) {
+            [&](const Desc &d, const uint32_t *sw, uint32_t, uint32_t, uint32_t m) {
               const Grid g = load_grid(a.grids + d.grid);
-              if (!decode_dispatch<CHECKED>(d, g, sw, sI, lane, out_local, out_global, out_pos) &&
+              if (VTX) {
+                bool ok = true;
+                if (lane < a.n_attr) {
+                  const mc_attr_desc *ad = a.attr_desc + m;
+                  const uint32_t gi = __ldg(&ad->grid);
+                  ok = gi < a.n_attr_grids;
+                  if (ok) {
+                    const mc_attr_grid *ag = a.attr_grids + gi;
+                    ok = __ldg(&ag->attr_bits) == a.attr_bits;
+                    sa[lane] = __ldg(&ad->La[lane]);
+                    sa[5 + lane] = __float_as_uint(__ldg(&ag->G[lane]));
+                    sa[10 + lane] = __float_as_uint(__ldg(&ag->delta[lane]));
+                  }
+                }
+                if (!__all_sync(kFull, ok)) {
+                  if (lane == 0) set_status(status, MC_ERR_CORRUPT);
+                  return;
+                }
+                __syncwarp();
+              }
+              if (!decode_dispatch<CHECKED, VTX>(d, g, sw, sI, lane, out_local, out_global, out_pos,
+                                                 sa, a.n_attr, a.attr_bits) &&
                   lane == 0)
                 set_status(status, MC_ERR_CORRUPT);
             });
@@ -129,7 +155,7 @@ __global__ void __launch_bounds__(512) decode_requests_kernel(BatchArgs a, const
         if (lane == 0) set_status(status, MC_ERR_INVALID_ARG);
         continue;
       }
-      Desc d = load_desc(a.desc + m);
+      Desc d = with_attrs(load_desc(a.desc + m), a);
       d.tbase -= __ldg(&q->tri_base);
       d.vbase -= __ldg(&q->vertex_base);
       BatchArgs ra = a;
@@ -414,7 +440,7 @@ __global__ void __launch_bounds__(MAX_THREADS) decode_cull_kernel(BatchArgs a, c
                 [&](uint32_t m0, const uint32_t *sdesc, uint32_t cnt) {
                   return grab_outside(a, m0, sdesc, cnt, s_M, cones, s_eye, eye_ok, lane);
                 },
-                [&](const Desc &d, const uint32_t *sw, uint32_t j, uint32_t outside) {
+                [&](const Desc &d, const uint32_t *sw, uint32_t j, uint32_t outside, uint32_t) {
                   if ((outside >> j) & 1u) return;
                   const Grid g = load_grid(a.grids + d.grid);
                   // d.T <= max_tris (header_ok), so the meshlet fits an emptied buffer
@@ -530,22 +556,32 @@ cudaError_t launch_plain(const BatchArgs &a, uint32_t first, uint32_t count, uin
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch(const BatchArgs &a, uint32_t ctas, uint32_t warps, uint32_t per_grab,
-                         uint32_t max_block_words, bool checked, uint8_t *out_local,
-                         uint32_t *out_global, float *out_pos, uint32_t *status,
-                         uint32_t *scratch, cudaStream_t s) {
-  const uint32_t spw = batch_smem_per_warp(max_block_words, per_grab);
-  const uint32_t smem = spw * warps;
-  if (checked) {
-    prepare(fn(decode_batch_kernel<true>));
-    decode_batch_kernel<true><<<ctas, warps * 32, smem, s>>>(a, per_grab, spw, out_local,
-                                                             out_global, out_pos, status, scratch);
-  } else {
-    prepare(fn(decode_batch_kernel<false>));
-    decode_batch_kernel<false><<<ctas, warps * 32, smem, s>>>(a, per_grab, spw, out_local,
-                                                              out_global, out_pos, status, scratch);
-  }
+namespace {
+template <bool CHECKED, bool VTX>
+cudaError_t launch_batch_t(const BatchArgs &a, uint32_t ctas, uint32_t warps, uint32_t per_grab,
+                           uint32_t spw, uint8_t *out_local, uint32_t *out_global, float *out_pos,
+                           uint32_t *status, uint32_t *scratch, cudaStream_t s) {
+  prepare(fn(decode_batch_kernel<CHECKED, VTX>));
+  decode_batch_kernel<CHECKED, VTX><<<ctas, warps * 32, spw * warps, s>>>(
+      a, per_grab, spw, out_local, out_global, out_pos, status, scratch);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_batch(const BatchArgs &a, uint32_t ctas, uint32_t warps, uint32_t per_grab,
+                         uint32_t max_block_words, bool checked, bool vertices,
+                         uint8_t *out_local, uint32_t *out_global, float *out_pos,
+                         uint32_t *status, uint32_t *scratch, cudaStream_t s) {
+  const uint32_t spw = batch_smem_per_warp(max_block_words, per_grab);
+  if (vertices)
+    return checked ? launch_batch_t<true, true>(a, ctas, warps, per_grab, spw, out_local, out_global,
+                                                out_pos, status, scratch, s)
+                   : launch_batch_t<false, true>(a, ctas, warps, per_grab, spw, out_local,
+                                                 out_global, out_pos, status, scratch, s);
+  return checked ? launch_batch_t<true, false>(a, ctas, warps, per_grab, spw, out_local, out_global,
+                                               out_pos, status, scratch, s)
+                 : launch_batch_t<false, false>(a, ctas, warps, per_grab, spw, out_local, out_global,
+                                                out_pos, status, scratch, s);
 }
 
 namespace {
@@ -606,10 +642,15 @@ int max_ctas_per_sm_requests(uint32_t warps, uint32_t max_block_words) {
   return occupancy(fn(decode_requests_kernel<false>), warps * 32, smem);
 }
 
-int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words, uint32_t per_grab) {
+int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words, uint32_t per_grab,
+                          bool vertices) {
   const int smem = (int)(batch_smem_per_warp(max_block_words, per_grab) * warps);
-  prepare(fn(decode_batch_kernel<true>));
-  return occupancy(fn(decode_batch_kernel<false>), warps * 32, smem);
+  if (vertices) {
+    prepare(fn(decode_batch_kernel<true, true>));
+    return occupancy(fn(decode_batch_kernel<false, true>), warps * 32, smem);
+  }
+  prepare(fn(decode_batch_kernel<true, false>));
+  return occupancy(fn(decode_batch_kernel<false, false>), warps * 32, smem);
 }
 
 int max_ctas_per_sm_cull(uint32_t warps, uint32_t max_block_words, uint32_t max_tris,

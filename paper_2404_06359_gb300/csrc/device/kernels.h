@@ -17,17 +17,19 @@ cudaError_t launch_plain(const BatchArgs &a, uint32_t first, uint32_t count, uin
                          uint32_t max_block_words, bool checked, uint8_t *out_local,
                          uint32_t *out_global, float *out_pos, uint32_t *status, cudaStream_t s);
 
+// vertices: out_pos receives full 8-float vertices (positions + attributes)
 cudaError_t launch_batch(const BatchArgs &a, uint32_t ctas, uint32_t warps, uint32_t per_grab,
-                         uint32_t max_block_words, bool checked, uint8_t *out_local,
-                         uint32_t *out_global, float *out_pos, uint32_t *status,
-                         uint32_t *scratch, cudaStream_t s);
+                         uint32_t max_block_words, bool checked, bool vertices,
+                         uint8_t *out_local, uint32_t *out_global, float *out_pos,
+                         uint32_t *status, uint32_t *scratch, cudaStream_t s);
 
 cudaError_t launch_cull(const BatchArgs &a, const float *view_proj, const mc_cone *cones,
                         uint32_t ctas, uint32_t warps, uint32_t per_grab, bool checked,
                         uint32_t *tri_out, uint32_t *tri_count, float *out_pos, uint32_t *status,
                         uint32_t *scratch, cudaStream_t s);
 
-int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words, uint32_t per_grab);
+int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words, uint32_t per_grab,
+                          bool vertices = false);
 int max_ctas_per_sm_cull(uint32_t warps, uint32_t max_block_words, uint32_t max_tris,
                          uint32_t per_grab);
 

@@ -35,6 +35,7 @@ struct Packed {
   std::vector<uint8_t> ent;     // plain GTS (w = 0): stream entry of triangles 1..T'-1
   uint32_t flag_words[8], inc_words[8];
   uint32_t L[3];
+  uint32_t La[5];  // attribute channels: meshlet minimum on their grid
 };
 
 inline void put_bits(uint32_t *w, uint64_t bit, uint32_t nbits, uint32_t value) {
@@ -135,6 +136,10 @@ extern "C" mc_status mc_encode(const mc_meshlets *m, const float *pos, uint32_t 
     for (uint32_t i = 0; i < nm; i++)
       if (p->pos_bits_per_meshlet[i] < 1 || p->pos_bits_per_meshlet[i] > 32)
         return MC_ERR_INVALID_ARG;
+  const uint32_t n_attr = p->n_attr;
+  if (n_attr > 5 || (n_attr && (!p->attrs || p->attr_bits < 1 || p->attr_bits > 32)))
+    return MC_ERR_INVALID_ARG;
+  const uint32_t attr_bits = n_attr ? p->attr_bits : 0;
   if (p->order) {
     std::vector<uint8_t> seen(nm, 0);
     for (uint32_t i = 0; i < nm; i++) {
@@ -201,7 +206,7 @@ extern "C" mc_status mc_encode(const mc_meshlets *m, const float *pos, uint32_t 
           // plain GTS (w = 0) = L/R words + one byte per triangle k >= 1
           const uint32_t conn = x.w ? 2 * ((tp + 31) / 32) + (x.R * x.w + 31) / 32
                                     : (tp + 31) / 32 + (tp + 2) / 4;
-          const uint32_t words = conn + (3 * x.V * x.b + 31) / 32;
+          const uint32_t words = conn + (3 * x.V * x.b + 31) / 32 + (n_attr * x.V * attr_bits + 31) / 32;
           x.words = (words + 3) / 4 * 4;
         },
         256);
@@ -268,6 +273,56 @@ extern "C" mc_status mc_encode(const mc_meshlets *m, const float *pos, uint32_t 
       }
     }
 
+    // ---- attribute channels: one crack-free grid per channel for the mesh,
+    // by the rules of the positions (Sec. 4.4)
+    float GA[5] = {0, 0, 0, 0, 0}, DA[5] = {0, 0, 0, 0, 0};
+    if (n_attr) {
+      const float *at = p->attrs;
+      const double qmax = std::ldexp(1.0, (int)attr_bits) - 1.0;
+      for (uint32_t c = 0; c < n_attr; c++) {
+        float g0 = at[c];
+        for (uint32_t v = 1; v < n_verts; v++) g0 = std::min(g0, at[(size_t)n_attr * v + c]);
+        GA[c] = g0;
+        double wmax = 0;
+        for (uint32_t i = 0; i < nm; i++) {
+          float lo = at[(size_t)n_attr * pk[i].gv[0] + c], hi = lo;
+          for (uint32_t g : pk[i].gv) {
+            const float x = at[(size_t)n_attr * g + c];
+            lo = std::min(lo, x);
+            hi = std::max(hi, x);
+          }
+          wmax = std::max(wmax, (double)hi - (double)lo);
+        }
+        float D = wmax > 0 ? round_up_float(wmax / qmax) : 1.0f;
+        for (;;) {
+          std::atomic<int> over{0};
+          parallel_for(
+              nm, threads,
+              [&](uint64_t i) {
+                Packed &x = pk[i];
+                double lo = 0, hi = 0;
+                for (uint32_t j = 0; j < x.V; j++) {
+                  const double y = ((double)at[(size_t)n_attr * x.gv[j] + c] - (double)GA[c]) / (double)D;
+                  const double g = std::floor(y + 0.5);
+                  if (j == 0 || g < lo) lo = g;
+                  if (j == 0 || g > hi) hi = g;
+                }
+                if (hi > 4294967295.0 || lo + qmax > 4294967295.0) over.store(2);
+                else if (hi - lo > qmax) over.store(std::max(over.load(), 1));
+                else x.La[c] = (uint32_t)lo;
+              },
+              1024);
+          if (over.load() == 2) {
+            delete blob;
+            return MC_ERR_LIMIT;
+          }
+          if (over.load() == 0) break;
+          D = std::nextafter(D, INFINITY);
+        }
+        DA[c] = D;
+      }
+    }
+
     // ---- layout in blob order
     std::vector<uint32_t> slot(nm);
     for (uint32_t s = 0; s < nm; s++) slot[s] = p->order ? p->order[s] : s;
@@ -286,6 +341,9 @@ extern "C" mc_status mc_encode(const mc_meshlets *m, const float *pos, uint32_t 
     blob->payload.assign(off[nm] * 4, 0);
     blob->vmap.resize(vb[nm]);
     blob->cones.resize(nm);
+    blob->n_attr = n_attr;
+    blob->attr_bits = attr_bits;
+    if (n_attr) blob->attr_desc.assign(nm, mc_attr_desc{});
     uint32_t *words = reinterpret_cast<uint32_t *>(blob->payload.data());
     parallel_for(
         nm, threads,
@@ -317,6 +375,18 @@ extern "C" mc_status mc_encode(const mc_meshlets *m, const float *pos, uint32_t 
               put_bits(pw, (3 * (uint64_t)v + c) * x.b, x.b, q);
               P[3 * v + c] = grid_to_float(x.L[c] + q, G[c], delta[x.b][c]);
             }
+          if (n_attr) {
+            uint32_t *aw = pw + (3 * x.V * x.b + 31) / 32;
+            for (uint32_t v = 0; v < x.V; v++)
+              for (uint32_t c = 0; c < n_attr; c++) {
+                const double y = ((double)p->attrs[(size_t)n_attr * x.gv[v] + c] - (double)GA[c]) /
+                                 (double)DA[c];
+                const uint32_t q = (uint32_t)(std::floor(y + 0.5) - (double)x.La[c]);
+                put_bits(aw, ((uint64_t)n_attr * v + c) * attr_bits, attr_bits, q);
+              }
+            mc_attr_desc &ad = blob->attr_desc[s];
+            for (uint32_t c = 0; c < n_attr; c++) ad.La[c] = x.La[c];
+          }
           {
             // the meshlet's input triangles in local ids (vertex -> local id
             // through a per-thread table over the mesh's vertices)
@@ -342,6 +412,16 @@ extern "C" mc_status mc_encode(const mc_meshlets *m, const float *pos, uint32_t 
         },
         256);
 
+    if (n_attr) {
+      mc_attr_grid ag{};
+      for (uint32_t c = 0; c < n_attr; c++) {
+        ag.G[c] = GA[c];
+        ag.delta[c] = DA[c];
+      }
+      ag.attr_bits = attr_bits;
+      ag.mesh_id = p->mesh_id;
+      blob->attr_grids.push_back(ag);
+    }
     blob->grids.resize(n_grids);
     for (uint32_t b = 1; b <= 32; b++) {
       if (!present[b]) continue;
@@ -406,7 +486,14 @@ extern "C" mc_status mc_blob_concat(const mc_blob *const *blobs, uint32_t n, mc_
     b->grids.reserve(ng);
     b->vmap.reserve(nv);
     b->cones.reserve(nm);
-    uint64_t o16 = 0, vb = 0, tb = 0, gb = 0, mb = 0;
+    b->n_attr = blobs[0]->n_attr;
+    b->attr_bits = blobs[0]->attr_bits;
+    for (uint32_t i = 0; i < n; i++)
+      if (blobs[i]->n_attr != b->n_attr || blobs[i]->attr_bits != b->attr_bits) {
+        delete b;
+        return MC_ERR_INVALID_ARG;  // attribute channels must agree
+      }
+    uint64_t o16 = 0, vb = 0, tb = 0, gb = 0, mb = 0, ab = 0;
     for (uint32_t i = 0; i < n; i++) {
       const mc_blob *s = blobs[i];
       for (mc_desc d : s->desc) {
@@ -429,6 +516,15 @@ extern "C" mc_status mc_blob_concat(const mc_blob *const *blobs, uint32_t n, mc_
       }
       b->vmap.insert(b->vmap.end(), s->vmap.begin(), s->vmap.end());
       b->cones.insert(b->cones.end(), s->cones.begin(), s->cones.end());
+      for (mc_attr_desc ad : s->attr_desc) {
+        ad.grid = (uint16_t)(ad.grid + ab);
+        b->attr_desc.push_back(ad);
+      }
+      for (mc_attr_grid ag : s->attr_grids) {
+        ag.mesh_id = i;
+        b->attr_grids.push_back(ag);
+      }
+      ab += s->attr_grids.size();
       o16 += s->payload.size() / 16;
       vb += s->total_verts;
       tb += s->total_tris;
@@ -474,6 +570,11 @@ extern "C" mc_status mc_blob_view(const mc_blob *b, mc_blob_view_t *v) {
   v->max_block_words = b->max_block_words;
   v->max_tris = b->max_tris;
   v->cones = b->cones.data();
+  v->n_attr = b->n_attr;
+  v->attr_bits = b->attr_bits;
+  v->attr_desc = b->attr_desc.empty() ? nullptr : b->attr_desc.data();
+  v->attr_grids = b->attr_grids.empty() ? nullptr : b->attr_grids.data();
+  v->n_attr_grids = (uint32_t)b->attr_grids.size();
   return MC_OK;
 }
 

@@ -60,6 +60,9 @@ struct mc_blob {
   std::vector<mc_mesh_info> meshes;
   std::vector<uint32_t> vmap;
   std::vector<mc_cone> cones;
+  uint32_t n_attr = 0, attr_bits = 0;
+  std::vector<mc_attr_desc> attr_desc;
+  std::vector<mc_attr_grid> attr_grids;
   uint64_t total_tris = 0, total_verts = 0, input_tris = 0;
   uint64_t restarts = 0, split_meshlets = 0, conn_bits = 0, pos_bits_total = 0;
   uint32_t max_block_words = 0, max_tris = 0;

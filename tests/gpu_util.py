@@ -8,7 +8,7 @@ import oracle as O
 from paper_2404_06359_gb300 import codec as mc
 
 
-def block_words_max(desc: np.ndarray) -> int:
+def block_words_max(desc: np.ndarray, n_attr: int = 0, attr_bits: int = 0) -> int:
     w = desc.view(np.uint32).reshape(-1, 8)
     V = (w[:, 3] & 0xFFFF).astype(np.int64)
     T = (w[:, 3] >> 16).astype(np.int64)
@@ -17,7 +17,7 @@ def block_words_max(desc: np.ndarray) -> int:
     R = T + 2 - V
     nw = (T + 31) // 32
     conn = np.where(rw == 0, nw + (T + 2) // 4, 2 * nw + (R * rw + 31) // 32)  # w = 0: plain GTS
-    words = conn + (3 * V * b + 31) // 32
+    words = conn + (3 * V * b + 31) // 32 + (n_attr * V * attr_bits + 31) // 32
     return int(((words + 3) // 4 * 4).max()) if words.size else 4
 
 
@@ -27,9 +27,13 @@ def max_tris(desc: np.ndarray) -> int:
 
 
 def device_batch_from_oracle(blob: O.Blob, cones: bool = False) -> mc.DeviceBatch:
+    at = blob.attrs
     return mc.DeviceBatch.from_arrays(blob.desc, blob.payload, blob.grids, blob.total_tris,
-                                      blob.total_verts, block_words_max(blob.desc),
-                                      max_tris(blob.desc), cones=blob.cones if cones else None)
+                                      blob.total_verts,
+                                      block_words_max(blob.desc, at["n_attr"] if at else 0,
+                                                      at["attr_bits"] if at else 0),
+                                      max_tris(blob.desc), cones=blob.cones if cones else None,
+                                      attrs=at)
 
 
 def run_decode(db: mc.DeviceBatch, mode="batch", tuning=None, local=True, global_=True):

@@ -71,6 +71,31 @@ def test_blob_bytes_identical(both):
     assert s["input_tris"] == mesh.n_tris
 
 
+@pytest.mark.parametrize("mode,bits,abits", [(0, 16, 16), (1, 12, 10), (2, 16, 20)])
+def test_attribute_channels_identical(mode, bits, abits):
+    """Blocks with attribute words, records and grids: library == oracle,
+    byte for byte, alone and concatenated."""
+    rng = np.random.Generator(np.random.PCG64(8 + mode))
+    meshes = [G.uv_sphere(6_000, rng), G.torus(5_000, rng), G.grid_mesh(12)]
+    blobs, oblobs = [], []
+    for i, mesh in enumerate(meshes):
+        at = G.vertex_attributes(mesh)
+        m = mc.mc_meshletize(mesh.tris, mesh.n_verts, [(64, 126)])
+        blobs.append(mc.mc_encode(m, mesh.pos, bits, mode, mesh_id=i, attrs=at, attr_bits=abits))
+        oblobs.append(O.encode_mesh(mesh, (64, 126), bits, mode, mesh_id=i, attrs=at, attr_bits=abits))
+        a = blobs[-1].arrays()
+        assert np.array_equal(a["payload"], oblobs[-1].payload)
+        assert np.array_equal(a["attr_desc"], oblobs[-1].attrs["adesc"])
+        assert np.array_equal(a["attr_grids"], oblobs[-1].attrs["agrids"])
+        assert blobs[-1].stats()["n_attr"] == 5 and blobs[-1].stats()["attr_bits"] == abits
+    a = mc.mc_blob_concat(blobs).arrays()
+    ocat = O.concat(oblobs)
+    assert np.array_equal(a["desc"], ocat.desc)
+    assert np.array_equal(a["payload"], ocat.payload)
+    assert np.array_equal(a["attr_desc"], ocat.attrs["adesc"])
+    assert np.array_equal(a["attr_grids"], ocat.attrs["agrids"])
+
+
 def test_concat_matches_oracle_concat():
     rng = np.random.Generator(np.random.PCG64(2))
     meshes = [G.uv_sphere(3000, rng), G.torus(2500, rng), G.grid_mesh(16)]
