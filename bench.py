@@ -174,13 +174,13 @@ def _barrier(ws):
         dist.barrier()
 
 
-def build_workload(cfg: int, rank: int, codec: str = "reuse"):
+def build_workload(cfg: int, rank: int, codec: str = "reuse", attrs: bool = False):
     from paper_2404_06359_gb300 import workloads as W
     if cfg == 1:
         blob, meshes = W.cfg1()
         return blob, meshes, None
     if cfg == 2:
-        blob, meshes = W.cfg2(rank, plain_gts=codec == "gts")
+        blob, meshes = W.cfg2(rank, plain_gts=codec == "gts", attrs=attrs)
         return blob, meshes, None
     if cfg == 3:
         blob, meshes = W.cfg3(rank, plain_gts=codec == "gts")
@@ -299,6 +299,9 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--pool-meshes", type=int, default=128)
+    ap.add_argument("--attrs", action="store_true",
+                    help="config 2 with 8-channel vertices (position, normal, texture coordinate; "
+                         "16-bit attributes) decoded by mc_decode_batch_vertices")
     ap.add_argument("--codec", choices=("reuse", "gts"), default="reuse",
                     help="connectivity encoding of configs 2/3: GTS-Reuse (default) or plain GTS "
                          "(one stored 8-bit entry per triangle)")
@@ -322,10 +325,13 @@ def main():
     t_build = time.time()
     if args.codec == "gts" and args.config not in (2, 3):
         raise SystemExit("--codec gts applies to configs 2 and 3")
-    blob, meshes, vps = build_workload(args.config, rank, args.codec)
+    if args.attrs and args.config != 2:
+        raise SystemExit("--attrs applies to config 2")
+    blob, meshes, vps = build_workload(args.config, rank, args.codec, args.attrs)
     t_build = time.time() - t_build
     stats = blob.stats()
-    db = mc.DeviceBatch(blob, "cuda", cones=args.config == 4)  # cfg4: normal-cone meshlet test on
+    db = mc.DeviceBatch(blob, "cuda", cones=args.config == 4,  # cfg4: normal-cone meshlet test on
+                        attrs=args.attrs)
     arrays = blob.arrays()
     input_tris = stats["input_tris"]
     stream = torch.cuda.Stream()
@@ -335,7 +341,10 @@ def main():
     want_local = True
     want_global = args.config != 1
     out = db.outputs(want_local, want_global)
-    nbytes = W.algorithmic_bytes(stats, arrays["desc"], want_local, want_global)
+    if args.attrs:  # full 8-float vertices instead of positions
+        out["vertex"] = torch.empty(8 * stats["total_verts"], dtype=torch.float32, device="cuda")
+    nbytes = W.algorithmic_bytes(stats, arrays["desc"], want_local, want_global,
+                                 vertices=args.attrs)
     extra = {}
     with torch.cuda.stream(stream):
         if cull:
@@ -361,8 +370,8 @@ def main():
             else:
                 tune, tune_ms = mc.mc_autotune(db, out["local"], out["global"], out["pos"],
                                                out["status"], scratch, stream)
-            graph = mc.mc_graph_capture_batch(db, out["local"], out["global"], out["pos"],
-                                              out["status"], scratch, tune, stream)
+            graph = None if args.attrs else mc.mc_graph_capture_batch(
+                db, out["local"], out["global"], out["pos"], out["status"], scratch, tune, stream)
             launches_per_step = 1
             extra["tuning"] = {"warps_per_cta": tune.warps_per_cta, "ctas_per_sm": tune.ctas_per_sm,
                                "meshlets_per_grab": tune.meshlets_per_grab}
@@ -370,6 +379,9 @@ def main():
         def step():
             if graph is not None:
                 graph.launch(stream)
+            elif args.attrs:
+                mc.mc_decode_batch_vertices(db, out["local"], out["global"], out["vertex"],
+                                            out["status"], scratch, tune, stream)
             else:
                 mc.mc_decode_plain(db, 0, stats["n_meshlets"], out["local"],
                                    out["global"] if want_global else None, out["pos"], out["status"],
@@ -401,7 +413,7 @@ def main():
 
         # plain one-launch-per-mesh decoder on the same batch (the baseline)
         plain = None
-        if not cull and args.config != 1 and args.plain_steps > 0:
+        if not cull and args.config != 1 and args.plain_steps > 0 and not args.attrs:
             pt = []
             for i in range(args.plain_steps + 2):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -420,7 +432,7 @@ def main():
 
         # end to end through the C ABI with host buffers (pinned), copies timed
         e2e = None
-        if not cull and args.e2e_steps > 0:
+        if not cull and args.e2e_steps > 0 and not args.attrs:
             T, V = stats["total_tris"], stats["total_verts"]
             d_desc = torch.empty(32 * stats["n_meshlets"], dtype=torch.uint8, device="cuda")
             d_pay = torch.empty(stats["payload_bytes"], dtype=torch.uint8, device="cuda")
@@ -484,7 +496,7 @@ def main():
         ach = bytes_per_launch / per_launch_s / 1e9
         tr = NCU_TRAFFIC.get(_kernel_hash())
         traffic = None
-        if tr and args.config in tr:
+        if tr and args.config in tr and args.codec == "reuse" and not args.attrs:
             traffic = int(tr[args.config] * stats["total_tris"])  # per launch (one view for cfg4)
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "traffic": traffic,
@@ -499,7 +511,9 @@ def main():
         "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.config] + (" [plain GTS connectivity]"
-                                                          if args.codec == "gts" else ""),
+                                                          if args.codec == "gts" else "")
+                   + (" [8-channel vertices: position, normal, texture coordinate; 32 B out]"
+                      if args.attrs else ""),
                    "connectivity_bits_per_triangle": round(stats["conn_bits"] / input_tris, 3),
                    "input_triangles": input_tris,
                    "decoded_triangle_slots": stats["total_tris"], "vertices": stats["total_verts"],

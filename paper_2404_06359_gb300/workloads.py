@@ -32,12 +32,16 @@ def _threads():
     return os.cpu_count() or 4
 
 
-def encode_meshes(meshes, limits=((64, 126),), pos_bits=16, reuse_mode=0):
-    """Encode each mesh (in parallel, one thread per mesh) and concatenate."""
+def encode_meshes(meshes, limits=((64, 126),), pos_bits=16, reuse_mode=0, attrs=False):
+    """Encode each mesh (in parallel, one thread per mesh) and concatenate.
+    attrs: also encode normals and texture coordinates (5 channels at 16
+    bits, the rest of an 8-channel attribute vector)."""
     def enc(i):
         m = meshes[i]
         ml = mc.mc_meshletize(m.tris, m.n_verts, limits, m.tri_class, n_threads=1)
-        return mc.mc_encode(ml, m.pos, pos_bits, reuse_mode, mesh_id=i, n_threads=1)
+        at = G.vertex_attributes(m) if attrs else None
+        return mc.mc_encode(ml, m.pos, pos_bits, reuse_mode, mesh_id=i, n_threads=1, attrs=at,
+                            attr_bits=16)
     with ThreadPoolExecutor(_threads()) as ex:
         blobs = list(ex.map(enc, range(len(meshes))))
     return mc.mc_blob_concat(blobs)
@@ -49,11 +53,12 @@ def cfg1():
     return mc.mc_encode(ml, mesh.pos, 16, 0), [mesh]
 
 
-def cfg2(rank: int = 0, plain_gts: bool = False):
+def cfg2(rank: int = 0, plain_gts: bool = False, attrs: bool = False):
     """plain_gts: store every strip entry at 8 bits (Sec. 4.2) instead of the
-    GTS-Reuse packing."""
+    GTS-Reuse packing; attrs: 8-channel vertices (position, normal, texture
+    coordinate)."""
     meshes = G.surface_batch(256, 10_000, 200_000, SEEDS[2] + 1000 * rank)
-    return encode_meshes(meshes, reuse_mode=2 if plain_gts else 0), meshes
+    return encode_meshes(meshes, reuse_mode=2 if plain_gts else 0, attrs=attrs), meshes
 
 
 def cfg3(rank: int = 0, total_tris: int = 50_000_000, plain_gts: bool = False):
@@ -86,18 +91,24 @@ def _block_words(T, V, w, b):
     return conn + (3 * V * b + 31) // 32
 
 
-def algorithmic_bytes(stats: dict, desc: np.ndarray, local=True, global_=True) -> dict:
+def algorithmic_bytes(stats: dict, desc: np.ndarray, local=True, global_=True,
+                      vertices: bool = False) -> dict:
     """Bytes one decode must move: compressed input read (descriptors, payload
-    without block padding, grids) and decoded output written."""
+    without block padding, grids; with attribute channels their words,
+    records and grids) and decoded output written (vertices: 32 B per vertex
+    instead of 12)."""
     w = desc.view(np.uint32).reshape(-1, 8)
     V = (w[:, 3] & 0xFFFF).astype(np.int64)
     T = (w[:, 3] >> 16).astype(np.int64)
     rw = (w[:, 4] & 0xFF).astype(np.int64)
     b = ((w[:, 4] >> 8) & 0xFF).astype(np.int64)
-    words = _block_words(T, V, rw, b)
+    n_attr, abits = int(stats.get("n_attr", 0)), int(stats.get("attr_bits", 0))
+    words = _block_words(T, V, rw, b) + (n_attr * V * abits + 31) // 32
     read = 32 * w.shape[0] + 4 * int(words.sum()) + 32 * stats["n_grids"]
+    if vertices:
+        read += 32 * w.shape[0] + 48 * int(stats.get("n_meshes", 1))
     Tt, Vt = int(T.sum()), int(V.sum())
-    write = (3 * Tt if local else 0) + (12 * Tt if global_ else 0) + 12 * Vt
+    write = (3 * Tt if local else 0) + (12 * Tt if global_ else 0) + (32 if vertices else 12) * Vt
     return {"read": read, "write": write, "total": read + write,
             "padding": 4 * int(((words + 3) // 4 * 4 - words).sum())}
 
