@@ -56,7 +56,7 @@ def _peaks():
 # capture (profiles/decode_batch_cfg2.md for cfg2, profiles/decode_cull_cfg4.md
 # for cfg4), per decoded triangle slot and keyed by the kernel-source hash it
 # was taken on; reported only while the sources match.
-NCU_TRAFFIC = {"467fbca66fd41906": {2: 429.659840e6 / 18015946, 4: 896.483840e6 / 55596770}}
+NCU_TRAFFIC = {"4c328bdd02633302": {2: 429.168128e6 / 18015946, 4: 879.191040e6 / 55596770}}
 
 
 def _kernel_hash():
