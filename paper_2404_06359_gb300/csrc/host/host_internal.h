@@ -29,8 +29,9 @@ struct StripOut {
 // Per-thread scratch of the strip builder.
 struct StripScratch {
   std::vector<uint64_t> keys;
-  std::vector<int32_t> nb;
+  std::vector<int32_t> nb, adj, pos;
   std::vector<uint8_t> visited;
+  std::vector<uint32_t> path, order, lens, best_order, best_lens;
 };
 
 // Greedy strip over the triangles tri[ids[i]], i = list position.
