@@ -402,6 +402,23 @@ mc_status mc_decode_cull(const mc_device_batch *b, const float *d_view_proj,
                          uint32_t *d_status, void *d_scratch, const mc_tuning *t,
                          void *stream);
 
+/* The fused cull with the survivors in a fixed order: meshlet order, then
+ * triangle order within a meshlet -- the order of a sequential decode and
+ * cull.  Same arguments and results as mc_decode_cull otherwise, plus
+ *   d_order  device buffer of mc_cull_order_bytes(b) bytes, 8-byte aligned,
+ *            library-owned for the duration of the call (cleared by it)
+ * The order comes from a decoupled look-back over the work-queue grabs
+ * (each warp publishes its grab's survivor count and sums its predecessors'
+ * back to the nearest published prefix); grabs hold at most 6 meshlets in
+ * this mode.  Every wait is bounded: a wait that gives up sets
+ * MC_ERR_TIMEOUT in the status word.  Calls that overlap on the GPU must not
+ * share d_order or d_scratch. */
+size_t mc_cull_order_bytes(const mc_device_batch *b);
+mc_status mc_decode_cull_ordered(const mc_device_batch *b, const float *d_view_proj,
+                                 uint32_t *d_tri_out, uint32_t *d_tri_count, float *d_pos,
+                                 uint32_t *d_status, void *d_scratch, void *d_order,
+                                 const mc_tuning *t, void *stream);
+
 /* ------------------------------------------------------------------ runtime */
 
 /* Time candidate launch shapes of mc_decode_batch on this batch (the outputs

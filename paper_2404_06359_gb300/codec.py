@@ -92,6 +92,9 @@ _SIGS = [
                                           C.POINTER(mc_tuning), P]),
     ("mc_decode_cull", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P, P,
                                  C.POINTER(mc_tuning), P]),
+    ("mc_cull_order_bytes", C.c_size_t, [C.POINTER(mc_device_batch)]),
+    ("mc_decode_cull_ordered", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P, P, P,
+                                         C.POINTER(mc_tuning), P]),
     ("mc_decode_requests", C.c_int, [C.POINTER(mc_device_batch), P, u32, u32, P, P,
                                      C.POINTER(mc_tuning), P]),
     ("mc_autotune", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P, P,
@@ -384,6 +387,22 @@ def mc_decode_batch(db: DeviceBatch, d_local, d_global, d_pos, d_status, d_scrat
     _check(lib().mc_decode_batch(C.byref(db.c), _tptr(d_local), _tptr(d_global), _tptr(d_pos),
                                  _tptr(d_status), _tptr(d_scratch), _tuning(tuning), _stream(stream)),
            "mc_decode_batch")
+
+
+def mc_decode_cull_ordered(db: DeviceBatch, d_view_proj, d_tri_out, d_tri_count, d_pos, d_status,
+                           d_scratch, d_order=None, tuning=None, stream=None):
+    """Fused cull with the survivors in meshlet order, then triangle order.
+    d_order: uint8 device buffer of mc_cull_order_bytes bytes (allocated here
+    when None)."""
+    if d_order is None:
+        import torch
+        d_order = torch.empty(int(lib().mc_cull_order_bytes(C.byref(db.c))), dtype=torch.uint8,
+                              device="cuda")
+    _check(lib().mc_decode_cull_ordered(C.byref(db.c), _tptr(d_view_proj), _tptr(d_tri_out),
+                                        _tptr(d_tri_count), _tptr(d_pos), _tptr(d_status),
+                                        _tptr(d_scratch), _tptr(d_order), _tuning(tuning),
+                                        _stream(stream)),
+           "mc_decode_cull_ordered")
 
 
 def mc_decode_batch_vertices(db: DeviceBatch, d_local, d_global, d_vertex, d_status, d_scratch,

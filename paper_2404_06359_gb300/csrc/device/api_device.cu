@@ -246,12 +246,16 @@ extern "C" mc_status mc_decode_batch_vertices(const mc_device_batch *b, uint8_t 
 }
 
 namespace {
+constexpr uint32_t kOrderedGrabMax = 6;  // a whole grab's survivors fit a warp's buffer
+
 mc_status launch_cull_checked(const mc_device_batch *b, const float *d_vp, uint32_t *d_tri_out,
                               uint32_t *d_tri_count, float *d_pos, uint32_t *d_status,
-                              void *d_scratch, const mc_tuning *t, cudaStream_t s) {
+                              void *d_scratch, const mc_tuning *t, cudaStream_t s,
+                              uint64_t *d_order = nullptr) {
   const uint32_t warps = (t && t->warps_per_cta) ? t->warps_per_cta : 4;
-  const uint32_t per_grab = (t && t->meshlets_per_grab) ? t->meshlets_per_grab : 4;
+  uint32_t per_grab = (t && t->meshlets_per_grab) ? t->meshlets_per_grab : 4;
   if (warps < 1 || warps > 32 || per_grab < 1 || per_grab > 16) return MC_ERR_INVALID_ARG;
+  if (d_order) per_grab = std::min<uint32_t>(per_grab, kOrderedGrabMax);
   const BatchArgs a = args_of(b);
   // a grab's survivors are buffered in shared memory: shrink the grab until
   // the requested number of warps fits on an SM
@@ -262,8 +266,12 @@ mc_status launch_cull_checked(const mc_device_batch *b, const float *d_vp, uint3
   uint32_t per_sm = (t && t->ctas_per_sm) ? std::min<uint32_t>(t->ctas_per_sm, occ) : (uint32_t)occ;
   uint32_t ctas = per_sm * (uint32_t)sm_count();
   if (ctas == 0) return MC_ERR_CUDA;
-  cudaError_t e = launch_cull(a, d_vp, b->cones, ctas, warps, grab, t && t->checked, d_tri_out,
-                              d_tri_count, d_pos, d_status, static_cast<uint32_t *>(d_scratch), s);
+  cudaError_t e = cudaSuccess;
+  if (d_order)  // the look-back state starts at "not published" for every grab
+    e = cudaMemsetAsync(d_order, 0, 8ull * ((b->n_meshlets + grab - 1) / grab), s);
+  if (e == cudaSuccess)
+    e = launch_cull(a, d_vp, b->cones, ctas, warps, grab, t && t->checked, d_tri_out, d_tri_count,
+                    d_pos, d_status, static_cast<uint32_t *>(d_scratch), d_order, s);
   if (e == cudaSuccess) g_launches++;
   return from_cuda(e);
 }
@@ -282,6 +290,26 @@ extern "C" mc_status mc_decode_cull(const mc_device_batch *b, const float *d_vie
     return MC_ERR_INVALID_ARG;
   return launch_cull_checked(b, d_view_proj, d_tri_out, d_tri_count, d_pos, d_status, d_scratch, t,
                              static_cast<cudaStream_t>(stream));
+}
+
+extern "C" size_t mc_cull_order_bytes(const mc_device_batch *b) {
+  return b ? 8ull * b->n_meshlets + 16 : 0;
+}
+
+extern "C" mc_status mc_decode_cull_ordered(const mc_device_batch *b, const float *d_view_proj,
+                                            uint32_t *d_tri_out, uint32_t *d_tri_count,
+                                            float *d_pos, uint32_t *d_status, void *d_scratch,
+                                            void *d_order, const mc_tuning *t, void *stream) {
+  if (!b || !d_tri_count) return MC_ERR_INVALID_ARG;
+  if (b->n_meshlets == 0)
+    return from_cuda(cudaMemsetAsync(d_tri_count, 0, 4, static_cast<cudaStream_t>(stream)));
+  mc_status st = check_batch(b);
+  if (st != MC_OK) return st;
+  if (!d_view_proj || !d_tri_out || !d_pos || !d_scratch || !aligned(d_scratch, 16) || !d_order ||
+      !aligned(d_order, 8))
+    return MC_ERR_INVALID_ARG;
+  return launch_cull_checked(b, d_view_proj, d_tri_out, d_tri_count, d_pos, d_status, d_scratch, t,
+                             static_cast<cudaStream_t>(stream), static_cast<uint64_t *>(d_order));
 }
 
 extern "C" mc_status mc_decode_requests(const mc_device_batch *pool, const mc_request *d_reqs,

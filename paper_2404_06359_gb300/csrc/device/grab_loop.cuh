@@ -78,15 +78,19 @@ __host__ __device__ inline uint32_t grab_loop_bytes(uint32_t max_block_words, ui
 // index m0 + j) of the
 // grab whose header passes header_ok, with sw its payload block in shared
 // memory; a failed header sets MC_ERR_CORRUPT.
+// After the grab's meshlets, post(m0, cnt) is called by all lanes.
 struct NoPre {
   __device__ __forceinline__ uint32_t operator()(uint32_t, const uint32_t *, uint32_t) const {
     return 0;
   }
 };
-template <class Pre, class Body>
+struct NoPost {
+  __device__ __forceinline__ void operator()(uint32_t, uint32_t) const {}
+};
+template <class Pre, class Body, class Post = NoPost>
 __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab, uint8_t *wbase,
                                           uint32_t lane, uint32_t *queue, uint32_t *status,
-                                          Pre &&pre, Body &&body) {
+                                          Pre &&pre, Body &&body, Post &&post = Post{}) {
   const uint32_t *sdesc = reinterpret_cast<const uint32_t *>(wbase);
   const uint32_t bar = smem_addr(wbase + 32 * (per_grab + 1));
   uint32_t *spay = reinterpret_cast<uint32_t *>(wbase + 32 * (per_grab + 1) + 16);
@@ -154,6 +158,7 @@ __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab,
       body(d, sw, j, word, m0 + j);
     }
     __syncwarp();
+    post(m0, cnt);
   }
 }
 

@@ -408,17 +408,77 @@ __device__ __forceinline__ void cull_flush(const uint32_t *surv, const uint32_t 
   __syncwarp();
 }
 
+// Ordered compaction: decoupled look-back over the grabs (each grab is a
+// contiguous run of meshlets taken from the queue in order).  Grab g
+// publishes its survivor count as an aggregate, the warp sums the values its
+// predecessors have published back to the nearest inclusive prefix (32 at a
+// time, one per lane), then publishes its own inclusive prefix.  Grabs are
+// handed out in order to running warps and no grab waits on a later one, so
+// the chain resolves; every wait is bounded (about a second).  State word:
+// bits 62-63 = 0 not yet, 1 aggregate, 2 inclusive prefix; bits 0-31 = value.
+// Returns the exclusive prefix, or 0xFFFFFFFF when a wait gave up.
+__device__ __forceinline__ void st_release_u64(uint64_t *p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t grab_lookback(uint64_t *state, uint32_t g, uint32_t count,
+                                                  uint32_t lane) {
+  constexpr uint64_t kAgg = 1ull << 62, kInc = 2ull << 62;
+  if (lane == 0) st_release_u64(state + g, (g == 0 ? kInc : kAgg) | count);
+  if (g == 0) return 0;
+  uint32_t excl = 0;
+  int64_t j = (int64_t)g - 1;
+  const long long t0 = clock64();
+  for (;;) {
+    const int64_t idx = j - (int64_t)lane;
+    const uint64_t v = idx >= 0 ? ld_acquire_u64(state + idx) : kInc;  // before grab 0: prefix 0
+    const uint32_t flag = (uint32_t)(v >> 62);
+    const uint32_t inc_mask = __ballot_sync(kFull, flag == 2u);
+    const uint32_t wait_mask = __ballot_sync(kFull, flag == 0u);
+    const uint32_t stop = inc_mask ? (uint32_t)__ffs(inc_mask) - 1u : 31u;  // lanes 0..stop count
+    const uint32_t upto = stop == 31u ? kFull : ((2u << stop) - 1u);
+    if (wait_mask & upto) {
+      if (__any_sync(kFull, clock64() - t0 > kWaitCycles)) return 0xFFFFFFFFu;
+      continue;
+    }
+    excl += __reduce_add_sync(kFull, lane <= stop ? (uint32_t)v : 0u);
+    if (inc_mask) break;
+    j -= 32;
+  }
+  if (lane == 0) st_release_u64(state + g, kInc | (uint64_t)(excl + count));
+  return excl;
+}
+
+// Writes a grab's buffered survivors at a known output position (ordered
+// compaction); same layout as cull_flush.
+__device__ __forceinline__ void cull_write_at(const uint32_t *surv, const uint32_t *svb, uint32_t n,
+                                              uint32_t lane, uint32_t *tri_out, uint32_t dst) {
+  uint32_t *o = tri_out + 3ull * dst;
+  for (uint32_t e = lane; e < 3 * n; e += 32) {
+    const uint32_t t = e / 3, c = e - 3 * t;
+    const uint32_t p = surv[t];
+    o[e] = svb[p >> 24] + ((p >> (8 * c)) & 0xFFu);
+  }
+  __syncwarp();
+}
+
 // Fused decode + cull + compaction.  Persistent warps run the grab loop,
 // drop meshlets whose box is outside the frustum before touching their
 // triangles, decode and cull the rest and collect survivors in shared memory
 // across grabs; a full buffer (or the end of the work) is written out with
-// one atomicAdd.
-template <bool CHECKED, int MAX_THREADS>
+// one atomicAdd.  ORDERED: survivors are written in meshlet order -- each
+// grab's survivors (per_grab <= kSurvMeshlets meshlets) at the position the
+// look-back over order_state gives it; the last grab writes the count.
+template <bool CHECKED, int MAX_THREADS, bool ORDERED>
 __global__ void __launch_bounds__(MAX_THREADS) decode_cull_kernel(BatchArgs a, const float *view_proj,
                                                           const mc_cone *cones, uint32_t per_grab,
                                                           uint32_t *tri_out, uint32_t *tri_count,
                                                           float *out_pos, uint32_t *status,
-                                                          uint32_t *scratch) {
+                                                          uint32_t *scratch, uint64_t *order_state) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ float s_M[16];
   __shared__ float s_eye[4];  // camera position, [3] = 1 when there is one
@@ -444,7 +504,8 @@ __global__ void __launch_bounds__(MAX_THREADS) decode_cull_kernel(BatchArgs a, c
                   if ((outside >> j) & 1u) return;
                   const Grid g = load_grid(a.grids + d.grid);
                   // d.T <= max_tris (header_ok), so the meshlet fits an emptied buffer
-                  if (n_keep + d.T > L.cap || n_src == kSurvSources) {
+                  // (ordered: a whole grab always fits)
+                  if (!ORDERED && (n_keep + d.T > L.cap || n_src == kSurvSources)) {
                     cull_flush(surv, svb, n_keep, lane, tri_out, scratch + kCount);
                     n_keep = 0;
                     n_src = 0;
@@ -459,15 +520,28 @@ __global__ void __launch_bounds__(MAX_THREADS) decode_cull_kernel(BatchArgs a, c
                     n_src++;
                   }
                   __syncwarp();
+                },
+                [&](uint32_t m0, uint32_t) {
+                  if (!ORDERED) return;
+                  const uint32_t g = m0 / per_grab;
+                  const uint32_t excl = grab_lookback(order_state, g, n_keep, lane);
+                  if (excl == 0xFFFFFFFFu) {
+                    if (lane == 0) set_status(status, MC_ERR_TIMEOUT);
+                  } else {
+                    cull_write_at(surv, svb, n_keep, lane, tri_out, excl);
+                    if (lane == 0 && m0 + per_grab >= a.n_meshlets) *tri_count = excl + n_keep;
+                  }
+                  n_keep = 0;
+                  n_src = 0;
                 });
-  if (n_keep) cull_flush(surv, svb, n_keep, lane, tri_out, scratch + kCount);
+  if (!ORDERED && n_keep) cull_flush(surv, svb, n_keep, lane, tri_out, scratch + kCount);
   // the last CTA publishes the count and resets the scratch
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     if (atomicAdd(scratch + kDone, 1u) == gridDim.x - 1) {
       __threadfence();
-      *tri_count = atomicAdd(scratch + kCount, 0u);
+      if (!ORDERED) *tri_count = atomicAdd(scratch + kCount, 0u);
       atomicExch(scratch + kCount, 0u);
       atomicExch(scratch + kQueue, 0u);
       atomicExch(scratch + kDone, 0u);
@@ -587,34 +661,48 @@ cudaError_t launch_batch(const BatchArgs &a, uint32_t ctas, uint32_t warps, uint
 namespace {
 // Small CTAs (up to 4 warps) get a build whose register budget needs no
 // spills; larger CTAs the 512-thread build.
-template <int MAX_THREADS>
+template <bool CHECKED, int MAX_THREADS, bool ORDERED>
 cudaError_t launch_cull_t(const BatchArgs &a, const float *view_proj, const mc_cone *cones,
+                          uint32_t ctas, uint32_t warps, uint32_t per_grab, uint32_t *tri_out,
+                          uint32_t *tri_count, float *out_pos, uint32_t *status, uint32_t *scratch,
+                          uint64_t *order_state, cudaStream_t s) {
+  const uint32_t smem = cull_smem_per_warp(a.max_block_words, a.max_tris, per_grab) * warps;
+  prepare(fn(decode_cull_kernel<CHECKED, MAX_THREADS, ORDERED>));
+  decode_cull_kernel<CHECKED, MAX_THREADS, ORDERED><<<ctas, warps * 32, smem, s>>>(
+      a, view_proj, cones, per_grab, tri_out, tri_count, out_pos, status, scratch, order_state);
+  return cudaGetLastError();
+}
+template <int MAX_THREADS, bool ORDERED>
+cudaError_t launch_cull_c(const BatchArgs &a, const float *view_proj, const mc_cone *cones,
                           uint32_t ctas, uint32_t warps, uint32_t per_grab, bool checked,
                           uint32_t *tri_out, uint32_t *tri_count, float *out_pos, uint32_t *status,
-                          uint32_t *scratch, cudaStream_t s) {
-  const uint32_t smem = cull_smem_per_warp(a.max_block_words, a.max_tris, per_grab) * warps;
-  if (checked) {
-    prepare(fn(decode_cull_kernel<true, MAX_THREADS>));
-    decode_cull_kernel<true, MAX_THREADS><<<ctas, warps * 32, smem, s>>>(
-        a, view_proj, cones, per_grab, tri_out, tri_count, out_pos, status, scratch);
-  } else {
-    prepare(fn(decode_cull_kernel<false, MAX_THREADS>));
-    decode_cull_kernel<false, MAX_THREADS><<<ctas, warps * 32, smem, s>>>(
-        a, view_proj, cones, per_grab, tri_out, tri_count, out_pos, status, scratch);
-  }
-  return cudaGetLastError();
+                          uint32_t *scratch, uint64_t *order_state, cudaStream_t s) {
+  if (checked)
+    return launch_cull_t<true, MAX_THREADS, ORDERED>(a, view_proj, cones, ctas, warps, per_grab,
+                                                     tri_out, tri_count, out_pos, status, scratch,
+                                                     order_state, s);
+  return launch_cull_t<false, MAX_THREADS, ORDERED>(a, view_proj, cones, ctas, warps, per_grab,
+                                                    tri_out, tri_count, out_pos, status, scratch,
+                                                    order_state, s);
 }
 }  // namespace
 
 cudaError_t launch_cull(const BatchArgs &a, const float *view_proj, const mc_cone *cones,
                         uint32_t ctas, uint32_t warps, uint32_t per_grab, bool checked,
                         uint32_t *tri_out, uint32_t *tri_count, float *out_pos, uint32_t *status,
-                        uint32_t *scratch, cudaStream_t s) {
+                        uint32_t *scratch, uint64_t *order_state, cudaStream_t s) {
+  if (order_state) {
+    if (warps <= 4)
+      return launch_cull_c<128, true>(a, view_proj, cones, ctas, warps, per_grab, checked, tri_out,
+                                      tri_count, out_pos, status, scratch, order_state, s);
+    return launch_cull_c<512, true>(a, view_proj, cones, ctas, warps, per_grab, checked, tri_out,
+                                    tri_count, out_pos, status, scratch, order_state, s);
+  }
   if (warps <= 4)
-    return launch_cull_t<128>(a, view_proj, cones, ctas, warps, per_grab, checked, tri_out,
-                              tri_count, out_pos, status, scratch, s);
-  return launch_cull_t<512>(a, view_proj, cones, ctas, warps, per_grab, checked, tri_out, tri_count,
-                            out_pos, status, scratch, s);
+    return launch_cull_c<128, false>(a, view_proj, cones, ctas, warps, per_grab, checked, tri_out,
+                                     tri_count, out_pos, status, scratch, nullptr, s);
+  return launch_cull_c<512, false>(a, view_proj, cones, ctas, warps, per_grab, checked, tri_out,
+                                   tri_count, out_pos, status, scratch, nullptr, s);
 }
 
 cudaError_t launch_requests(const BatchArgs &a, const mc_request *reqs, uint32_t n_reqs,
@@ -658,11 +746,15 @@ int max_ctas_per_sm_cull(uint32_t warps, uint32_t max_block_words, uint32_t max_
   const int smem = (int)(cull_smem_per_warp(max_block_words, max_tris, per_grab) * warps);
   if (warps > 16) return 0;
   if (warps <= 4) {
-    prepare(fn(decode_cull_kernel<true, 128>));
-    return occupancy(fn(decode_cull_kernel<false, 128>), warps * 32, smem);
+    prepare(fn(decode_cull_kernel<true, 128, false>));
+    prepare(fn(decode_cull_kernel<true, 128, true>));
+    prepare(fn(decode_cull_kernel<false, 128, true>));
+    return occupancy(fn(decode_cull_kernel<false, 128, false>), warps * 32, smem);
   }
-  prepare(fn(decode_cull_kernel<true, 512>));
-  return occupancy(fn(decode_cull_kernel<false, 512>), warps * 32, smem);
+  prepare(fn(decode_cull_kernel<true, 512, false>));
+  prepare(fn(decode_cull_kernel<true, 512, true>));
+  prepare(fn(decode_cull_kernel<false, 512, true>));
+  return occupancy(fn(decode_cull_kernel<false, 512, false>), warps * 32, smem);
 }
 
 }  // namespace mcdev

@@ -23,10 +23,12 @@ cudaError_t launch_batch(const BatchArgs &a, uint32_t ctas, uint32_t warps, uint
                          uint8_t *out_local, uint32_t *out_global, float *out_pos,
                          uint32_t *status, uint32_t *scratch, cudaStream_t s);
 
+// order_state (may be NULL): look-back state of the ordered compaction, one
+// zeroed 8-byte word per grab
 cudaError_t launch_cull(const BatchArgs &a, const float *view_proj, const mc_cone *cones,
                         uint32_t ctas, uint32_t warps, uint32_t per_grab, bool checked,
                         uint32_t *tri_out, uint32_t *tri_count, float *out_pos, uint32_t *status,
-                        uint32_t *scratch, cudaStream_t s);
+                        uint32_t *scratch, uint64_t *order_state, cudaStream_t s);
 
 int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words, uint32_t per_grab,
                           bool vertices = false);

@@ -210,3 +210,39 @@ def test_cull_plain_gts_vs_oracle(smooth_scene):
             assert np.array_equal(_sorted_rows(tri), _sorted_rows(ref_tri))
             vm = np.repeat(passed, f["V"].astype(np.int64)).astype(bool)
             assert np.array_equal(pos.reshape(-1, 3)[vm].view(np.uint32), ref_pos[vm].view(np.uint32))
+
+
+def _run_ordered(db, vp, tuning=None, cones=None):
+    import torch
+    T, V = db.stats["total_tris"], db.stats["total_verts"]
+    tri = torch.full((3 * T + 3,), -1, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    pos = torch.zeros(3 * V, dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    scratch = mc.new_scratch()
+    d_vp = torch.from_numpy(np.ascontiguousarray(vp, np.float32)).cuda()
+    mc.mc_decode_cull_ordered(db, d_vp, tri, cnt, pos, st, scratch, None, tuning)
+    torch.cuda.synchronize()
+    assert int(scratch.abs().sum()) == 0
+    n = int(cnt.item())
+    return tri[: 3 * n].cpu().numpy().view(np.uint32).reshape(-1, 3), pos.cpu().numpy(), int(st.item())
+
+
+@pytest.mark.parametrize("tuning", [None, {"warps_per_cta": 8, "meshlets_per_grab": 16},
+                                    {"warps_per_cta": 4, "meshlets_per_grab": 1, "checked": 1},
+                                    {"warps_per_cta": 16, "meshlets_per_grab": 5}])
+@pytest.mark.parametrize("which", ["scene", "smooth_scene"])
+def test_cull_ordered_is_the_sequential_order(request, which, tuning):
+    """The ordered mode returns exactly the oracle's survivor array (meshlet
+    order, then triangle order), with and without cones."""
+    blob, vps = request.getfixturevalue(which)
+    f = blob.fields()
+    for use_cones in (False, True):
+        db = device_batch_from_oracle(blob, cones=use_cones)
+        for vp in vps[:3]:
+            ref, ref_pos, passed = O.decode_cull(blob, vp, cones=blob.cones if use_cones else None)
+            tri, pos, st = _run_ordered(db, vp, tuning)
+            assert st == 0
+            assert np.array_equal(tri, ref)
+            vm = np.repeat(passed, f["V"].astype(np.int64)).astype(bool)
+            assert np.array_equal(pos.reshape(-1, 3)[vm].view(np.uint32), ref_pos[vm].view(np.uint32))

@@ -178,3 +178,27 @@ def test_cfg4_fullsize_cull(cfg4_data, cones):
     assert np.array_equal(pos.cpu().numpy().reshape(-1, 3)[vm].view(np.uint32), ref_pos[vm].view(np.uint32))
     print(f"cfg4 (cones={cones}): {s['input_tris']} triangles, kept fraction per view "
           f"{frac.min():.3f}..{frac.max():.3f}, meshlets decoded in the last view {passed.mean():.3f}")
+
+
+def test_cfg4_fullsize_cull_ordered(cfg4_data):
+    """Ordered compaction at full size: the survivors of one view equal the
+    oracle's array element for element."""
+    import torch
+    blob, meshes, vps = cfg4_data
+    s = blob.stats()
+    db = mc.DeviceBatch(blob, cones=True)
+    T, V = s["total_tris"], s["total_verts"]
+    tri = torch.empty(3 * T + 3, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    pos = torch.zeros(3 * V, dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    scratch = mc.new_scratch()
+    d_vp = torch.from_numpy(np.ascontiguousarray(vps[7], np.float32)).cuda()
+    mc.mc_decode_cull_ordered(db, d_vp, tri, cnt, pos, st, scratch)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and int(scratch.abs().sum()) == 0
+    a = blob.arrays()
+    ob = O.Blob(a["desc"], a["payload"], a["grids"])
+    ref, _, _ = O.decode_cull(ob, vps[7], cones=a["cones"])
+    got = tri[: 3 * int(cnt.item())].cpu().numpy().view(np.uint32).reshape(-1, 3)
+    assert np.array_equal(got, ref)
