@@ -302,6 +302,8 @@ def main():
     ap.add_argument("--attrs", action="store_true",
                     help="config 2 with 8-channel vertices (position, normal, texture coordinate; "
                          "16-bit attributes) decoded by mc_decode_batch_vertices")
+    ap.add_argument("--cull-views", type=int, default=8, choices=range(1, 9), metavar="1..8",
+                    help="config 4: views per fused-cull launch (1 = one launch per view)")
     ap.add_argument("--codec", choices=("reuse", "gts"), default="reuse",
                     help="connectivity encoding of configs 2/3: GTS-Reuse (default) or plain GTS "
                          "(one stored 8-bit entry per triangle)")
@@ -356,9 +358,19 @@ def main():
             if args.tuning:
                 w_, c_, g_ = (int(x) for x in args.tuning.split(","))
                 tune = mc.mc_tuning(w_, c_, g_, 0)
-            graph = mc.mc_graph_capture_cull(db, d_vps, len(vps), tri, counts, out["pos"],
-                                             out["status"], scratch, tune, stream)
-            launches_per_step = len(vps)
+            cv = args.cull_views
+            stride = 3 * T + 3
+            tri = torch.empty(cv * stride, dtype=torch.int32, device="cuda")
+
+            def capture_cull(batch):
+                if cv == 1:
+                    return mc.mc_graph_capture_cull(batch, d_vps, len(vps), tri, counts, out["pos"],
+                                                    out["status"], scratch, tune, stream)
+                return mc.mc_graph_capture_cull_views(batch, d_vps, len(vps), tri, stride, counts,
+                                                      out["pos"], out["status"], scratch, tune,
+                                                      stream)
+            graph = capture_cull(db)
+            launches_per_step = (len(vps) + cv - 1) // cv
         elif args.config == 1:
             graph = None
             launches_per_step = 1
@@ -467,12 +479,37 @@ def main():
     bytes_per_launch = nbytes["total"] if not cull else None
     if cull:
         counts_np = counts.cpu().numpy().astype(np.int64)
-        bytes_per_launch = W.cull_bytes(stats, arrays, vps, counts_np, cones=True)
+        bytes_per_launch = W.cull_bytes(stats, arrays, vps, counts_np, cones=True,
+                                        views_per_launch=cv)
+        if cv > 1:
+            # the same step with one single-view launch per view
+            g_1 = mc.mc_graph_capture_cull(db, d_vps, len(vps), tri, counts, out["pos"],
+                                           out["status"], scratch, tune, stream)
+            with torch.cuda.stream(stream):
+                t1 = []
+                for i in range(3 + max(3, args.steps // 10)):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    g_1.launch(stream)
+                    e1.record(stream)
+                    flush.zero_()
+                    if i >= 3:
+                        t1.append((e0, e1))
+                torch.cuda.synchronize()
+            ms1 = float(np.mean([a_.elapsed_time(b_) for a_, b_ in t1]))
+            assert int(out["status"].item()) == 0
+            assert np.array_equal(counts.cpu().numpy().astype(np.int64), counts_np)
+            b1 = W.cull_bytes(stats, arrays, vps, counts_np, cones=True)
+            a1 = b1 / (ms1 * 1e-3 / len(vps)) / 1e9
+            extra["cull_one_view_per_launch"] = {
+                "value": round(input_tris * len(vps) / (ms1 * 1e-3) / 1e9, 3), "unit": "Gtps",
+                "ms_per_step": round(ms1, 5), "launches_per_step": len(vps),
+                "algorithmic_bytes_per_launch": b1, "achieved_GBps": round(a1, 1),
+                "frac": round(a1 / _peaks()[0], 4)}
         # the same step without the normal-cone test (frustum + per-triangle only)
         db_nc = mc.DeviceBatch(blob, "cuda")
         with torch.cuda.stream(stream):
-            g_nc = mc.mc_graph_capture_cull(db_nc, d_vps, len(vps), tri, counts, out["pos"],
-                                            out["status"], scratch, tune, stream)
+            g_nc = capture_cull(db_nc)
             nc_t = []
             for i in range(3 + max(3, args.steps // 10)):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -486,11 +523,35 @@ def main():
         nc_ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in nc_t]))
         assert int(out["status"].item()) == 0
         counts_nc = counts.cpu().numpy().astype(np.int64)
+        # the same step with survivors in meshlet order (decoupled look-back)
+        d_order = torch.empty(int(mc.lib().mc_cull_order_bytes(mc.C.byref(db.c))), dtype=torch.uint8,
+                              device="cuda")
+        with torch.cuda.stream(stream):
+            or_t = []
+            for i in range(3 + max(3, args.steps // 10)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for v in range(len(vps)):
+                    mc.mc_decode_cull_ordered(db, d_vps[v], tri, counts[v:v + 1], out["pos"],
+                                              out["status"], scratch, d_order, tune, stream)
+                e1.record(stream)
+                flush.zero_()
+                if i >= 3:
+                    or_t.append((e0, e1))
+            torch.cuda.synchronize()
+        or_ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in or_t]))
+        assert int(out["status"].item()) == 0
+        assert np.array_equal(counts.cpu().numpy().astype(np.int64), counts_np)
+        extra["cull_ordered"] = {
+            "value": round(input_tris * len(vps) / (or_ms * 1e-3) / 1e9, 3), "unit": "Gtps",
+            "ms_per_step": round(or_ms, 5), "launches_per_step": len(vps),
+            "note": "survivors in meshlet order; launched one view at a time (no graph)"}
         extra["cull_without_cones"] = {
             "value": round(input_tris * len(vps) / (nc_ms * 1e-3) / 1e9, 3), "unit": "Gtps",
             "ms_per_step": round(nc_ms, 5),
             "kept_fraction_mean": float(counts_nc.mean() / input_tris),
-            "algorithmic_bytes_per_launch": W.cull_bytes(stats, arrays, vps, counts_nc)}
+            "algorithmic_bytes_per_launch": W.cull_bytes(stats, arrays, vps, counts_nc,
+                                                         views_per_launch=cv)}
     roof = None
     if bytes_per_launch:
         ach = bytes_per_launch / per_launch_s / 1e9
@@ -505,7 +566,8 @@ def main():
                 "bytes_per_input_triangle": round(bytes_per_launch / input_tris, 2)}
     if cull:
         extra["cull"] = {"kept_fraction_mean": float(counts_np.mean() / input_tris),
-                         "views": len(vps), "triangles_per_step": input_tris * len(vps)}
+                         "views": len(vps), "views_per_launch": cv,
+                         "triangles_per_step": input_tris * len(vps)}
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gtps", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True,

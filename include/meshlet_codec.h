@@ -402,6 +402,25 @@ mc_status mc_decode_cull(const mc_device_batch *b, const float *d_view_proj,
                          uint32_t *d_status, void *d_scratch, const mc_tuning *t,
                          void *stream);
 
+/* The fused cull against several views in one persistent launch: each
+ * meshlet is staged, dequantised and strip-walked once, then tested, culled
+ * and compacted once per view whose meshlet tests it passes.
+ *   d_view_projs  n_views x 16 FP32 row-major clip matrices, 1 <= n_views <= 8
+ *   d_tri_out     u32; view v's survivors (global index triples, unspecified
+ *                 order) at d_tri_out + v * tri_stride
+ *   tri_stride    u32 elements per view region, >= 3 * total_tris
+ *   d_tri_counts  u32 [n_views]: survivors per view
+ *   d_pos         f32 [3 * total_verts], written for meshlets that pass the
+ *                 meshlet tests of at least one view
+ * Per view, the tests and their FP32 evaluation are mc_decode_cull's, so view
+ * v's survivors are the ones mc_decode_cull returns for matrix v (as a set).
+ * Uses d_scratch words 8-15 for the per-view counts; grabs hold at most 4
+ * meshlets.  MC_ERR_INVALID_ARG for n_views outside 1..8 or a short stride. */
+mc_status mc_decode_cull_views(const mc_device_batch *b, const float *d_view_projs,
+                               uint32_t n_views, uint32_t *d_tri_out, uint64_t tri_stride,
+                               uint32_t *d_tri_counts, float *d_pos, uint32_t *d_status,
+                               void *d_scratch, const mc_tuning *t, void *stream);
+
 /* The fused cull with the survivors in a fixed order: meshlet order, then
  * triangle order within a meshlet -- the order of a sequential decode and
  * cull.  Same arguments and results as mc_decode_cull otherwise, plus
@@ -448,6 +467,16 @@ mc_status mc_graph_capture_cull(const mc_device_batch *b, const float *d_view_pr
                                 uint32_t n_views, uint32_t *d_tri_out, uint32_t *d_tri_count,
                                 float *d_pos, uint32_t *d_status, void *d_scratch,
                                 const mc_tuning *t, void *stream, mc_graph **out);
+/* Same for the multi-view cull: ceil(n_views / 8) launches of
+ * mc_decode_cull_views, launch i covering views 8 i .. 8 i + 7 (any n_views >=
+ * 1); view v writes d_tri_counts[v] and region v mod 8 of d_tri_out (so
+ * d_tri_out holds min(n_views, 8) regions of tri_stride words, which later
+ * launches overwrite). */
+mc_status mc_graph_capture_cull_views(const mc_device_batch *b, const float *d_view_projs,
+                                      uint32_t n_views, uint32_t *d_tri_out, uint64_t tri_stride,
+                                      uint32_t *d_tri_counts, float *d_pos, uint32_t *d_status,
+                                      void *d_scratch, const mc_tuning *t, void *stream,
+                                      mc_graph **out);
 mc_status mc_graph_launch(mc_graph *g, void *stream);
 void mc_graph_free(mc_graph *g);
 

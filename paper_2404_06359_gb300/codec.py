@@ -92,6 +92,8 @@ _SIGS = [
                                           C.POINTER(mc_tuning), P]),
     ("mc_decode_cull", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P, P,
                                  C.POINTER(mc_tuning), P]),
+    ("mc_decode_cull_views", C.c_int, [C.POINTER(mc_device_batch), P, u32, P, u64, P, P, P, P,
+                                       C.POINTER(mc_tuning), P]),
     ("mc_cull_order_bytes", C.c_size_t, [C.POINTER(mc_device_batch)]),
     ("mc_decode_cull_ordered", C.c_int, [C.POINTER(mc_device_batch), P, P, P, P, P, P, P,
                                          C.POINTER(mc_tuning), P]),
@@ -103,6 +105,8 @@ _SIGS = [
                                          C.POINTER(mc_tuning), P, C.POINTER(P)]),
     ("mc_graph_capture_cull", C.c_int, [C.POINTER(mc_device_batch), P, u32, P, P, P, P, P,
                                         C.POINTER(mc_tuning), P, C.POINTER(P)]),
+    ("mc_graph_capture_cull_views", C.c_int, [C.POINTER(mc_device_batch), P, u32, P, u64, P, P,
+                                              P, P, C.POINTER(mc_tuning), P, C.POINTER(P)]),
     ("mc_graph_launch", C.c_int, [P, P]),
     ("mc_graph_free", None, [P]),
     ("mc_decode_batch_host", C.c_int, [C.POINTER(mc_blob_view_t), P, P, P, P, P, P, P, P,
@@ -424,6 +428,16 @@ def mc_decode_batch_noalloc(db: DeviceBatch, d_local, d_global, d_pos, d_status,
                                          _stream(stream)), "mc_decode_batch_noalloc")
 
 
+def mc_decode_cull_views(db: DeviceBatch, d_view_projs, n_views, d_tri_out, tri_stride, d_tri_counts,
+                         d_pos, d_status, d_scratch, tuning=None, stream=None):
+    """Fused cull against n_views (1..8) matrices in one launch: view v's
+    survivors at d_tri_out[v * tri_stride:], its count in d_tri_counts[v]."""
+    _check(lib().mc_decode_cull_views(C.byref(db.c), _tptr(d_view_projs), n_views, _tptr(d_tri_out),
+                                      tri_stride, _tptr(d_tri_counts), _tptr(d_pos),
+                                      _tptr(d_status), _tptr(d_scratch), _tuning(tuning),
+                                      _stream(stream)), "mc_decode_cull_views")
+
+
 def mc_decode_cull(db: DeviceBatch, d_view_proj, d_tri_out, d_tri_count, d_pos, d_status, d_scratch,
                    tuning=None, stream=None):
     _check(lib().mc_decode_cull(C.byref(db.c), _tptr(d_view_proj), _tptr(d_tri_out),
@@ -484,6 +498,20 @@ def mc_graph_capture_cull(db: DeviceBatch, d_view_projs, n_views, d_tri_out, d_t
                                        _tptr(d_tri_count), _tptr(d_pos), _tptr(d_status),
                                        _tptr(d_scratch), _tuning(tuning), _stream(stream), C.byref(h)),
            "mc_graph_capture_cull")
+    return Graph(h)
+
+
+def mc_graph_capture_cull_views(db: DeviceBatch, d_view_projs, n_views, d_tri_out, tri_stride,
+                                d_tri_counts, d_pos, d_status, d_scratch, tuning=None,
+                                stream=None) -> Graph:
+    """Graph of ceil(n_views / 8) multi-view cull launches; view v writes
+    region v % 8 of d_tri_out (tri_stride words each) and d_tri_counts[v]."""
+    h = P()
+    _check(lib().mc_graph_capture_cull_views(C.byref(db.c), _tptr(d_view_projs), n_views,
+                                             _tptr(d_tri_out), tri_stride, _tptr(d_tri_counts),
+                                             _tptr(d_pos), _tptr(d_status), _tptr(d_scratch),
+                                             _tuning(tuning), _stream(stream), C.byref(h)),
+           "mc_graph_capture_cull_views")
     return Graph(h)
 
 

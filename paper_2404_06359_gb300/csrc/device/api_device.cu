@@ -292,6 +292,62 @@ extern "C" mc_status mc_decode_cull(const mc_device_batch *b, const float *d_vie
                              static_cast<cudaStream_t>(stream));
 }
 
+namespace {
+constexpr uint32_t kViewsGrabMax = 4;  // meshlets per grab of the multi-view cull (8 bits each)
+
+mc_status launch_cull_views_checked(const mc_device_batch *b, const float *d_vps, uint32_t n_views,
+                                    uint32_t *d_tri_out, uint64_t tri_stride,
+                                    uint32_t *d_tri_counts, float *d_pos, uint32_t *d_status,
+                                    void *d_scratch, const mc_tuning *t, cudaStream_t s) {
+  const uint32_t warps = (t && t->warps_per_cta) ? t->warps_per_cta : 4;
+  uint32_t per_grab = (t && t->meshlets_per_grab) ? t->meshlets_per_grab : kViewsGrabMax;
+  if (warps < 1 || warps > 32 || per_grab < 1 || per_grab > 16) return MC_ERR_INVALID_ARG;
+  per_grab = std::min(per_grab, kViewsGrabMax);
+  const BatchArgs a = args_of(b);
+  uint32_t grab = per_grab;
+  int occ = max_ctas_per_sm_cull_views(warps, b->max_block_words, a.max_tris, grab, n_views);
+  while (occ <= 0 && grab > 1)
+    occ = max_ctas_per_sm_cull_views(warps, b->max_block_words, a.max_tris, --grab, n_views);
+  if (occ <= 0) return MC_ERR_INVALID_ARG;
+  uint32_t per_sm = (t && t->ctas_per_sm) ? std::min<uint32_t>(t->ctas_per_sm, occ) : (uint32_t)occ;
+  uint32_t ctas = per_sm * (uint32_t)sm_count();
+  if (ctas == 0) return MC_ERR_CUDA;
+  cudaError_t e = launch_cull_views(a, d_vps, n_views, b->cones, ctas, warps, grab,
+                                    t && t->checked, d_tri_out, tri_stride, d_tri_counts, d_pos,
+                                    d_status, static_cast<uint32_t *>(d_scratch), s);
+  if (e == cudaSuccess) g_launches++;
+  return from_cuda(e);
+}
+
+mc_status check_cull_views(const mc_device_batch *b, const float *d_view_projs, uint32_t n_views,
+                           uint32_t *d_tri_out, uint64_t tri_stride, uint32_t *d_tri_counts,
+                           float *d_pos, void *d_scratch) {
+  mc_status st = check_batch(b);
+  if (st != MC_OK) return st;
+  if (!d_view_projs || !aligned(d_view_projs, 4) || n_views == 0 || !d_tri_out ||
+      !aligned(d_tri_out, 4) || !d_tri_counts || !d_pos || !d_scratch || !aligned(d_scratch, 16) ||
+      tri_stride < 3 * b->total_tris)
+    return MC_ERR_INVALID_ARG;
+  return MC_OK;
+}
+}  // namespace
+
+extern "C" mc_status mc_decode_cull_views(const mc_device_batch *b, const float *d_view_projs,
+                                          uint32_t n_views, uint32_t *d_tri_out,
+                                          uint64_t tri_stride, uint32_t *d_tri_counts,
+                                          float *d_pos, uint32_t *d_status, void *d_scratch,
+                                          const mc_tuning *t, void *stream) {
+  if (!b || !d_tri_counts || n_views == 0 || n_views > 8) return MC_ERR_INVALID_ARG;
+  if (b->n_meshlets == 0)
+    return from_cuda(
+        cudaMemsetAsync(d_tri_counts, 0, 4ull * n_views, static_cast<cudaStream_t>(stream)));
+  mc_status st =
+      check_cull_views(b, d_view_projs, n_views, d_tri_out, tri_stride, d_tri_counts, d_pos, d_scratch);
+  if (st != MC_OK) return st;
+  return launch_cull_views_checked(b, d_view_projs, n_views, d_tri_out, tri_stride, d_tri_counts,
+                                   d_pos, d_status, d_scratch, t, static_cast<cudaStream_t>(stream));
+}
+
 extern "C" size_t mc_cull_order_bytes(const mc_device_batch *b) {
   return b ? 8ull * b->n_meshlets + 16 : 0;
 }
@@ -467,6 +523,33 @@ extern "C" mc_status mc_graph_capture_cull(const mc_device_batch *b, const float
         for (uint32_t i = 0; i < n_views; i++) {
           mc_status s2 = launch_cull_checked(b, d_view_projs + 16 * (size_t)i, d_tri_out,
                                              d_tri_count + i, d_pos, d_status, d_scratch, t, cs);
+          if (s2 != MC_OK) return s2;
+        }
+        return MC_OK;
+      },
+      out);
+}
+
+extern "C" mc_status mc_graph_capture_cull_views(const mc_device_batch *b,
+                                                 const float *d_view_projs, uint32_t n_views,
+                                                 uint32_t *d_tri_out, uint64_t tri_stride,
+                                                 uint32_t *d_tri_counts, float *d_pos,
+                                                 uint32_t *d_status, void *d_scratch,
+                                                 const mc_tuning *t, void *stream, mc_graph **out) {
+  if (!out) return MC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!b || b->n_meshlets == 0) return MC_ERR_INVALID_ARG;
+  mc_status st =
+      check_cull_views(b, d_view_projs, n_views, d_tri_out, tri_stride, d_tri_counts, d_pos, d_scratch);
+  if (st != MC_OK) return st;
+  (void)stream;
+  return capture(
+      [&](cudaStream_t cs) {
+        for (uint32_t v0 = 0; v0 < n_views; v0 += 8) {
+          mc_status s2 = launch_cull_views_checked(b, d_view_projs + 16 * (size_t)v0,
+                                                   std::min(8u, n_views - v0), d_tri_out, tri_stride,
+                                                   d_tri_counts + v0, d_pos, d_status, d_scratch, t,
+                                                   cs);
           if (s2 != MC_OK) return s2;
         }
         return MC_OK;

@@ -32,6 +32,17 @@ cudaError_t launch_cull(const BatchArgs &a, const float *view_proj, const mc_con
 
 int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words, uint32_t per_grab,
                           bool vertices = false);
+// Multi-view fused cull (1 <= n_views <= 8, per_grab <= 4): view v's
+// survivors go to tri_out + v * tri_stride, its count to tri_counts[v].
+uint32_t cull_views_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, uint32_t per_grab,
+                                  uint32_t n_views);
+cudaError_t launch_cull_views(const BatchArgs &a, const float *view_projs, uint32_t n_views,
+                              const mc_cone *cones, uint32_t ctas, uint32_t warps,
+                              uint32_t per_grab, bool checked, uint32_t *tri_out,
+                              uint64_t tri_stride, uint32_t *tri_counts, float *out_pos,
+                              uint32_t *status, uint32_t *scratch, cudaStream_t s);
+int max_ctas_per_sm_cull_views(uint32_t warps, uint32_t max_block_words, uint32_t max_tris,
+                               uint32_t per_grab, uint32_t n_views);
 int max_ctas_per_sm_cull(uint32_t warps, uint32_t max_block_words, uint32_t max_tris,
                          uint32_t per_grab);
 

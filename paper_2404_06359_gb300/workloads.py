@@ -123,14 +123,11 @@ def _eye64(vp: np.ndarray):
     return np.linalg.solve(a, -m[[0, 1, 3], 3])
 
 
-def cull_bytes(stats: dict, arrays: dict, vps: np.ndarray, counts: np.ndarray,
-               cones: bool = False) -> int:
-    """Mean algorithmic bytes of one fused decode+cull launch: every descriptor
-    and grid entry (and cone record, with cones), the payload and positions of
-    the meshlets that pass the meshlet tests -- quantisation box not wholly
-    outside one clip plane, normal cone not facing away (both in FP64: exact
-    decisions near a boundary do not matter for a byte count) -- and the
-    surviving triangles (12 B each)."""
+def _meshlet_passes(arrays: dict, vps: np.ndarray, cones: bool):
+    """Per view, the meshlets that pass the meshlet tests -- quantisation box
+    not wholly outside one clip plane, normal cone not facing away (both in
+    FP64: exact decisions near a boundary do not matter for a byte count) --
+    and each meshlet's payload words and vertex count."""
     w = arrays["desc"].view(np.uint32).reshape(-1, 8)
     V = (w[:, 3] & 0xFFFF).astype(np.int64)
     T = (w[:, 3] >> 16).astype(np.int64)
@@ -147,8 +144,8 @@ def cull_bytes(stats: dict, arrays: dict, vps: np.ndarray, counts: np.ndarray,
     ch = np.concatenate([corners, np.ones(corners.shape[:2] + (1,))], 2)
     if cones:
         cn = arrays["cones"].view(np.float32).reshape(-1, 8).astype(np.float64)
-    total = 0.0
-    for vp, cnt in zip(vps, counts):
+    keeps = []
+    for vp in vps:
         clip = ch @ vp.reshape(4, 4).astype(np.float64).T           # [M, 8, 4]
         wv = clip[..., 3]
         out = np.zeros(w.shape[0], bool)
@@ -159,7 +156,25 @@ def cull_bytes(stats: dict, arrays: dict, vps: np.ndarray, counts: np.ndarray,
             v = cn[:, 0:3] - eye
             d = (cn[:, 4:7] * v).sum(1)
             out |= (cn[:, 7] < 1) & (d >= cn[:, 7] * np.linalg.norm(v, axis=1) + cn[:, 3])
-        keep = ~out
-        total += (4 * words[keep].sum() + 12 * V[keep].sum() + 12 * int(cnt))
+        keeps.append(~out)
+    return keeps, words, V
+
+
+def cull_bytes(stats: dict, arrays: dict, vps: np.ndarray, counts: np.ndarray,
+               cones: bool = False, views_per_launch: int = 1) -> int:
+    """Mean algorithmic bytes of one fused decode+cull launch over
+    views_per_launch consecutive views: every descriptor and grid entry (and
+    cone record, with cones), the payload and positions of the meshlets that
+    pass the meshlet tests of at least one of the launch's views, and the
+    surviving triangles of each view (12 B each)."""
+    keeps, words, V = _meshlet_passes(arrays, vps, cones)
+    M = words.size
     per_meshlet = 64 if cones else 32
-    return int(per_meshlet * w.shape[0] + 32 * stats["n_grids"] + total / len(vps))
+    launches = []
+    for v0 in range(0, len(vps), views_per_launch):
+        k = np.zeros(M, bool)
+        for kk in keeps[v0:v0 + views_per_launch]:
+            k |= kk
+        n = int(np.sum(np.asarray(counts[v0:v0 + views_per_launch], np.int64)))
+        launches.append(4 * words[k].sum() + 12 * V[k].sum() + 12 * n)
+    return int(per_meshlet * M + 32 * stats["n_grids"] + float(np.mean(launches)))

@@ -246,3 +246,116 @@ def test_cull_ordered_is_the_sequential_order(request, which, tuning):
             assert np.array_equal(tri, ref)
             vm = np.repeat(passed, f["V"].astype(np.int64)).astype(bool)
             assert np.array_equal(pos.reshape(-1, 3)[vm].view(np.uint32), ref_pos[vm].view(np.uint32))
+
+
+def _affine_view(blob):
+    lo = blob.grids.view(np.float32).reshape(-1, 8)[:, :3].min(0)
+    vp = np.eye(4, dtype=np.float32) * np.float32(0.02)
+    vp[3, 3] = 1.0
+    vp[:3, 3] = -0.02 * (lo + 4.0)
+    return vp.reshape(16)
+
+
+def _views_of(blob, vps, n):
+    """n matrices: the fixture's views, an affine one (no camera), repeats."""
+    pool = [np.asarray(v, np.float32).reshape(16) for v in vps] + [_affine_view(blob)]
+    pool += pool[::-1]
+    return np.stack(pool[:n])
+
+
+def _run_views(db, vps, tuning=None):
+    import torch
+    T, V = db.stats["total_tris"], db.stats["total_verts"]
+    n = len(vps)
+    stride = 3 * T + 5
+    tri = torch.full((n * stride,), -1, dtype=torch.int32, device="cuda")
+    cnt = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    pos = torch.zeros(3 * V, dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    scratch = mc.new_scratch()
+    d_vps = torch.from_numpy(np.ascontiguousarray(vps, np.float32)).cuda()
+    mc.mc_decode_cull_views(db, d_vps, n, tri, stride, cnt, pos, st, scratch, tuning)
+    torch.cuda.synchronize()
+    assert int(scratch.abs().sum()) == 0
+    t = tri.cpu().numpy().view(np.uint32)
+    c = cnt.cpu().numpy()
+    outs = [t[v * stride: v * stride + 3 * int(c[v])].reshape(-1, 3) for v in range(n)]
+    # nothing past each view's survivors is written
+    for v in range(n):
+        assert np.all(t[v * stride + 3 * int(c[v]): (v + 1) * stride] == 0xFFFFFFFF)
+    return outs, pos.cpu().numpy(), int(st.item())
+
+
+@pytest.mark.parametrize("tuning", [None, {"warps_per_cta": 8, "meshlets_per_grab": 16},
+                                    {"warps_per_cta": 4, "meshlets_per_grab": 1, "checked": 1},
+                                    {"warps_per_cta": 16, "meshlets_per_grab": 3}])
+@pytest.mark.parametrize("which", ["scene", "smooth_scene"])
+def test_cull_views_vs_oracle(request, which, tuning):
+    """One launch against n views gives, per view, the oracle's survivors for
+    that matrix (as a multiset); positions of meshlets passing any view are
+    the oracle's to 0 ulp."""
+    blob, vps = request.getfixturevalue(which)
+    f = blob.fields()
+    ref_pos = O.decode(blob)[2]
+    for use_cones in (False, True):
+        db = device_batch_from_oracle(blob, cones=use_cones)
+        for n in (1, 3, 8):
+            views = _views_of(blob, vps, n)
+            outs, pos, st = _run_views(db, views, tuning)
+            assert st == 0
+            any_pass = np.zeros(f["V"].size, bool)
+            for v in range(n):
+                ref, _, passed = O.decode_cull(blob, views[v], cones=blob.cones if use_cones else None)
+                assert outs[v].shape == ref.shape, (v, outs[v].shape, ref.shape)
+                assert np.array_equal(_sorted_rows(outs[v]), _sorted_rows(ref)), v
+                any_pass |= passed.astype(bool)
+            vm = np.repeat(any_pass, f["V"].astype(np.int64))
+            assert np.array_equal(pos.reshape(-1, 3)[vm].view(np.uint32), ref_pos[vm].view(np.uint32))
+
+
+def test_cull_views_graph_64_views(smooth_scene):
+    """The multi-view graph over more views than one launch takes: every
+    count equals the oracle's, the last launch's regions hold its views."""
+    import torch
+    blob, vps = smooth_scene
+    db = device_batch_from_oracle(blob, cones=True)
+    T, V = db.stats["total_tris"], db.stats["total_verts"]
+    views = np.concatenate([_views_of(blob, vps, 8)] * 3)[:19]  # 3 launches: 8 + 8 + 3
+    stride = 3 * T
+    tri = torch.zeros(8 * stride, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(len(views), dtype=torch.int32, device="cuda")
+    pos = torch.zeros(3 * V, dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    scratch = mc.new_scratch()
+    d_vps = torch.from_numpy(np.ascontiguousarray(views, np.float32)).cuda()
+    g = mc.mc_graph_capture_cull_views(db, d_vps, len(views), tri, stride, cnt, pos, st, scratch)
+    for _ in range(2):
+        g.launch()
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and int(scratch.abs().sum()) == 0
+    c = cnt.cpu().numpy()
+    t = tri.cpu().numpy().view(np.uint32)
+    for v in range(len(views)):
+        ref, _, _ = O.decode_cull(blob, views[v], cones=blob.cones)
+        assert c[v] == ref.shape[0], v
+        if v >= 16:  # the last launch's views (regions 0..2)
+            r = v - 16
+            got = t[r * stride: r * stride + 3 * int(c[v])].reshape(-1, 3)
+            assert np.array_equal(_sorted_rows(got), _sorted_rows(ref))
+
+
+def test_cull_views_arguments():
+    import torch
+    blob = O.encode_mesh(G.grid_mesh(8), (64, 126), 16, 0)
+    db = device_batch_from_oracle(blob)
+    T, V = db.stats["total_tris"], db.stats["total_verts"]
+    vps = torch.zeros((9, 16), dtype=torch.float32, device="cuda")
+    tri = torch.zeros(9 * 3 * T, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(9, dtype=torch.int32, device="cuda")
+    pos = torch.zeros(3 * V, dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    scratch = mc.new_scratch()
+    for n, stride in ((0, 3 * T), (9, 3 * T), (2, 3 * T - 1)):
+        with pytest.raises(mc.CodecError) as e:
+            mc.mc_decode_cull_views(db, vps, n, tri, stride, cnt, pos, st, scratch)
+        assert e.value.status == 1
