@@ -174,7 +174,8 @@ def _barrier(ws):
         dist.barrier()
 
 
-def build_workload(cfg: int, rank: int, codec: str = "reuse", attrs: bool = False):
+def build_workload(cfg: int, rank: int, codec: str = "reuse", attrs: bool = False,
+                   cfg4_tris: int = 50_000_000):
     from paper_2404_06359_gb300 import workloads as W
     if cfg == 1:
         blob, meshes = W.cfg1()
@@ -186,7 +187,7 @@ def build_workload(cfg: int, rank: int, codec: str = "reuse", attrs: bool = Fals
         blob, meshes = W.cfg3(rank, plain_gts=codec == "gts")
         return blob, meshes, None
     if cfg == 4:
-        return W.cfg4(rank)
+        return W.cfg4(rank, min_tris=cfg4_tris)
     raise SystemExit(f"unknown config {cfg}")
 
 
@@ -304,6 +305,8 @@ def main():
                          "16-bit attributes) decoded by mc_decode_batch_vertices")
     ap.add_argument("--cull-views", type=int, default=8, choices=range(1, 9), metavar="1..8",
                     help="config 4: views per fused-cull launch (1 = one launch per view)")
+    ap.add_argument("--cfg4-tris", type=int, default=50_000_000,
+                    help="config 4 batch size (smaller only for profiler captures)")
     ap.add_argument("--codec", choices=("reuse", "gts"), default="reuse",
                     help="connectivity encoding of configs 2/3: GTS-Reuse (default) or plain GTS "
                          "(one stored 8-bit entry per triangle)")
@@ -329,7 +332,7 @@ def main():
         raise SystemExit("--codec gts applies to configs 2 and 3")
     if args.attrs and args.config != 2:
         raise SystemExit("--attrs applies to config 2")
-    blob, meshes, vps = build_workload(args.config, rank, args.codec, args.attrs)
+    blob, meshes, vps = build_workload(args.config, rank, args.codec, args.attrs, args.cfg4_tris)
     t_build = time.time() - t_build
     stats = blob.stats()
     db = mc.DeviceBatch(blob, "cuda", cones=args.config == 4,  # cfg4: normal-cone meshlet test on
@@ -575,7 +578,9 @@ def main():
         "config": {"workload": WORKLOADS[args.config] + (" [plain GTS connectivity]"
                                                           if args.codec == "gts" else "")
                    + (" [8-channel vertices: position, normal, texture coordinate; 32 B out]"
-                      if args.attrs else ""),
+                      if args.attrs else "")
+                   + (f" [reduced to >= {args.cfg4_tris} triangles]"
+                      if args.config == 4 and args.cfg4_tris != 50_000_000 else ""),
                    "connectivity_bits_per_triangle": round(stats["conn_bits"] / input_tris, 3),
                    "input_triangles": input_tris,
                    "decoded_triangle_slots": stats["total_tris"], "vertices": stats["total_verts"],

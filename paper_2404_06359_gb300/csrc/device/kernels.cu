@@ -196,6 +196,27 @@ __device__ __forceinline__ float clip_row(const float *M, int r, float x, float 
   return __fmaf_rn(M[4 * r + 2], z, __fmaf_rn(M[4 * r + 1], y, __fmaf_rn(M[4 * r + 0], x, M[4 * r + 3])));
 }
 
+// Rows 0, 1 and 3 of a clip matrix in registers (clip x, y and w), so that a
+// loop whose shared-memory stores could alias the matrix does not reload it.
+struct ClipRows {
+  float m[12];
+};
+__device__ __forceinline__ ClipRows clip_rows(const float *M) {
+  ClipRows c;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    c.m[i] = M[i];
+    c.m[4 + i] = M[4 + i];
+    c.m[8 + i] = M[12 + i];
+  }
+  return c;
+}
+// clip_row's operation order; r = 0, 1, 2 for rows 0, 1, 3
+__device__ __forceinline__ float clip_dot(const ClipRows &c, int r, float x, float y, float z) {
+  return __fmaf_rn(c.m[4 * r + 2], z,
+                   __fmaf_rn(c.m[4 * r + 1], y, __fmaf_rn(c.m[4 * r + 0], x, c.m[4 * r + 3])));
+}
+
 // Camera position of a clip matrix M (row-major, in shared memory): the point
 // whose clip x, y and w are zero, from rows r0, r1, r3 and b_i = -M[i][3] by
 // the cross-product inverse in FP64,
@@ -625,7 +646,8 @@ struct CullViewsLayout {
 // the strip entries, the meshlet's positions (x, y, z arrays) and clip x, y,
 // w (V <= min(T' + 2, 256) entries), one packed word per triangle slot of
 // the strip walk (32 per word of flags), and one survivor buffer of cap
-// words per view.
+// bytes per view (the survivors' triangle slots: a quarter of the shared
+// memory packed words would take, which leaves room for more warps per SM).
 __host__ __device__ inline CullViewsLayout cull_views_layout(uint32_t max_block_words,
                                                              uint32_t max_tris, uint32_t per_grab,
                                                              uint32_t n_views) {
@@ -636,8 +658,8 @@ __host__ __device__ inline CullViewsLayout cull_views_layout(uint32_t max_block_
   l.clip = l.pos + 12 * l.n_vtx;
   l.tri = l.clip + 12 * l.n_vtx;
   l.surv = l.tri + 4 * ((max_tris + 31) & ~31u);
-  l.cap = (max_tris + 3) & ~3u;
-  l.bytes = l.surv + 4 * l.cap * n_views;
+  l.cap = (max_tris + 15) & ~15u;
+  l.bytes = l.surv + ((l.cap * n_views + 15) & ~15u);
   return l;
 }
 uint32_t cull_views_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, uint32_t per_grab,
@@ -649,7 +671,8 @@ uint32_t cull_views_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, u
 // positions go to out_pos and to shared memory, the strip walk leaves one
 // word per triangle slot (x | y << 8 | z << 16, or 0 for a dead slot or a
 // triangle with two equal indices), then per view the clip coordinates,
-// the back-face test and the compaction into that view's buffer.  Lane v
+// the back-face test and the compaction of the surviving slots (one byte
+// each) into that view's buffer.  Lane v
 // returns the survivor count of view v (0 for the others); the result is
 // false for a corrupt stream (checked build).
 template <bool CHECKED, bool B16, int RM>
@@ -689,16 +712,16 @@ __device__ __forceinline__ bool cull_views_staged(const Desc &d, const Grid &g, 
   const uint32_t tpasses = (d.T + 31) >> 5;
   for (uint32_t vw = views; vw; vw &= vw - 1) {
     const uint32_t view = __ffs(vw) - 1;
-    const float *M = Ms + 16 * view;
+    const ClipRows cr = clip_rows(Ms + 16 * view);
     v = lane;
     for (uint32_t i = 0; i < vpasses; i++, v += 32) {
       const uint32_t vv = min(v, d.V - 1);
       const float x = px[vv], y = py[vv], z = pz[vv];
-      cxy[vv] = make_float2(clip_row(M, 0, x, y, z), clip_row(M, 1, x, y, z));
-      cw[vv] = clip_row(M, 3, x, y, z);
+      cxy[vv] = make_float2(clip_dot(cr, 0, x, y, z), clip_dot(cr, 1, x, y, z));
+      cw[vv] = clip_dot(cr, 2, x, y, z);
     }
     __syncwarp();
-    const uint32_t a_surv = smem_addr(surv + cap * view);
+    const uint32_t a_surv = smem_addr(reinterpret_cast<uint8_t *>(surv) + cap * view);
     uint32_t n = 0;
     uint32_t k = lane;
     for (uint32_t i = 0; i < tpasses; i++, k += 32) {
@@ -713,7 +736,7 @@ __device__ __forceinline__ bool cull_views_staged(const Desc &d, const Grid &g, 
       const bool behind = (w0 <= 0.0f) | (w1 <= 0.0f) | (w2 <= 0.0f);
       const bool keep = (t != 0u) & (behind | (det > 0.0f));
       const uint32_t bal = __ballot_sync(kFull, keep);
-      sts_u32_if(a_surv + 4 * (n + __popc(bal & ((1u << lane) - 1u))), t, keep);
+      sts_u8_if(a_surv + n + __popc(bal & ((1u << lane) - 1u)), k, keep);
       n += __popc(bal);
     }
     if (lane == view) my_n = n;
@@ -782,18 +805,22 @@ __global__ void __launch_bounds__(MAX_THREADS) decode_cull_views_kernel(
                 __syncwarp();
                 return;
               }
-              // one atomic per view with survivors (lane v), then the views' writes
+              // one atomic per view with survivors (lane v), then the views' writes:
+              // a lane per survivor, its packed word looked up by slot
               uint32_t dst = 0;
               if (my_n) dst = atomicAdd(scratch + kViewCount + lane, my_n);
               for (uint32_t vw = __ballot_sync(kFull, my_n != 0); vw; vw &= vw - 1) {
                 const uint32_t view = __ffs(vw) - 1;
                 const uint32_t n = __shfl_sync(kFull, my_n, view);
                 const uint32_t o0 = __shfl_sync(kFull, dst, view);
-                uint32_t *o = tri_out + tri_stride * view + 3ull * o0;
-                const uint32_t *sv = surv + L.cap * view;
-                for (uint32_t e = lane; e < 3 * n; e += 32) {
-                  const uint32_t t = e / 3, c = e - 3 * t;
-                  o[e] = d.vbase + ((sv[t] >> (8 * c)) & 0xFFu);
+                // one survivor per lane: three global indices from its packed word
+                uint32_t *o = tri_out + tri_stride * view + 3ull * (o0 + lane);
+                const uint32_t a_sv = smem_addr(reinterpret_cast<uint8_t *>(surv) + L.cap * view);
+                const uint32_t a_tr = smem_addr(stri);
+                for (uint32_t t = lane; t < n; t += 32, o += 96) {
+                  const uint32_t p = lds_u32(a_tr + 4 * lds_u8(a_sv + t));
+                  stg3_u32_if(o, d.vbase + (p & 0xFFu), d.vbase + ((p >> 8) & 0xFFu),
+                              d.vbase + (p >> 16), true);
                 }
               }
               __syncwarp();
