@@ -53,10 +53,13 @@ def _peaks():
 
 
 # DRAM bytes (read + write) of one launch of the dominant kernel from an ncu
-# capture (profiles/decode_batch_cfg2.md for cfg2, profiles/decode_cull_cfg4.md
-# for cfg4), per decoded triangle slot and keyed by the kernel-source hash it
-# was taken on; reported only while the sources match.
-NCU_TRAFFIC = {"4c328bdd02633302": {2: 429.168128e6 / 18015946, 4: 879.191040e6 / 55596770}}
+# capture (profiles/decode_batch_cfg2.md for cfg2: one decode_batch launch;
+# profiles/decode_cull_views_cfg4.md for cfg4: one 8-view decode_cull_views
+# launch, captured on the 20 M-triangle reduction of the batch), per decoded
+# triangle slot and keyed by the kernel-source hash it was taken on; reported
+# only while the sources match.
+NCU_TRAFFIC = {"6f68312ae776f512": {2: 415.40352e6 / 17124622,
+                                    4: (113.75744e6 + 1029.676e6) / 21162408}}
 
 
 def _kernel_hash():
@@ -560,7 +563,8 @@ def main():
         ach = bytes_per_launch / per_launch_s / 1e9
         tr = NCU_TRAFFIC.get(_kernel_hash())
         traffic = None
-        if tr and args.config in tr and args.codec == "reuse" and not args.attrs:
+        if (tr and args.config in tr and args.codec == "reuse" and not args.attrs
+                and (args.config != 4 or args.cull_views == 8)):
             traffic = int(tr[args.config] * stats["total_tris"])  # per launch (one view for cfg4)
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "traffic": traffic,
