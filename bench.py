@@ -58,18 +58,22 @@ def _peaks():
 # launch, captured on the 20 M-triangle reduction of the batch), per decoded
 # triangle slot and keyed by the kernel-source hash it was taken on; reported
 # only while the sources match.
-NCU_TRAFFIC = {"6f68312ae776f512": {2: 415.40352e6 / 17124622,
-                                    4: (113.75744e6 + 1029.676e6) / 21162408}}
+NCU_TRAFFIC = {  # config -> (device-code hash, DRAM bytes per decoded triangle slot)
+    2: ("846363d9384b0863", (86.488064e6 + 328.722688e6) / 17124622),
+    4: ("61f54bf40e08143c", (114.16832e6 + 1030.18e6) / 21162408),
+}
 
 
-def _kernel_hash():
-    """Hash of the device code (kernels.cu up to its host launchers, and the
-    device headers)."""
+def _kernel_hash(config: int):
+    """Hash of the device code the config's dominant kernel is built from: the
+    shared device headers and its kernel file (kernels.cu for the decoders,
+    cull_views.cu with the cull helpers for the multi-view cull), each up to
+    its host launchers."""
     import hashlib
     h = hashlib.sha256()
-    for p in ("paper_2404_06359_gb300/csrc/device/kernels.cu",
-              "paper_2404_06359_gb300/csrc/device/decode_warp.cuh",
-              "paper_2404_06359_gb300/csrc/device/grab_loop.cuh"):
+    files = ["cull_views.cu", "cull_common.cuh"] if config == 4 else ["kernels.cu"]
+    for p in ["paper_2404_06359_gb300/csrc/device/" + f
+              for f in files + ["decode_warp.cuh", "grab_loop.cuh"]]:
         with open(os.path.join(ROOT, p), "rb") as f:
             b = f.read()
         h.update(b.split(b"// ------------------------------------------------------------- launchers")[0])
@@ -561,11 +565,11 @@ def main():
     roof = None
     if bytes_per_launch:
         ach = bytes_per_launch / per_launch_s / 1e9
-        tr = NCU_TRAFFIC.get(_kernel_hash())
+        tr = NCU_TRAFFIC.get(args.config)
         traffic = None
-        if (tr and args.config in tr and args.codec == "reuse" and not args.attrs
+        if (tr and tr[0] == _kernel_hash(args.config) and args.codec == "reuse" and not args.attrs
                 and (args.config != 4 or args.cull_views == 8)):
-            traffic = int(tr[args.config] * stats["total_tris"])  # per launch (one view for cfg4)
+            traffic = int(tr[1] * stats["total_tris"])  # per launch (8 views for cfg4)
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS hbm_gbs)",

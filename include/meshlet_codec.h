@@ -427,9 +427,10 @@ mc_status mc_decode_cull_views(const mc_device_batch *b, const float *d_view_pro
  *   d_order  device buffer of mc_cull_order_bytes(b) bytes, 8-byte aligned,
  *            library-owned for the duration of the call (cleared by it)
  * The order comes from a decoupled look-back over the work-queue grabs
- * (each warp publishes its grab's survivor count and sums its predecessors'
- * back to the nearest published prefix); grabs hold at most 6 meshlets in
- * this mode.  Every wait is bounded: a wait that gives up sets
+ * (each warp publishes its grab's survivor count as soon as the grab is
+ * decoded, and after its next grab sums the counts of the first grab's
+ * predecessors back to the nearest published prefix); grabs hold at most 3
+ * meshlets in this mode.  Every wait is bounded: a wait that gives up sets
  * MC_ERR_TIMEOUT in the status word.  Calls that overlap on the GPU must not
  * share d_order or d_scratch. */
 size_t mc_cull_order_bytes(const mc_device_batch *b);

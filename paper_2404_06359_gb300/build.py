@@ -19,8 +19,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmeshletcodec.so")
 
 HOST_SOURCES = ["host/meshletize.cpp", "host/strip.cpp", "host/encode.cpp"]
-DEVICE_SOURCES = ["device/kernels.cu", "device/api_device.cu"]
-HEADERS = ["host/host_internal.h", "device/decode_warp.cuh", "device/grab_loop.cuh", "device/kernels.h"]
+DEVICE_SOURCES = ["device/kernels.cu", "device/cull.cu", "device/cull_views.cu", "device/api_device.cu"]
+HEADERS = ["host/host_internal.h", "device/decode_warp.cuh", "device/grab_loop.cuh", "device/cull_common.cuh", "device/kernels.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

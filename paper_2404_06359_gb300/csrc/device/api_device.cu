@@ -246,7 +246,7 @@ extern "C" mc_status mc_decode_batch_vertices(const mc_device_batch *b, uint8_t 
 }
 
 namespace {
-constexpr uint32_t kOrderedGrabMax = 6;  // a whole grab's survivors fit a warp's buffer
+constexpr uint32_t kOrderedGrabMax = 3;  // two grabs' survivors fit a warp's buffer
 
 mc_status launch_cull_checked(const mc_device_batch *b, const float *d_vp, uint32_t *d_tri_out,
                               uint32_t *d_tri_count, float *d_pos, uint32_t *d_status,

@@ -18,6 +18,9 @@
 
 namespace mcdev {
 
+// Scratch words used by the persistent kernels.
+enum { kQueue = 0, kDone = 1, kCount = 2, kViewCount = 8 };  // kViewCount..+7: per-view counts
+constexpr uint32_t kMaxViews = 8;
 constexpr long long kWaitCycles = 1ll << 31;  // about one second at 2 GHz
 
 // mbarrier / bulk-copy / proxy-fence primitives (32-bit shared addresses).

@@ -9,6 +9,15 @@
 
 namespace mcdev {
 
+// Launch set-up shared by the kernel files: raises a kernel's dynamic
+// shared-memory limit once per device (prepare) and caches occupancy answers.
+void prepare(const void *f);
+int occupancy(const void *f, int threads, int smem);
+template <class K>
+const void *fn(K k) {
+  return reinterpret_cast<const void *>(k);
+}
+
 uint32_t decode_smem_per_warp(uint32_t max_block_words);
 uint32_t cull_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, uint32_t per_grab);
 uint32_t batch_smem_per_warp(uint32_t max_block_words, uint32_t per_grab);
