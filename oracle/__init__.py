@@ -304,6 +304,33 @@ def decode(blob: Blob, first: int = 0, count: int | None = None, want_pos64: boo
             None if pos64 is None else pos64.reshape(-1, 3))
 
 
+def decode_into(blob: Blob, first: int, count: int, loc: np.ndarray, glob: np.ndarray,
+                pos: np.ndarray) -> None:
+    """orc_decode of meshlets [first, first + count) into caller-owned
+    whole-batch arrays (uint8 [3 T'_total], uint32 [3 T'_total], float32
+    [3 V_total]).  ctypes releases the GIL during the call, so disjoint
+    ranges may be decoded from several threads at once."""
+    _check(lib().orc_decode(_p(blob.desc), blob.n_meshlets, _p(blob.payload), blob.payload.size,
+                            _p(blob.grids), blob.n_grids, first, count, _p(loc), _p(glob),
+                            _p(pos), None), "orc_decode")
+
+
+def decode_cull_into(blob: Blob, vp: np.ndarray, first: int, count: int, cones, out: np.ndarray,
+                     pos: np.ndarray) -> int:
+    """orc_decode_cull of meshlets [first, first + count): survivors from
+    out[0] (uint32, room for 3 T' of the range), positions into the
+    whole-batch pos (float32 [3 V_total]); returns the survivor count.  Like
+    decode_into, callable from several threads on disjoint ranges."""
+    cnt = C.c_uint64(0)
+    vp = np.ascontiguousarray(np.asarray(vp, np.float32).reshape(16))
+    cn = None if cones is None else np.ascontiguousarray(np.asarray(cones, np.uint8).reshape(-1, 32))
+    _check(lib().orc_decode_cull(_p(blob.desc), blob.n_meshlets, _p(blob.payload),
+                                 blob.payload.size, _p(blob.grids), blob.n_grids, first, count,
+                                 _p(vp), _p(cn), _p(out), C.byref(cnt), _p(pos), None),
+           "orc_decode_cull")
+    return int(cnt.value)
+
+
 def decode_attrs(blob: Blob, first: int = 0, count: int | None = None) -> np.ndarray:
     """float32 [V_total, n_attr] decoded attribute channels (meshlets outside
     the range left zero)."""
