@@ -15,7 +15,7 @@ height-field scans, Sec. 5):
                            Gaussian noise along the normal (sigma = 1% of the
                            sphere radius or of the torus tube radius).
 * ``height_field_disc``    jittered grid clipped to a disc, each quad split
-                           along its shorter diagonal, heights from 4-octave
+                           along its Delaunay diagonal, heights from 4-octave
                            value noise, triangles tagged with one of three
                            120-degree sectors (meshlet-limit classes).
 * ``vertex_attributes``    normals and texture coordinates (the rest of an
@@ -258,8 +258,16 @@ SECTOR_LIMITS = ((64, 126), (128, 128), (256, 256))
 def height_field_disc(total_tris: int = 50_000_000, seed: int = SEED_BASE + 3,
                       jitter: float = 0.25) -> Mesh:
     """Jittered unit grid clipped to a disc (quads whose four corners lie in
-    the disc), each quad split along its shorter xy diagonal, z from 4-octave
-    value noise. ``tri_class`` = 120-degree sector of the quad centre (0,1,2)."""
+    the disc), each quad split along its Delaunay diagonal, z from 4-octave
+    value noise. ``tri_class`` = 120-degree sector of the quad centre (0,1,2).
+
+    The diagonal v00-v11 is taken unless v01 lies strictly inside the
+    circumcircle of (v00, v10, v11) (the in-circle determinant, in FP64 on the
+    FP32 xy positions, relative to v01).  With jitter <= 0.25 no other point
+    comes inside those circles, so the triangles are exactly the Delaunay
+    triangles of the point set that fall in the clipped region (up to the
+    rounding of quads within about 1e-12 of cocircular, where either diagonal
+    is Delaunay to that precision)."""
     rng = _rng(seed)
     radius = math.sqrt(total_tris / (2.0 * math.pi))
     rc = int(math.ceil(radius)) + 1
@@ -286,10 +294,15 @@ def height_field_disc(total_tris: int = 50_000_000, seed: int = SEED_BASE + 3,
     v10 = vid[qy, qx + 1]
     v01 = vid[qy + 1, qx]
     v11 = vid[qy + 1, qx + 1]
-    p = pos.astype(np.float64)
-    d_main = np.sum((p[v11, :2] - p[v00, :2]) ** 2, 1)
-    d_anti = np.sum((p[v01, :2] - p[v10, :2]) ** 2, 1)
-    main = d_main <= d_anti
+    p = pos[:, :2].astype(np.float64)
+    d = p[v01]
+    ax, ay = p[v00, 0] - d[:, 0], p[v00, 1] - d[:, 1]
+    bx, by = p[v10, 0] - d[:, 0], p[v10, 1] - d[:, 1]
+    cx, cy = p[v11, 0] - d[:, 0], p[v11, 1] - d[:, 1]
+    incircle = ((ax * ax + ay * ay) * (bx * cy - cx * by) - (bx * bx + by * by) * (ax * cy - cx * ay)
+                + (cx * cx + cy * cy) * (ax * by - bx * ay))
+    main = incircle <= 0.0  # v01 not inside the circle of the counter-clockwise (v00, v10, v11)
+    del p, d, ax, ay, bx, by, cx, cy, incircle
     nq = qy.shape[0]
     t = np.empty((nq, 2, 3), np.int64)
     t[:, 0] = np.where(main[:, None], np.stack([v00, v10, v11], -1), np.stack([v00, v10, v01], -1))

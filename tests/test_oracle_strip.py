@@ -185,3 +185,4 @@ def test_corrupt_streams_rejected():
     d3[0, 0] = 1000
     with pytest.raises(O.OracleError):
         O.decode(O.Blob(d3.view(np.uint8), payload, grids))
+
