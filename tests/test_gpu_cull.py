@@ -359,3 +359,36 @@ def test_cull_views_arguments():
         with pytest.raises(mc.CodecError) as e:
             mc.mc_decode_cull_views(db, vps, n, tri, stride, cnt, pos, st, scratch)
         assert e.value.status == 1
+
+
+def test_corrupt_stream_flagged_by_checked_cull_kernels():
+    """A meshlet whose increment flags claim one vertex more than V: every
+    checked cull form (one view, ordered, several views) reports
+    MC_ERR_CORRUPT, finishes and leaves the scratch reset."""
+    import torch
+    from tests import blobpack as bp
+    good = ([0, 1, 0, 1, 0], [0, 1, 2, 3, 4, 5, 6])
+    desc, payload, grids = bp.pack([good] * 3)
+    bad = payload.copy().view(np.uint32)
+    off1 = int(desc.view(np.uint32)[1, 0]) * 4
+    bad[off1 + 1] &= ~np.uint32(1 << 3)
+    T, V = 15, 21
+    db = mc.DeviceBatch.from_arrays(desc, bad.view(np.uint8), grids, T, V, 8)
+    vp = np.diag([1e-6, 1e-6, 1e-6, 1.0]).astype(np.float32).reshape(16)
+    d_vps = torch.from_numpy(np.ascontiguousarray(np.stack([vp, vp]))).cuda()
+    for form in ("one", "ordered", "views"):
+        tri = torch.zeros(2 * (3 * T + 3), dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(2, dtype=torch.int32, device="cuda")
+        pos = torch.zeros(3 * V, dtype=torch.float32, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        scratch = mc.new_scratch()
+        t = {"checked": 1}
+        if form == "one":
+            mc.mc_decode_cull(db, d_vps[0], tri, cnt, pos, st, scratch, t)
+        elif form == "ordered":
+            mc.mc_decode_cull_ordered(db, d_vps[0], tri, cnt, pos, st, scratch, None, t)
+        else:
+            mc.mc_decode_cull_views(db, d_vps, 2, tri, 3 * T + 3, cnt, pos, st, scratch, t)
+        torch.cuda.synchronize()
+        assert int(st.item()) & (1 << mc.MC_ERR_CORRUPT), form
+        assert int(scratch.abs().sum()) == 0, form
