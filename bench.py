@@ -200,40 +200,66 @@ def build_workload(cfg: int, rank: int, codec: str = "reuse", attrs: bool = Fals
     raise SystemExit(f"unknown config {cfg}")
 
 
-def cpu_oracle_baseline(blob, budget_s: float = 10.0, vp=None):
+class OracleSample:
     """The oracle's sequential C decode (or, given a view-projection matrix,
-    its fused decode + normal-cone/frustum/back-face cull for that view) in
-    one call over a prefix of the batch, sized from a short probe to take
-    about ``budget_s``, on one host core."""
-    import oracle as O
-    a = blob.arrays()
-    ob = O.Blob(a["desc"], a["payload"], a["grids"])
-    n = ob.n_meshlets
+    its fused decode + normal-cone/frustum/back-face cull for that view) over
+    the first `count` meshlets of the batch, into output arrays allocated
+    once (so a timed call pays for no allocation); `count` is sized from a
+    probe so that one call takes about budget_s."""
 
-    def run(count):
-        if vp is None:
-            return O.decode(ob, 0, count, want_pos64=False)
-        return O.decode_cull(ob, vp, 0, count, cones=a["cones"])
+    def __init__(self, blob, budget_s: float, vp=None):
+        import oracle as O
+        self.O, self.vp = O, vp
+        self.a = a = blob.arrays()
+        self.ob = ob = O.Blob(a["desc"], a["payload"], a["grids"])
+        self.n = n = ob.n_meshlets
+        T, V = ob.total_tris, ob.total_verts
+        self.loc, self.glob = np.zeros(3 * T, np.uint8), np.zeros(3 * T, np.uint32)
+        self.pos = np.zeros(3 * V, np.float32)
+        self.out = np.zeros(3 * T + 3, np.uint32) if vp is not None else None
+        self.run(min(n, 2000))
+        t0 = time.perf_counter()
+        self.run(min(n, 2000))
+        probe = time.perf_counter() - t0
+        self.count = int(min(n, max(2000, 2000 * budget_s / max(probe, 1e-6))))
+        # input (non-degenerate) triangles of the sample, counted outside any timing
+        O.decode_into(ob, 0, self.count, self.loc, self.glob, self.pos)
+        f = ob.fields()
+        end = int(f["tri_base"][self.count - 1]) + int(f["Tp"][self.count - 1])
+        t = self.loc[:3 * end].reshape(-1, 3).astype(np.int16)
+        self.tris = int(((t[:, 0] != t[:, 1]) & (t[:, 1] != t[:, 2]) & (t[:, 0] != t[:, 2])).sum())
+        self.run(self.count)  # first touch of the sample's output pages
 
-    t0 = time.perf_counter()
-    run(min(n, 2000))
-    probe = time.perf_counter() - t0
-    count = int(min(n, max(2000, 2000 * budget_s / max(probe, 1e-6))))
-    t0 = time.perf_counter()
-    run(count)
-    dt = time.perf_counter() - t0
-    # input (non-degenerate) triangles of the sample, counted outside the timing
-    loc = O.decode(ob, 0, count, want_pos64=False)[0]
-    f = ob.fields()
-    end = int(f["tri_base"][count - 1]) + int(f["Tp"][count - 1])
-    t = loc[:end].astype(np.int16)
-    tris = int(((t[:, 0] != t[:, 1]) & (t[:, 1] != t[:, 2]) & (t[:, 0] != t[:, 2])).sum())
-    what = "decode + FP32 dequant" if vp is None else \
-        "decode + frustum/normal-cone/back-face cull + compaction, one view"
-    res = {"value": tris / dt / 1e9, "unit": "Gtps", "cores": 1, "kind": "oracle",
-           "sample": f"first {count} of {n} meshlets ({tris} input triangles) of the same batch, "
-                     f"sequential C {what} in one call, {dt:.2f} s, 1 thread"}
-    res["all_cores"] = _oracle_all_cores(O, ob, a, vp, count, tris, min(budget_s, 5.0))
+    def run(self, count=None):
+        count = self.count if count is None else count
+        if self.vp is None:
+            self.O.decode_into(self.ob, 0, count, self.loc, self.glob, self.pos)
+        else:
+            self.O.decode_cull_into(self.ob, self.vp, 0, count, self.a["cones"], self.out, self.pos)
+
+    def timed(self) -> float:
+        """One call over the sample; seconds."""
+        t0 = time.perf_counter()
+        self.run()
+        return time.perf_counter() - t0
+
+    def describe(self, dt: float) -> str:
+        what = "decode + FP32 dequant" if self.vp is None else \
+            "decode + frustum/normal-cone/back-face cull + compaction, one view"
+        return (f"first {self.count} of {self.n} meshlets ({self.tris} input triangles) of the same "
+                f"batch, sequential C {what} in one call, {dt:.2f} s, 1 thread")
+
+
+def cpu_oracle_baseline(blob, budget_s: float = 10.0, vp=None, all_cores: bool = True):
+    """The oracle on one host core over a sample of about budget_s (and, with
+    all_cores, the same calls on every host core)."""
+    smp = OracleSample(blob, budget_s, vp)
+    dt = smp.timed()
+    res = {"value": smp.tris / dt / 1e9, "unit": "Gtps", "cores": 1, "kind": "oracle",
+           "sample": smp.describe(dt)}
+    if all_cores:
+        res["all_cores"] = _oracle_all_cores(smp.O, smp.ob, smp.a, vp, smp.count, smp.tris,
+                                             min(budget_s, 5.0))
     return res
 
 
@@ -281,17 +307,22 @@ def run_reference(args, ws, rank):
     blob, meshes, vps = build_workload(args.config, 0)
     vp = vps[0] if args.config == 4 else None
     per = []
+    # one oracle call per step over a fixed sample, sized so that the whole run
+    # takes about ref_seconds of oracle time (at least 2000 meshlets a call)
+    smp = OracleSample(blob, max(0.01, args.ref_seconds / (args.warmup + args.steps)), vp)
+    dts = []
     for i in range(args.warmup + args.steps):
-        r = cpu_oracle_baseline(blob, budget_s=max(1.0, args.ref_seconds / max(1, args.steps)), vp=vp)
+        dt = smp.timed()
         if i >= args.warmup:
-            per.append(r["value"])
+            per.append(smp.tris / dt / 1e9)
+            dts.append(dt)
     v = float(np.mean(per))
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gtps", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "u32/f32", "data": "synthetic",
            "config": {"workload": WORKLOADS[args.config]},
            "cpu_baseline": {"value": v, "unit": "Gtps", "cores": 1, "kind": "oracle",
-                            "sample": r["sample"]},
+                            "sample": smp.describe(float(np.mean(dts))) + " (mean per step)"},
            "e2e": {"value": v, "unit": "Gtps", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
