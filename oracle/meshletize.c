@@ -9,8 +9,11 @@
  *     meshlet, numbered in the order they join the frontier (edges of a newly
  *     added triangle visited as (v0,v1), (v1,v2), (v2,v0); the triangles on
  *     one edge in increasing id);
- *   - pick: the earliest-joined frontier triangle that adds no new vertex,
- *     else the earliest-joined one (a frontier triangle adds at most one);
+ *   - pick: the frontier triangle that adds the fewest new vertices (0 or 1:
+ *     a frontier triangle adds at most one); among those, the one with the
+ *     most edges already shared with an assigned triangle of its class (any
+ *     meshlet: this takes triangles that would otherwise be left stranded
+ *     between full meshlets first); among those, the earliest-joined;
  *   - stop when the pick would exceed V~ vertices or T~ triangles.
  * A meshlet whose strip (restart degenerates included) is longer than T~ is
  * split into the first ceil(T/2) triangles of its strip order and the rest,
@@ -47,6 +50,25 @@ static int vertex_triangles(uint32_t nv, const uint32_t *tri, uint32_t nt,
 static int has_vertex(const uint32_t *tri, uint32_t t, uint32_t v) {
   return tri[3 * (size_t)t] == v || tri[3 * (size_t)t + 1] == v ||
          tri[3 * (size_t)t + 2] == v;
+}
+
+/* Edges of triangle t that an assigned triangle of the same class shares. */
+static uint32_t assigned_edges(const uint32_t *tri, const uint8_t *tri_class, uint32_t t,
+                               const uint32_t *vt_off, const uint32_t *vt,
+                               const uint8_t *assigned) {
+  uint32_t n = 0, cls = tri_class ? tri_class[t] : 0;
+  for (int e = 0; e < 3; e++) {
+    uint32_t u = tri[3 * (size_t)t + e], w = tri[3 * (size_t)t + (e + 1) % 3];
+    for (uint32_t k = vt_off[u]; k < vt_off[u + 1]; k++) {
+      uint32_t t3 = vt[k];
+      if (t3 != t && assigned[t3] && (tri_class ? tri_class[t3] : 0) == cls &&
+          has_vertex(tri, t3, w)) {
+        n++;
+        break;
+      }
+    }
+  }
+  return n;
 }
 
 /* Split driver: appends the final meshlets for the triangle list ids[0..T). */
@@ -140,16 +162,20 @@ int orc_meshletize(uint32_t n_verts, const uint32_t *tris, uint32_t n_tris,
           front[nf++] = t2;
         }
       }
-      /* pick: earliest cost-0 frontier triangle, else earliest one */
+      /* pick: fewest new vertices, then most assigned edges, then earliest */
       int64_t best = -1;
-      uint32_t best_cost = 0;
+      uint32_t best_cost = 0, best_nb = 0;
       for (uint32_t i = 0; i < nf; i++) {
         uint32_t t2 = front[i];
         if (assigned[t2]) continue;
         uint32_t cost = 0;
         for (int j = 0; j < 3; j++) cost += vstamp[tris[3 * (size_t)t2 + j]] != stamp;
-        if (cost == 0) { best = t2; best_cost = 0; break; }
-        if (best < 0) { best = t2; best_cost = cost; }
+        uint32_t nb = assigned_edges(tris, tri_class, t2, vt_off, vt, assigned);
+        if (best < 0 || cost < best_cost || (cost == best_cost && nb > best_nb)) {
+          best = t2;
+          best_cost = cost;
+          best_nb = nb;
+        }
       }
       if (best < 0) break;
       if (nT + 1 > max_t || nV + best_cost > max_v) break;

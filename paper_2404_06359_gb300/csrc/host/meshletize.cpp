@@ -6,12 +6,16 @@
 //   * frontier: unassigned triangles sharing an edge with the meshlet, each
 //     numbered when it first joins (edges of an added triangle in the order
 //     (v0,v1), (v1,v2), (v2,v0), the triangles on an edge by increasing id);
-//   * pick: the lowest-numbered frontier triangle adding no vertex, else the
-//     lowest-numbered one (a frontier triangle adds at most one vertex);
+//   * pick: the frontier triangle adding the fewest vertices (0 or 1: a
+//     frontier triangle adds at most one); among those, the one with the most
+//     edges shared with an assigned triangle of its class (any meshlet, so a
+//     triangle about to be enclosed by full meshlets goes first instead of
+//     being left behind as a one-triangle meshlet); among those, the
+//     lowest-numbered;
 //   * stop when the pick would exceed V~ or T~.
-// The frontier is kept as a min-heap of triangles that add no vertex and a
-// FIFO of the others; a triangle moves to the heap when its last missing
-// vertex joins.  Classes never share triangles, so each class grows on its
+// The frontier is a min-heap keyed by (vertices added, 3 - shared edges,
+// number); both only fall while a meshlet grows, so a changed triangle is
+// pushed again and outdated entries are skipped when they surface.  Classes never share triangles, so each class grows on its
 // own thread and the meshlets are merged back in seed order.  A grown meshlet
 // whose strip (restart degenerates included) exceeds T~ is split into the
 // first ceil(T/2) triangles of its strip order and the rest, recursively.
@@ -86,7 +90,7 @@ struct Grower {
   // the thread of its own class only)
   uint8_t *assigned;
   uint32_t *fstamp;   // frontier membership (meshlet stamp)
-  uint32_t *pstamp;   // "in the no-new-vertex heap" (meshlet stamp)
+  uint8_t *shared;    // edges shared with assigned same-class triangles (frontier only)
   uint32_t *seqof;    // frontier number
   // per-thread
   std::vector<uint32_t> vstamp;
@@ -104,11 +108,30 @@ struct Grower {
     return (vstamp[p[0]] != stamp) + (vstamp[p[1]] != stamp) + (vstamp[p[2]] != stamp);
   }
 
+  // edges of t that an assigned triangle of the current class shares
+  uint32_t shared_edges(uint32_t t) const {
+    const uint32_t *p = tri + 3 * (size_t)t;
+    uint32_t n = 0;
+    for (int e = 0; e < 3; e++) {
+      const uint32_t u = p[e], w = p[(e + 1) % 3];
+      for (uint32_t k = adj->off[u]; k < adj->off[u + 1]; k++) {
+        const uint32_t t3 = adj->lst[k];
+        if (t3 != t && same_class(t3) && assigned[t3] && has(t3, w)) {
+          n++;
+          break;
+        }
+      }
+    }
+    return n;
+  }
+
   void grow_class(uint32_t c, uint32_t n_tris, uint32_t max_v, uint32_t max_t,
                   uint32_t stamp_base, std::vector<Grown> &out) {
-    using Item = std::pair<uint32_t, uint32_t>;  // (seq, triangle)
-    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap0;
-    std::vector<uint32_t> fifo;
+    using Item = std::pair<uint64_t, uint32_t>;  // (key, triangle)
+    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+    auto key = [&](uint32_t t2) {
+      return ((uint64_t)cost(t2) << 40) | ((uint64_t)(3 - shared[t2]) << 32) | seqof[t2];
+    };
     stamp = stamp_base;
     cur_cls = c;
     uint32_t scan = 0;
@@ -119,9 +142,7 @@ struct Grower {
       Grown g;
       g.seed = scan;
       g.cls = c;
-      while (!heap0.empty()) heap0.pop();
-      fifo.clear();
-      size_t head = 0;
+      while (!heap.empty()) heap.pop();
       uint32_t seq = 0, nV = 0;
       uint32_t t = scan;
       for (;;) {
@@ -133,46 +154,41 @@ struct Grower {
           if (vstamp[v] == stamp) continue;
           vstamp[v] = stamp;
           nV++;
-          // frontier triangles whose last missing vertex is v move to heap0
+          // frontier triangles on v now add one vertex fewer
           for (uint32_t k = adj->off[v]; k < adj->off[v + 1]; k++) {
             uint32_t t2 = adj->lst[k];
-            if (!same_class(t2)) continue;
-            if (fstamp[t2] == stamp && !assigned[t2] && pstamp[t2] != stamp && cost(t2) == 0) {
-              pstamp[t2] = stamp;
-              heap0.push({seqof[t2], t2});
-            }
+            if (same_class(t2) && fstamp[t2] == stamp && !assigned[t2]) heap.push({key(t2), t2});
           }
         }
         for (int e = 0; e < 3; e++) {
           uint32_t u = p[e], w = p[(e + 1) % 3];
           for (uint32_t k = adj->off[u]; k < adj->off[u + 1]; k++) {
             uint32_t t2 = adj->lst[k];
-            if (t2 == t || !same_class(t2) || assigned[t2] || fstamp[t2] == stamp) continue;
-            if (!has(t2, w)) continue;
-            fstamp[t2] = stamp;
-            seqof[t2] = seq++;
-            if (cost(t2) == 0) {
-              pstamp[t2] = stamp;
-              heap0.push({seqof[t2], t2});
-            } else {
-              fifo.push_back(t2);
+            if (t2 == t || !same_class(t2) || assigned[t2] || !has(t2, w)) continue;
+            if (fstamp[t2] != stamp) {  // joins the frontier
+              fstamp[t2] = stamp;
+              seqof[t2] = seq++;
+              shared[t2] = (uint8_t)shared_edges(t2);
+              heap.push({key(t2), t2});
+            } else {  // t now shares this edge
+              const uint8_t n = (uint8_t)shared_edges(t2);
+              if (n != shared[t2]) {
+                shared[t2] = n;
+                heap.push({key(t2), t2});
+              }
             }
           }
         }
-        // pick
-        while (!heap0.empty() && assigned[heap0.top().second]) heap0.pop();
-        uint32_t pick, pcost;
-        if (!heap0.empty()) {
-          pick = heap0.top().second;
-          pcost = 0;
-        } else {
-          while (head < fifo.size() && (assigned[fifo[head]] || pstamp[fifo[head]] == stamp)) head++;
-          if (head == fifo.size()) break;
-          pick = fifo[head];
-          pcost = cost(pick);
+        // pick: the smallest current key (entries whose key has since fallen are stale)
+        while (!heap.empty()) {
+          const uint32_t t2 = heap.top().second;
+          if (!assigned[t2] && heap.top().first == key(t2)) break;
+          heap.pop();
         }
-        if (g.tris.size() + 1 > max_t || nV + pcost > max_v) break;
-        if (pcost == 0) heap0.pop(); else head++;
+        if (heap.empty()) break;
+        const uint32_t pick = heap.top().second;
+        if (g.tris.size() + 1 > max_t || nV + cost(pick) > max_v) break;
+        heap.pop();
         t = pick;
       }
       out.push_back(std::move(g));
@@ -239,7 +255,8 @@ extern "C" mc_status mc_meshletize(const uint32_t *tri_idx, uint32_t n_tris, uin
     Adjacency adj;
     build_adjacency(tri_idx, n_tris, n_verts, threads, adj);
     std::vector<uint8_t> assigned(n_tris, 0);
-    std::vector<uint32_t> fstamp(n_tris, 0), pstamp(n_tris, 0), seqof(n_tris, 0);
+    std::vector<uint32_t> fstamp(n_tris, 0), seqof(n_tris, 0);
+    std::vector<uint8_t> shared(n_tris, 0);
     // which classes occur
     std::vector<uint8_t> present(n_classes, 0);
     if (tri_class) {
@@ -258,7 +275,7 @@ extern "C" mc_status mc_meshletize(const uint32_t *tri_idx, uint32_t n_tris, uin
       g.adj = &adj;
       g.assigned = assigned.data();
       g.fstamp = fstamp.data();
-      g.pstamp = pstamp.data();
+      g.shared = shared.data();
       g.seqof = seqof.data();
       g.vstamp.assign(n_verts, 0);
       uint32_t c = cls_list[i];
