@@ -57,7 +57,9 @@ def _peaks():
 # profiles/decode_cull_views_cfg4.md for cfg4: one 8-view decode_cull_views
 # launch, captured on the 20 M-triangle reduction of the batch), per decoded
 # triangle slot and keyed by the kernel-source hash it was taken on; reported
-# only while the sources match.
+# only while the sources match.  Both captures predate the meshletizer's
+# shared-edge pick (same meshes, 7 % more meshlets), so the figure is scaled
+# by decoded triangle slots from that partition of the same meshes.
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal, for the second fraction beside the measured peak
 
 NCU_TRAFFIC = {  # config -> (device-code hash, DRAM bytes per decoded triangle slot)
