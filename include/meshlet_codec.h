@@ -374,7 +374,10 @@ mc_status mc_decode_batch_noalloc(const mc_device_batch *b, uint8_t *d_local, ui
                                   float *d_pos, uint32_t *d_status, const mc_tuning *t,
                                   void *stream);
 
-/* Fused decode + cull + compaction in one persistent launch.
+/* Fused decode + cull + compaction in one persistent launch: the decode of
+ * mc_decode_batch (Sec. 4.2-4.4) with per-meshlet culling (Sec. 3: meshlets
+ * are culled whole, by their bounds and normal cone, before their triangles)
+ * and a per-triangle back-face test.
  *   d_view_proj  16 FP32, row-major clip matrix: clip = M [x y z 1]^T
  *   d_tri_out    u32 [3 * total_tris]: surviving triangles as global index
  *                triples, compacted in unspecified order
@@ -402,7 +405,8 @@ mc_status mc_decode_cull(const mc_device_batch *b, const float *d_view_proj,
                          uint32_t *d_status, void *d_scratch, const mc_tuning *t,
                          void *stream);
 
-/* The fused cull against several views in one persistent launch: each
+/* The fused cull (as mc_decode_cull, Sec. 3 and 4.2-4.4) against several
+ * views in one persistent launch: each
  * meshlet is staged, dequantised and strip-walked once, then tested, culled
  * and compacted once per view whose meshlet tests it passes.
  *   d_view_projs  n_views x 16 FP32 row-major clip matrices, 1 <= n_views <= 8
@@ -421,7 +425,8 @@ mc_status mc_decode_cull_views(const mc_device_batch *b, const float *d_view_pro
                                uint32_t *d_tri_counts, float *d_pos, uint32_t *d_status,
                                void *d_scratch, const mc_tuning *t, void *stream);
 
-/* The fused cull with the survivors in a fixed order: meshlet order, then
+/* The fused cull (as mc_decode_cull, Sec. 3 and 4.2-4.4) with the survivors
+ * in a fixed order: meshlet order, then
  * triangle order within a meshlet -- the order of a sequential decode and
  * cull.  Same arguments and results as mc_decode_cull otherwise, plus
  *   d_order  device buffer of mc_cull_order_bytes(b) bytes, 8-byte aligned,
