@@ -85,7 +85,9 @@ typedef struct {
   uint8_t reuse_bits;     /* w, 1..8, 2^w >= V; 0 = plain GTS block */
   uint8_t pos_bits;       /* b, 1..32 */
   uint16_t grid;          /* index of the mc_grid entry */
-  uint32_t L[3];          /* meshlet minimum on the global grid (Sec. 4.4) */
+  uint32_t L[3];          /* meshlet minimum on the global grid (Sec. 4.4);
+                           * L[c] + 2^b - 1 < 2^32 (the whole quantisation box
+                           * is representable), else the meshlet is corrupt */
 } mc_desc;
 
 /* Global quantisation grid (Sec. 4.4): x = G + g * Delta for grid coordinate
@@ -280,6 +282,13 @@ typedef struct {
                                * do not fit warps_per_cta warps on an SM is
                                * reduced until they do */
   uint32_t checked;
+  uint32_t wait_cycles;       /* limit, in SM clock cycles, of each wait of a
+                               * warp on another warp's result (the look-back
+                               * of mc_decode_cull_ordered); 0 = 2^31 (about a
+                               * second).  A wait that runs out sets
+                               * MC_ERR_TIMEOUT in the status word.  The waits
+                               * of a warp for its own bulk copies keep their
+                               * fixed bound of 2^31 cycles. */
 } mc_tuning;
 
 /* Bytes of device scratch the persistent kernels need (work-queue counters).
@@ -369,7 +378,11 @@ mc_status mc_decode_requests(const mc_device_batch *pool, const mc_request *d_re
  *     the GPU (e.g. on two streams) race and give wrong results; serialise
  *     them.
  *   - MC_ERR_LIMIT if the batch has more than 2^31 meshlets (the 32-bit
- *     counters need headroom) or the device ordinal is 64 or more. */
+ *     counters need headroom) or the device ordinal is 64 or more.
+ *   - The looked-up address is kept for the life of the process: after a
+ *     cudaDeviceReset (or anything else that unloads the library's device
+ *     code on that device) it is stale, and this call must not be used on
+ *     that device again. */
 mc_status mc_decode_batch_noalloc(const mc_device_batch *b, uint8_t *d_local, uint32_t *d_global,
                                   float *d_pos, uint32_t *d_status, const mc_tuning *t,
                                   void *stream);

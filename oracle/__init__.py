@@ -316,17 +316,19 @@ def decode_into(blob: Blob, first: int, count: int, loc: np.ndarray, glob: np.nd
 
 
 def decode_cull_into(blob: Blob, vp: np.ndarray, first: int, count: int, cones, out: np.ndarray,
-                     pos: np.ndarray) -> int:
+                     pos: np.ndarray, passed: np.ndarray | None = None) -> int:
     """orc_decode_cull of meshlets [first, first + count): survivors from
     out[0] (uint32, room for 3 T' of the range), positions into the
-    whole-batch pos (float32 [3 V_total]); returns the survivor count.  Like
-    decode_into, callable from several threads on disjoint ranges."""
+    whole-batch pos (float32 [3 V_total]), and, when given, passed[m] (uint8
+    [M]) = 1 for each meshlet of the range that passes the meshlet tests;
+    returns the survivor count.  Like decode_into, callable from several
+    threads on disjoint ranges."""
     cnt = C.c_uint64(0)
     vp = np.ascontiguousarray(np.asarray(vp, np.float32).reshape(16))
     cn = None if cones is None else np.ascontiguousarray(np.asarray(cones, np.uint8).reshape(-1, 32))
     _check(lib().orc_decode_cull(_p(blob.desc), blob.n_meshlets, _p(blob.payload),
                                  blob.payload.size, _p(blob.grids), blob.n_grids, first, count,
-                                 _p(vp), _p(cn), _p(out), C.byref(cnt), _p(pos), None),
+                                 _p(vp), _p(cn), _p(out), C.byref(cnt), _p(pos), _p(passed)),
            "orc_decode_cull")
     return int(cnt.value)
 

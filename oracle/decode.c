@@ -88,6 +88,11 @@ int orc_decode_meshlet(const uint8_t *desc32, const uint8_t *payload,
   if (d.V < 3 || d.V > 256 || d.tp < 1 || d.tp > 256 || d.w > 8 || d.b < 1 ||
       d.b > 32 || d.grid >= n_grids || d.V > d.tp + 2)
     return ORC_ERR_CORRUPT;
+  /* the meshlet's quantisation box [L, L + 2^b - 1] must be representable as
+   * 32-bit grid coordinates (Sec. 4.4: the decoder adds q to L as integers);
+   * the encoder never writes a minimum closer than 2^b - 1 to 2^32 */
+  for (int ch = 0; ch < 3; ch++)
+    if ((uint64_t)d.L[ch] + ((1ull << d.b) - 1) > 0xFFFFFFFFull) return ORC_ERR_CORRUPT;
   const int gts = d.w == 0; /* plain GTS: one stored 8-bit entry per triangle */
   uint32_t R = d.tp + 2 - d.V;
   uint64_t nw = (d.tp + 31) / 32;
@@ -197,6 +202,9 @@ int orc_decode_attrs(const uint8_t *desc, const uint8_t *adesc, uint32_t n_meshl
     if (ag >= n_agrids) return ORC_ERR_CORRUPT;
     const uint8_t *g = agrids + 48 * (size_t)ag;
     if (get_u32(g + 40) != attr_bits) return ORC_ERR_CORRUPT;
+    for (uint32_t c = 0; c < n_attr; c++) /* the attribute box fits 32 bits, as for positions */
+      if ((uint64_t)get_u32(ar + 4 * c) + ((1ull << attr_bits) - 1) > 0xFFFFFFFFull)
+        return ORC_ERR_CORRUPT;
     uint64_t nw = (d.tp + 31) / 32;
     uint64_t cw = d.w == 0 ? nw + ((uint64_t)d.tp - 1 + 3) / 4
                            : 2 * nw + ((uint64_t)(d.tp + 2 - d.V) * d.w + 31) / 32;

@@ -81,6 +81,7 @@ BatchArgs args_of(const mc_device_batch *b) {
   a.attr_desc = b->attr_desc;
   a.attr_grids = b->attr_grids;
   a.n_attr_grids = b->n_attr_grids;
+  a.wait_cycles = 0;
   return a;
 }
 
@@ -256,7 +257,8 @@ mc_status launch_cull_checked(const mc_device_batch *b, const float *d_vp, uint3
   uint32_t per_grab = (t && t->meshlets_per_grab) ? t->meshlets_per_grab : 4;
   if (warps < 1 || warps > 32 || per_grab < 1 || per_grab > 16) return MC_ERR_INVALID_ARG;
   if (d_order) per_grab = std::min<uint32_t>(per_grab, kOrderedGrabMax);
-  const BatchArgs a = args_of(b);
+  BatchArgs a = args_of(b);
+  a.wait_cycles = t ? t->wait_cycles : 0;
   // a grab's survivors are buffered in shared memory: shrink the grab until
   // the requested number of warps fits on an SM
   uint32_t grab = per_grab;

@@ -32,7 +32,7 @@ __device__ __forceinline__ uint32_t grab_outside(const BatchArgs &a, uint32_t m0
       const uint32_t b = (w[4] >> 8) & 0xFFu, grid = w[4] >> 16;
       if (grid < a.n_grids) {
         const Grid g = load_grid(a.grids + grid);
-        const uint32_t ext = b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u);
+        const uint32_t ext = field_max(b);
         float p3[3];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -200,12 +200,14 @@ __device__ __forceinline__ void grab_publish(uint64_t *state, uint32_t g, uint32
   if (lane == 0) st_relaxed_u64(state + g, (g == 0 ? kInc : kAgg) | count);
 }
 // The exclusive prefix of grab g (published as an aggregate before), or
-// 0xFFFFFFFF when a wait gave up.
+// 0xFFFFFFFF when a wait on an unpublished predecessor gave up after
+// wait_cycles clock cycles (0 = kWaitCycles).
 __device__ __forceinline__ uint32_t grab_lookback(uint64_t *state, uint32_t g, uint32_t count,
-                                                  uint32_t lane) {
+                                                  uint32_t lane, uint32_t wait_cycles) {
   if (g == 0) return 0;
   uint32_t excl = 0;
   int64_t j = (int64_t)g - 1;
+  const long long limit = wait_cycles ? (long long)wait_cycles : kWaitCycles;
   const long long t0 = clock64();
   for (;;) {
     const int64_t idx = j - (int64_t)lane;
@@ -216,7 +218,7 @@ __device__ __forceinline__ uint32_t grab_lookback(uint64_t *state, uint32_t g, u
     const uint32_t stop = inc_mask ? (uint32_t)__ffs(inc_mask) - 1u : 31u;  // lanes 0..stop count
     const uint32_t upto = stop == 31u ? kFull : ((2u << stop) - 1u);
     if (wait_mask & upto) {
-      if (__any_sync(kFull, clock64() - t0 > kWaitCycles)) return 0xFFFFFFFFu;
+      if (__any_sync(kFull, clock64() - t0 > limit)) return 0xFFFFFFFFu;
       continue;
     }
     excl += __reduce_add_sync(kFull, lane <= stop ? (uint32_t)v : 0u);
@@ -278,7 +280,7 @@ __global__ void __launch_bounds__(MAX_THREADS) decode_cull_kernel(BatchArgs a, c
   __syncthreads();
   const bool eye_ok = s_eye[3] != 0.0f;
   auto resolve = [&](uint32_t m0, uint32_t n, uint32_t h) {
-    const uint32_t excl = grab_lookback(order_state, m0 / per_grab, n, lane);
+    const uint32_t excl = grab_lookback(order_state, m0 / per_grab, n, lane, a.wait_cycles);
     if (excl == 0xFFFFFFFFu) {
       if (lane == 0) set_status(status, MC_ERR_TIMEOUT);
       return;

@@ -34,7 +34,7 @@ __device__ __forceinline__ uint32_t grab_outside_views(const BatchArgs &a, uint3
     const uint32_t b = (w[4] >> 8) & 0xFFu, grid = w[4] >> 16;
     if (grid < a.n_grids) {
       const Grid g = load_grid(a.grids + grid);
-      const uint32_t ext = b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u);
+      const uint32_t ext = field_max(b);
 #pragma unroll
       for (int c = 0; c < 3; c++) {
         const uint32_t L = w[5 + c];

@@ -107,6 +107,7 @@ struct BatchArgs {
   const mc_attr_desc *attr_desc;
   const mc_attr_grid *attr_grids;
   uint32_t n_attr_grids;
+  uint32_t wait_cycles;  // limit of a wait on another warp (look-back), 0 = the default
 };
 
 // The attribute words of a meshlet follow its position words.
@@ -115,15 +116,24 @@ __device__ __forceinline__ Desc with_attrs(Desc d, const BatchArgs &a) {
   return d;
 }
 
+// Largest b-bit field value, 2^b - 1 (b <= 32).
+__device__ __forceinline__ uint32_t field_max(uint32_t b) {
+  return b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u);
+}
+
 // Header sanity (all builds): a descriptor that passes cannot make the decode
-// read or write outside its buffers.
+// read or write outside its buffers, and its whole quantisation box
+// [L, L + 2^b - 1] is representable as 32-bit grid coordinates (the encoder's
+// rule), so no g = L + q and no box corner wraps around.
 __device__ __forceinline__ bool header_ok(const Desc &d, const BatchArgs &a) {
   // evaluated without short-circuit branches (all terms are cheap)
   const bool shape = (d.V - 3u <= 253u) & (d.T - 1u <= 255u) & (d.V <= d.T + 2) &
                      (d.w <= 8u) & (d.b - 1u <= 31u) & (d.grid < a.n_grids) &
                      (d.T <= a.max_tris);
+  const uint32_t top = ~field_max(d.b);  // largest L with L + 2^b - 1 < 2^32
+  const bool box = (d.L[0] <= top) & (d.L[1] <= top) & (d.L[2] <= top);
   const uint32_t padded = (block_words(d) + 3) & ~3u;
-  return shape & (padded <= a.max_block_words) &
+  return shape & box & (padded <= a.max_block_words) &
          (16ull * d.off16 + 4ull * padded <= a.payload_bytes) &
          ((uint64_t)d.tbase + d.T <= a.total_tris) & ((uint64_t)d.vbase + d.V <= a.total_verts);
 }

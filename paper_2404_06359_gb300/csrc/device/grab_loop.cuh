@@ -11,7 +11,9 @@
 //
 // Every mbarrier wait is bounded (about a second): a wait that gives up sets
 // MC_ERR_TIMEOUT in the status word and ends the warp's work; the copy it
-// waited for is the only one the warp has in flight.
+// waited for is the only one the warp has in flight, and the warp waits for
+// it once more (again bounded) before it leaves, so that the copy is unlikely
+// to land in shared memory its CTA no longer owns.
 #pragma once
 
 #include "decode_warp.cuh"
@@ -122,6 +124,7 @@ __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab,
     }
     if (!mbar_wait(bar, parity)) {
       if (lane == 0) set_status(status, MC_ERR_TIMEOUT);
+      mbar_wait(bar, parity);  // a second bounded wait for the copy in flight
       return;
     }
     parity ^= 1u;
@@ -135,6 +138,7 @@ __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab,
       }
       if (!mbar_wait(bar, parity)) {
         if (lane == 0) set_status(status, MC_ERR_TIMEOUT);
+        mbar_wait(bar, parity);  // a second bounded wait for the copy in flight
         return;
       }
       parity ^= 1u;

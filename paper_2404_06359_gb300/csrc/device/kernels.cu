@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(512) decode_batch_kernel(BatchArgs a, uint32_t
                     const mc_attr_grid *ag = a.attr_grids + gi;
                     ok = __ldg(&ag->attr_bits) == a.attr_bits;
                     sa[lane] = __ldg(&ad->La[lane]);
+                    ok = ok & (sa[lane] <= ~field_max(a.attr_bits));  // La + 2^b - 1 fits 32 bits
                     sa[5 + lane] = __float_as_uint(__ldg(&ag->G[lane]));
                     sa[10 + lane] = __float_as_uint(__ldg(&ag->delta[lane]));
                   }

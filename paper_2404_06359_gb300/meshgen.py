@@ -393,6 +393,17 @@ def camera_poses(n: int, center, radius: float, seed: int = SEED_BASE + 4,
     return out
 
 
+def scene_views(meshes, n_views: int, seed: int) -> np.ndarray:
+    """n_views camera poses around a batch of meshes: the eye on a sphere of
+    1.5 times the radius of the batch's bounding box around its centre
+    (camera_poses)."""
+    lo = np.min([m.pos.min(0) for m in meshes], 0).astype(np.float64)
+    hi = np.max([m.pos.max(0) for m in meshes], 0).astype(np.float64)
+    center = 0.5 * (lo + hi)
+    radius = float(np.linalg.norm(hi - lo) / 2)
+    return camera_poses(n_views, center, radius, seed)
+
+
 def poisson_arrivals(rate: float, duration: float, n_choices: int, seed: int):
     """Arrival times (s) of a Poisson process of ``rate`` per second over
     ``duration`` seconds, and a uniformly drawn mesh index per arrival."""

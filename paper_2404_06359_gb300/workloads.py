@@ -74,12 +74,7 @@ def cfg3(rank: int = 0, total_tris: int = 50_000_000, plain_gts: bool = False):
 def cfg4(rank: int = 0, min_tris: int = 50_000_000, n_views: int = 64):
     meshes = G.surface_batch(256, 10_000, 200_000, SEEDS[2] + 1000 * rank, min_total_tris=min_tris)
     blob = encode_meshes(meshes)
-    lo = np.min([m.pos.min(0) for m in meshes], 0).astype(np.float64)
-    hi = np.max([m.pos.max(0) for m in meshes], 0).astype(np.float64)
-    center = 0.5 * (lo + hi)
-    radius = float(np.linalg.norm(hi - lo) / 2)
-    vps = G.camera_poses(n_views, center, radius, SEEDS[4] + rank)
-    return blob, meshes, vps
+    return blob, meshes, G.scene_views(meshes, n_views, SEEDS[4] + rank)
 
 
 def _block_words(T, V, w, b):

@@ -112,7 +112,8 @@ def test_long_fans_reuse_widths_and_bits():
         for wmode in (8, "log2"):
             desc, payload, grids = bp.pack(cases, reuse_w=wmode, pos_bits=b,
                                            q_fn=lambda v, c, b=b: int(rng.integers(0, min(2 ** b, 2 ** 31))),
-                                           L=(7, 2 ** 20, 3), grid=(-1.5, 2.0, 0.25, 1e-3, 3e-5, 0.5))
+                                           L=tuple(min(x, 2 ** 32 - 2 ** b) for x in (7, 2 ** 20, 3)),
+                                           grid=(-1.5, 2.0, 0.25, 1e-3, 3e-5, 0.5))
             blob = O.Blob(desc, payload, grids)
             ref = O.decode(blob)
             db = mc.DeviceBatch.from_arrays(desc, payload, grids, blob.total_tris, blob.total_verts,

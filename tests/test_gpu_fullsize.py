@@ -1,12 +1,14 @@
 """Full-size parity at the benchmark workloads, in the launch configuration
 bench.py times (autotuned shape, CUDA-graph replay).
 
-At these sizes the oracle decodes sampled meshlets one by one (2,000 random
-meshlets plus the first and last), compared bit for bit; properties that hold
-at any size are checked on every decoded triangle and vertex.  The inputs
-come from the library's host encoder, which the CPU suite proves
-byte-identical to the oracle's encoder; here that is re-checked on sampled
-whole meshes of cfg2.
+Every decoded array is compared whole, element by element, with the oracle's
+sequential decode of the whole batch (indices exact, positions 0 ulp); the
+fused cull of the 8-view kernel is compared view by view (survivors as a
+multiset, their order across warps being unspecified) with the oracle's
+decode + cull of each view.  Properties that hold at any size are checked on
+every decoded triangle and vertex as well.  The inputs come from the
+library's host encoder, which the CPU suite proves byte-identical to the
+oracle's encoder; here that is re-checked on whole meshes of cfg2.
 """
 import numpy as np
 import pytest
@@ -36,24 +38,18 @@ def _decode_graph(db):
     return ({k: out[k].cpu().numpy() for k in ("local", "global", "pos")}, tune)
 
 
-def _check_sampled(blob, res, n_samples=2000, seed=0):
+def _check_whole(blob, res):
+    """The whole decoded batch against the oracle's decode of the whole batch."""
     a = blob.arrays()
     ob = O.Blob(a["desc"], a["payload"], a["grids"])
-    f = ob.fields()
-    n = ob.n_meshlets
-    rng = np.random.Generator(np.random.PCG64(seed))
-    sample = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, n_samples)]))
-    loc = res["local"].reshape(-1, 3)
-    glob = res["global"].view(np.uint32).reshape(-1, 3)
-    pos = res["pos"].view(np.uint32).reshape(-1, 3)
-    for m in sample:
-        tb, vb = int(f["tri_base"][m]), int(f["vertex_base"][m])
-        T, V = int(f["Tp"][m]), int(f["V"][m])
-        rl, rp, _ = O.decode_meshlet(ob, int(m))
-        assert np.array_equal(loc[tb:tb + T], rl), f"meshlet {m}: local"
-        assert np.array_equal(glob[tb:tb + T], rl.astype(np.uint32) + vb), f"meshlet {m}: global"
-        assert np.array_equal(pos[vb:vb + V], rp.view(np.uint32)), f"meshlet {m}: positions"
-    return len(sample)
+    loc, glob, pos, _ = O.decode(ob, want_pos64=False)
+    got_l = res["local"].reshape(-1, 3)
+    bad = np.nonzero((got_l != loc).any(1))[0]
+    assert bad.size == 0, f"{bad.size} local triangles differ, first {bad[:5]}"
+    assert np.array_equal(res["global"].view(np.uint32).reshape(-1, 3), glob)
+    same = res["pos"].view(np.uint32).reshape(-1, 3) == pos.view(np.uint32)
+    assert same.all(), f"{(~same).sum()} position components differ"
+    return ob.n_meshlets
 
 
 def _check_properties(blob, res):
@@ -95,7 +91,7 @@ def test_cfg2_fullsize():
     blob, meshes = W.cfg2()
     db = mc.DeviceBatch(blob)
     res, tune = _decode_graph(db)
-    n = _check_sampled(blob, res)
+    n = _check_whole(blob, res)
     _check_properties(blob, res)
     # the per-mesh plain decoder agrees with the batched one everywhere
     import torch
@@ -123,7 +119,7 @@ def test_cfg2_fullsize():
         assert np.array_equal(a["payload"][p0:p0 + ob.payload.size], ob.payload)
         g = a["grids"][int(w[mi["first_meshlet"], 4] >> 16)].view(np.float32)
         assert np.array_equal(g[[0, 1, 2, 4, 5, 6]], ob.grids[0].view(np.float32)[[0, 1, 2, 4, 5, 6]])
-    print(f"cfg2: {blob.stats()['n_meshlets']} meshlets, {n} sampled, tuning "
+    print(f"cfg2: {n} meshlets compared whole, tuning "
           f"{tune.warps_per_cta}x{tune.ctas_per_sm}/{tune.meshlets_per_grab}")
 
 
@@ -131,11 +127,11 @@ def test_cfg3_fullsize():
     blob, _ = W.cfg3()
     db = mc.DeviceBatch(blob)
     res, tune = _decode_graph(db)
-    n = _check_sampled(blob, res, 2000, seed=3)
+    n = _check_whole(blob, res)
     _check_properties(blob, res)
     s = blob.stats()
     assert s["input_tris"] >= 49_000_000
-    print(f"cfg3: {s['n_meshlets']} meshlets ({s['split_meshlets']} from splits), {n} sampled")
+    print(f"cfg3: {n} meshlets ({s['split_meshlets']} from splits) compared whole")
 
 
 @pytest.fixture(scope="module")
@@ -202,3 +198,47 @@ def test_cfg4_fullsize_cull_ordered(cfg4_data):
     ref, _, _ = O.decode_cull(ob, vps[7], cones=a["cones"])
     got = tri[: 3 * int(cnt.item())].cpu().numpy().view(np.uint32).reshape(-1, 3)
     assert np.array_equal(got, ref)
+
+
+def test_cfg4_fullsize_cull_views(cfg4_data):
+    """The multi-view fused cull as the benchmark runs it: 64 views in one
+    graph of 8 launches of 8 views each.  The last launch's views (56..63)
+    stay in the 8 output regions; each is compared with the oracle's decode +
+    cull of that view (survivors as a multiset, count exact), and the
+    positions of every meshlet that passes the meshlet tests of one of those
+    views (0 ulp)."""
+    import torch
+    blob, meshes, vps = cfg4_data
+    s = blob.stats()
+    db = mc.DeviceBatch(blob, cones=True)
+    T, V = s["total_tris"], s["total_verts"]
+    stride = 3 * T + 3
+    tri = torch.empty(8 * stride, dtype=torch.int32, device="cuda")
+    counts = torch.zeros(len(vps), dtype=torch.int32, device="cuda")
+    pos = torch.full((3 * V,), float("nan"), dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    scratch = mc.new_scratch()
+    d_vps = torch.from_numpy(np.ascontiguousarray(vps, np.float32)).cuda()
+    g = mc.mc_graph_capture_cull_views(db, d_vps, len(vps), tri, stride, counts, pos, st, scratch)
+    g.launch()
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and int(scratch.abs().sum()) == 0
+    c = counts.cpu().numpy().astype(np.int64)
+    a = blob.arrays()
+    ob = O.Blob(a["desc"], a["payload"], a["grids"])
+    f = ob.fields()
+    t_all = tri.cpu().numpy().view(np.uint32)
+    p_all = pos.cpu().numpy().view(np.uint32).reshape(-1, 3)
+    union = np.zeros(ob.n_meshlets, bool)
+    ref_pos = None
+    for v in range(len(vps) - 8, len(vps)):
+        ref, rp, passed = O.decode_cull(ob, vps[v], cones=a["cones"])
+        assert int(c[v]) == ref.shape[0], v
+        r = v % 8
+        got = t_all[r * stride: r * stride + 3 * int(c[v])].reshape(-1, 3)
+        assert np.array_equal(got[np.lexsort(got.T[::-1])], ref[np.lexsort(ref.T[::-1])]), v
+        union |= passed.astype(bool)
+        vm = np.repeat(passed, f["V"].astype(np.int64)).astype(bool)
+        assert np.array_equal(p_all[vm], rp[vm].view(np.uint32)), v
+    print(f"cfg4 8-view launch: views 56..63, {int(c[-8:].sum())} survivors compared, "
+          f"{union.mean():.3f} of the meshlets pass one of them")

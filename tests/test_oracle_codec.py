@@ -352,3 +352,38 @@ def test_cull_matches_fp64_geometry_and_halves_closed_surfaces():
         assert not vin[passed[vm] == 0].any()
         frac = out.shape[0] / (~deg[inside]).sum() if inside.any() else 0.5
         assert 0.35 < frac < 0.65, frac
+
+
+def test_quantisation_box_must_fit_32_bits(encoded):
+    """Sec. 4.4 decodes g = L + q as a 32-bit integer add.  The format rule is
+    that the whole quantisation box [L, L + 2^b - 1] is representable: the
+    encoder never writes a minimum closer than 2^b - 1 to 2^32, a minimum at
+    exactly 2^32 - 2^b decodes (its top vertex at g = 2^32 - 1), and one more
+    is rejected as corrupt by the decoder and by the decode + cull."""
+    from tests import blobpack as bp
+    f = encoded[3].fields()
+    top = f["L"].astype(np.int64) + (2 ** f["b"].astype(np.int64) - 1)[:, None]
+    assert (top < 2 ** 32).all()
+    case = ([0, 1, 0], [0, 1, 2, 3, 4])
+    grid = (-2.0, 1.0, 0.5, 2.0 ** -20, 3e-7, 1e-5)
+    for b in (1, 12, 16, 27, 32):
+        lim = 2 ** 32 - 2 ** b
+        qmax = 2 ** b - 1
+        desc, payload, grids = bp.pack([case], pos_bits=b, q_fn=lambda v, c: qmax if v == 0 else v,
+                                       L=(lim, lim, lim), grid=grid)
+        blob = O.Blob(desc, payload, grids)
+        _, p32, p64 = O.decode_meshlet(blob, 0)
+        G0 = np.asarray(grid[:3], np.float32)
+        D = np.asarray(grid[3:], np.float32)
+        for c in range(3):
+            assert p32[0, c] == np.float32(O.dequant32(2 ** 32 - 1, float(G0[c]), float(D[c])))
+            assert p64[0, c] == float(G0[c]) + (2 ** 32 - 1) * float(D[c])
+        for c in range(3):
+            L = [lim, lim, lim]
+            L[c] += 1
+            d2, _, _ = bp.pack([case], pos_bits=b, q_fn=lambda v, c: 0, L=tuple(L), grid=grid)
+            bad = O.Blob(d2, payload, grids)
+            with pytest.raises(O.OracleError):
+                O.decode(bad)
+            with pytest.raises(O.OracleError):
+                O.decode_cull(bad, np.eye(4, dtype=np.float32).reshape(16))

@@ -5,9 +5,10 @@ device memory of its own -- hosts that own every allocation, or render loops
 where a cudaMalloc would synchronise the device mid-frame.  It keeps its
 work-queue counters in a small static device array instead of a caller
 buffer.  This test decodes the same batch through both entry points of the C
-ABI, twice in a row, and requires identical outputs (bit for bit, the
-tolerance of every decode test here).  It lives in its own file, collected
-last, and builds everything it needs itself, so it also runs alone.
+ABI, twice in a row, and requires outputs identical to each other and to the
+CPU oracle's decode of the same blob (bit for bit: indices exact, positions
+0 ulp, the tolerance of every decode test here).  It lives in its own file,
+collected last, and builds everything it needs itself, so it also runs alone.
 """
 import numpy as np
 import pytest
@@ -30,19 +31,23 @@ def _batch():
     rw, b = (w[:, 4] & 0xFF).astype(np.int64), ((w[:, 4] >> 8) & 0xFF).astype(np.int64)
     words = 2 * ((T + 31) // 32) + ((T + 2 - V) * rw + 31) // 32 + (3 * V * b + 31) // 32
     mbw = int(((words + 3) // 4 * 4).max())
-    return mc.DeviceBatch.from_arrays(blob.desc, blob.payload, blob.grids, blob.total_tris,
-                                      blob.total_verts, mbw)
+    return blob, mc.DeviceBatch.from_arrays(blob.desc, blob.payload, blob.grids, blob.total_tris,
+                                            blob.total_verts, mbw)
 
 
 def test_noalloc_matches_regular_entry_point_twice():
     import torch
-    db = _batch()
+    blob, db = _batch()
+    loc, glob, pos, _ = O.decode(blob, want_pos64=False)
     ref = db.outputs()
     scratch = mc.new_scratch()
     mc.mc_decode_batch(db, ref["local"], ref["global"], ref["pos"], ref["status"], scratch)
     torch.cuda.synchronize()
     assert int(ref["status"].item()) == 0
     want = {k: ref[k].cpu().numpy() for k in ("local", "global", "pos")}
+    assert np.array_equal(want["local"].reshape(-1, 3), loc)
+    assert np.array_equal(want["global"].view(np.uint32).reshape(-1, 3), glob)
+    assert np.array_equal(want["pos"].view(np.uint32).reshape(-1, 3), pos.view(np.uint32))
     out = db.outputs()
     for call in range(2):
         out["local"].fill_(0xAA)
