@@ -404,6 +404,12 @@ def _timed_steps(step, stream, flush, warmup, steps, ws, local, clocks=True):
     return times, launches, clk.summary() if clk else None
 
 
+def _parse_tuning(mc, text: str):
+    """--tuning warps,ctas_per_sm,meshlets_per_grab[,lanes_per_meshlet]."""
+    v = [int(x) for x in text.split(",")]
+    return mc.mc_tuning(v[0], v[1], v[2], 0, 0, v[3] if len(v) > 3 else 32)
+
+
 def _roofline(bytes_per_launch, per_launch_s, traffic, extra=None):
     peak, peak_kind = _peaks()
     ach = bytes_per_launch / per_launch_s / 1e9
@@ -441,15 +447,15 @@ def measure_decode(args, cfg, blob, ws, local, stream, flush, main=True):
             graph, tune = None, {"warps_per_cta": 4}
         else:
             if args.tuning:
-                w_, c_, g_ = (int(x) for x in args.tuning.split(","))
-                tune = mc.mc_tuning(w_, c_, g_, 0)
+                tune = _parse_tuning(mc, args.tuning)
             else:
                 tune, _ = mc.mc_autotune(db, out["local"], out["global"], out["pos"], out["status"],
                                          scratch, stream)
             graph = None if attrs else mc.mc_graph_capture_batch(
                 db, out["local"], out["global"], out["pos"], out["status"], scratch, tune, stream)
             rec["tuning"] = {"warps_per_cta": tune.warps_per_cta, "ctas_per_sm": tune.ctas_per_sm,
-                             "meshlets_per_grab": tune.meshlets_per_grab}
+                             "meshlets_per_grab": tune.meshlets_per_grab,
+                             "lanes_per_meshlet": tune.lanes_per_meshlet or 32}
 
         def step():
             if graph is not None:
@@ -578,8 +584,7 @@ def measure_cull(args, blob, vps, ws, local, stream, flush):
         counts = torch.zeros(len(vps), dtype=torch.int32, device="cuda")
         tune = None
         if args.tuning:
-            w_, c_, g_ = (int(x) for x in args.tuning.split(","))
-            tune = mc.mc_tuning(w_, c_, g_, 0)
+            tune = _parse_tuning(mc, args.tuning)
 
         def capture_cull(batch):
             if cv == 1:
@@ -826,7 +831,8 @@ def main():
                     help="config 4 without the one-view, no-cone and ordered variants")
     ap.add_argument("--plain-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=10)
-    ap.add_argument("--tuning", default="", help="warps,ctas_per_sm,meshlets_per_grab (skips the autotuner)")
+    ap.add_argument("--tuning", default="",
+                    help="warps,ctas_per_sm,meshlets_per_grab[,lanes_per_meshlet] (skips the autotuner)")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--pool-meshes", type=int, default=512)

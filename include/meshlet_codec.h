@@ -289,6 +289,12 @@ typedef struct {
                                * MC_ERR_TIMEOUT in the status word.  The waits
                                * of a warp for its own bulk copies keep their
                                * fixed bound of 2^31 cycles. */
+  uint32_t lanes_per_meshlet; /* sub-warp width of mc_decode_batch and its
+                               * graph / host-buffer forms: 32 = one meshlet
+                               * per warp, 16 = two meshlets per warp (one
+                               * per half; grabs of at least 2 meshlets);
+                               * 0 = the autotuned value, else 32.  Other
+                               * calls use 32. */
 } mc_tuning;
 
 /* Bytes of device scratch the persistent kernels need (work-queue counters).
@@ -460,7 +466,9 @@ mc_status mc_decode_cull_ordered(const mc_device_batch *b, const float *d_view_p
 /* ------------------------------------------------------------------ runtime */
 
 /* Time candidate launch shapes of mc_decode_batch on this batch (the outputs
- * are overwritten) and remember the fastest for batches with the same
+ * are overwritten) -- warps per CTA {4, 8, 16} x meshlets per grab {1, 2, 4,
+ * 8, 16} x CTAs per SM {the occupancy limit, half of it} x lanes per meshlet
+ * {32, 16} -- and remember the fastest for batches with the same
  * signature (meshlet count, payload size, largest block) on this device.
  * Each shape runs four times, each run after the positions have been
  * rewritten (which evicts the input from L2 when it is larger than L2, as

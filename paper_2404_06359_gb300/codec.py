@@ -61,7 +61,7 @@ class mc_request(C.Structure):
 
 class mc_tuning(C.Structure):
     _fields_ = [("warps_per_cta", u32), ("ctas_per_sm", u32), ("meshlets_per_grab", u32),
-                ("checked", u32), ("wait_cycles", u32)]
+                ("checked", u32), ("wait_cycles", u32), ("lanes_per_meshlet", u32)]
 
 
 STATUS = {0: "MC_OK", 1: "MC_ERR_INVALID_ARG", 2: "MC_ERR_LIMIT", 3: "MC_ERR_CORRUPT",

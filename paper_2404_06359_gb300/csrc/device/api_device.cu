@@ -103,8 +103,12 @@ mc_tuning resolve_batch(const mc_device_batch *b, const mc_tuning *t) {
   if (!r.warps_per_cta) r.warps_per_cta = 8;
   if (!r.meshlets_per_grab) r.meshlets_per_grab = 2;
   if (r.meshlets_per_grab > 16) r.meshlets_per_grab = 16;
+  if (r.lanes_per_meshlet != 16) r.lanes_per_meshlet = 32;
+  if (r.lanes_per_meshlet == 16 && r.meshlets_per_grab < 2) r.meshlets_per_grab = 2;
   if (!r.ctas_per_sm) {
-    int occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, r.meshlets_per_grab);
+    int occ = r.lanes_per_meshlet == 16
+                  ? max_ctas_per_sm_batch_pairs(r.warps_per_cta, b->max_block_words, r.meshlets_per_grab)
+                  : max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, r.meshlets_per_grab);
     r.ctas_per_sm = occ > 0 ? (uint32_t)occ : 1;
   }
   return r;
@@ -116,19 +120,29 @@ mc_status launch_batch_checked(const mc_device_batch *b, uint8_t *d_local, uint3
   if (r.warps_per_cta < 1 || r.warps_per_cta > 32 || r.meshlets_per_grab < 1 ||
       r.meshlets_per_grab > 16)
     return MC_ERR_INVALID_ARG;
-  // a grab's two pipeline buffers live in shared memory: shrink the grab
-  // until the requested number of warps fits on an SM
-  uint32_t grab = r.meshlets_per_grab;
-  int occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, grab, vertices);
-  while (occ <= 0 && grab > 1)
-    occ = max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, --grab, vertices);
+  // two meshlets per warp: the decoder of positions only, grabs of >= 2
+  const bool pairs = r.lanes_per_meshlet == 16 && !vertices;
+  auto occ_of = [&](uint32_t g) {
+    return pairs ? max_ctas_per_sm_batch_pairs(r.warps_per_cta, b->max_block_words, g)
+                 : max_ctas_per_sm_batch(r.warps_per_cta, b->max_block_words, g, vertices);
+  };
+  // a grab's buffers live in shared memory: shrink the grab until the
+  // requested number of warps fits on an SM
+  const uint32_t min_grab = pairs ? 2u : 1u;
+  uint32_t grab = std::max(r.meshlets_per_grab, min_grab);
+  int occ = occ_of(grab);
+  while (occ <= 0 && grab > min_grab) occ = occ_of(--grab);
   if (occ <= 0) return MC_ERR_INVALID_ARG;
   uint32_t per_sm = std::min<uint32_t>(r.ctas_per_sm, (uint32_t)occ);
   uint32_t ctas = per_sm * (uint32_t)sm_count();
   if (ctas == 0) return MC_ERR_CUDA;
-  cudaError_t e = launch_batch(args_of(b), ctas, r.warps_per_cta, grab, b->max_block_words,
-                               r.checked != 0, vertices, d_local, d_global, d_pos, d_status,
-                               static_cast<uint32_t *>(d_scratch), s);
+  cudaError_t e =
+      pairs ? launch_batch_pairs(args_of(b), ctas, r.warps_per_cta, grab, b->max_block_words,
+                                 r.checked != 0, d_local, d_global, d_pos, d_status,
+                                 static_cast<uint32_t *>(d_scratch), s)
+            : launch_batch(args_of(b), ctas, r.warps_per_cta, grab, b->max_block_words,
+                           r.checked != 0, vertices, d_local, d_global, d_pos, d_status,
+                           static_cast<uint32_t *>(d_scratch), s);
   if (e == cudaSuccess) g_launches++;
   return from_cuda(e);
 }
@@ -409,15 +423,20 @@ extern "C" mc_status mc_autotune(const mc_device_batch *b, uint8_t *d_local, uin
   float bms = 1e30f;
   const uint32_t warps_c[] = {4, 8, 16};
   const uint32_t grab_c[] = {1, 2, 4, 8, 16};
+  const uint32_t lanes_c[] = {32, 16};
   st = MC_OK;
+  for (uint32_t lanes : lanes_c)
   for (uint32_t w : warps_c) {
     for (uint32_t g : grab_c) {
-      int occ = max_ctas_per_sm_batch(w, b->max_block_words, g);
+      if (lanes == 16 && g < 2) continue;
+      int occ = lanes == 16 ? max_ctas_per_sm_batch_pairs(w, b->max_block_words, g)
+                            : max_ctas_per_sm_batch(w, b->max_block_words, g);
       if (occ <= 0) continue;
       for (uint32_t frac = 0; frac < 2; frac++) {
         mc_tuning c{};
         c.warps_per_cta = w;
         c.meshlets_per_grab = g;
+        c.lanes_per_meshlet = lanes;
         c.ctas_per_sm = frac == 0 ? (uint32_t)occ : std::max(1u, (uint32_t)occ / 2);
         if (frac == 1 && c.ctas_per_sm == (uint32_t)occ) continue;
         float ms_min = 1e30f;

@@ -470,6 +470,135 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
   return true;
 }
 
+// Two meshlets per warp: half h = lane / 16 decodes its own staged meshlet
+// (d, sw; live = false for a half without one) with lanes hl = lane % 16
+// owning triangles k = hl, hl + 16, ... and vertices v = hl, hl + 16, ...
+// The arithmetic is decode_staged's, on 16-triangle halves of the 32-bit
+// flag words: s_k from the add-scan of the increment bits up to k, the
+// third vertex from the highest flag transition at or below k (or the
+// carried last transition), orientation by the flag.  Shuffles stay within a
+// half (width 16); both halves run max(passes) iterations, a half past its
+// own triangles idle (its loads stay inside the staged block and its slack).
+// sI points at this half's strip-stream buffer.  Returns false when this
+// half's meshlet is corrupt (CHECKED only).
+template <bool CHECKED, bool B16, int RM>
+__device__ __forceinline__ bool decode_pair(const Desc &d, bool live_half, const Grid &g,
+                                            const uint32_t *sw, uint8_t *sI, uint32_t lane,
+                                            uint8_t *out_local, uint32_t *out_global,
+                                            float *out_pos) {
+  bool ok = live_half;
+  if (CHECKED && ok) ok = stream_header_ok(d, sw);
+  const uint32_t hl = lane & 15u;
+  const uint32_t T = ok ? d.T : 0u, V = ok ? d.V : 0u;
+  const uint32_t np = (T + 15) >> 4, vp = (V + 15) >> 4;
+  const uint32_t npass = max(np, __shfl_xor_sync(kFull, np, 16));
+  const uint32_t nvpass = max(vp, __shfl_xor_sync(kFull, vp, 16));
+  const uint32_t nw = (d.T + 31) >> 5;
+  const uint32_t a_sw = smem_addr(sw);
+  const uint32_t a_rb = a_sw + 8 * nw;
+  const uint32_t a_eb = a_sw + 4 * nw;
+  const uint32_t a_sI = smem_addr(sI);
+  if (hl < 2) sts_u8(a_sI + hl, hl);
+  const uint32_t le = (2u << hl) - 1u;
+  uint8_t *pl = out_local ? out_local + 3ull * (d.tbase + hl) : nullptr;
+  uint32_t *pg = out_global ? out_global + 3ull * (d.tbase + hl) : nullptr;
+  const bool want_l = pl != nullptr, want_g = pg != nullptr;
+  const uint32_t vb = d.vbase;
+  uint32_t base = 1, carry = 1, cf = 1, lastT = 0;
+  bool bad = false;
+  uint32_t k = hl;
+  for (uint32_t p = 0; p < npass; p++, k += 16) {
+    const uint32_t wa = a_sw + 4 * (p >> 1), sh = (p & 1u) << 4;
+    const uint32_t f = (lds_u32(wa) >> sh) & 0xFFFFu;
+    uint32_t n;
+    if (RM == kPlainGts) {
+      const uint32_t e = lds_u8(a_eb + (k ? k - 1 : 0u));
+      n = k ? e : 2u;
+    } else {
+      const uint32_t inc = ((lds_u32(wa + 4 * nw) >> sh) & 0xFFFFu) | (p == 0 ? 1u : 0u);
+      const uint32_t s = base + __popc(inc & le);
+      const bool is_new = (inc >> hl) & 1u;
+      const uint32_t slot = is_new ? 0u : k + 1 - s;
+      const uint32_t r = RM == kReuseBytes ? lds_u8(a_rb + slot) : extract(sw + 2 * nw, slot * d.w, d.w);
+      n = is_new ? s : r;
+      if (CHECKED && k < T && !is_new && r > s) bad = true;
+      base += __popc(inc);
+    }
+    const bool live = k < T;
+    sts_u8_if(a_sI + k + 2, n, live);
+    uint32_t prev = __shfl_up_sync(kFull, n, 1, 16);
+    if (hl == 0) prev = carry;
+    carry = __shfl_sync(kFull, n, 15, 16);
+    const uint32_t D = (f ^ ((f << 1) | cf)) & 0xFFFFu;  // flag transitions of this half word
+    cf = f >> 15;
+    __syncwarp();
+    const uint32_t m = msb(D & le);
+    const uint32_t run = m == 0xFFFFFFFFu ? lastT : 16 * p + m;
+    const uint32_t old = lds_u8(a_sI + run);
+    const bool fk = (f >> hl) & 1u;
+    const uint32_t ta = fk ? prev : old, tb = fk ? old : prev;
+    stg3_u8_if(pl, ta, tb, n, live && want_l);
+    stg3_u32_if(pg, vb + ta, vb + tb, vb + n, live && want_g);
+    pl += 48;
+    pg += 48;
+    if (D) lastT = 16 * p + msb(D);
+  }
+  if (CHECKED) ok = ok && !bad;
+  const uint32_t *pw = sw + conn_words(d);
+  float *op = out_pos + 3ull * (d.vbase + hl);
+  if (B16 && small_coords(d)) {
+    uint32_t a = smem_addr(pw) + 6 * hl;
+    uint32_t v = hl;
+    for (uint32_t i = 0; i < nvpass; i++, v += 16, a += 96, op += 48) {
+      const bool lv = v < V;
+      const uint32_t aa = lv ? a : smem_addr(pw);
+      const float x = dequant_small(d.L[0] + lds_u16(aa), g.G[0], g.D[0]);
+      const float y = dequant_small(d.L[1] + lds_u16(aa + 2), g.G[1], g.D[1]);
+      const float z = dequant_small(d.L[2] + lds_u16(aa + 4), g.G[2], g.D[2]);
+      stg3_f32_if(op, x, y, z, lv);
+    }
+  } else {
+    uint32_t v = hl;
+    for (uint32_t i = 0; i < nvpass; i++, v += 16, op += 48) {
+      uint32_t q[3];
+      vertex_q<B16>(pw, v < V ? v : 0u, d.b, q);  // idle lanes re-read vertex 0
+      stg3_f32_if(op, dequant(d.L[0] + q[0], g.G[0], g.D[0]), dequant(d.L[1] + q[1], g.G[1], g.D[1]),
+                  dequant(d.L[2] + q[2], g.G[2], g.D[2]), v < V);
+    }
+  }
+  __syncwarp();
+  return ok || !live_half;
+}
+
+// Pair dispatch: both halves take the connectivity / position path of their
+// meshlets when these agree; otherwise the generic one (funnel-shift reads
+// serve every width), or, when one half holds plain GTS and the other
+// GTS-Reuse, each path in turn with the other half idle.  Returns this
+// half's status as decode_pair.
+template <bool CHECKED>
+__device__ __forceinline__ bool decode_pair_dispatch(const Desc &d, bool live_half, const Grid &g,
+                                                     const uint32_t *sw, uint8_t *sI, uint32_t lane,
+                                                     uint8_t *out_local, uint32_t *out_global,
+                                                     float *out_pos) {
+  // 0 idle, 1 plain GTS, 2 byte reuse entries + 16-bit positions, 3 any other
+  const uint32_t mode = !live_half ? 0u : d.w == 0 ? 1u : (d.b == 16 && d.w == 8) ? 2u : 3u;
+  const uint32_t other = __shfl_xor_sync(kFull, mode, 16);
+#define MC_PAIR(B, R, LIVE) \
+  decode_pair<CHECKED, B, R>(d, LIVE, g, sw, sI, lane, out_local, out_global, out_pos)
+  if (mode == other || mode == 0 || other == 0) {
+    const uint32_t m = mode | other;  // the one live mode (or both alike)
+    if (m == 2) return MC_PAIR(true, kReuseBytes, live_half);
+    if (m == 1) return MC_PAIR(false, kPlainGts, live_half);
+    return MC_PAIR(false, kReuseBits, live_half);
+  }
+  if (mode != 1 && other != 1) return MC_PAIR(false, kReuseBits, live_half);
+  // plain GTS beside GTS-Reuse: one round each, the other half idle
+  const bool a = MC_PAIR(false, kPlainGts, live_half && mode == 1);
+  const bool b = MC_PAIR(false, kReuseBits, live_half && mode != 1);
+  return mode == 1 ? a : b;
+#undef MC_PAIR
+}
+
 // out_pos: positions (3 FP32 per vertex) or, VTX, full vertices (8 FP32 per
 // vertex, sa / n_attr / attr_bits as for vertex_stage_full).
 template <bool CHECKED, bool VTX = false>

@@ -169,4 +169,101 @@ __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab,
   }
 }
 
+// The work loop with two meshlets per warp (per_grab >= 2): grabs are taken
+// and staged as in grab_loop (the same steps, written out here so that each
+// loop keeps its own registers), and the meshlets of a grab are handed out
+// in pairs, meshlet j + h to the half h = lane / 16: body(d, live, sw, m) is
+// called by all lanes with this half's descriptor, whether it holds a
+// meshlet that passed header_ok (live), its staged block sw and its batch
+// index m.  Blocks outside the grab's staged range are staged pair by pair
+// into the first two slots of the payload buffer.
+template <class Body>
+__device__ __forceinline__ void grab_loop_pairs(const BatchArgs &a, uint32_t per_grab,
+                                                uint8_t *wbase, uint32_t lane, uint32_t *queue,
+                                                uint32_t *status, Body &&body) {
+  const uint32_t *sdesc = reinterpret_cast<const uint32_t *>(wbase);
+  const uint32_t bar = smem_addr(wbase + 32 * (per_grab + 1));
+  uint32_t *spay = reinterpret_cast<uint32_t *>(wbase + 32 * (per_grab + 1) + 16);
+  const uint32_t slot_words = (a.max_block_words + 3) & ~3u;
+  const uint32_t cap16 = (per_grab * slot_words) / 4;
+  const uint32_t bytes16 =
+      a.payload_bytes / 16 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)(a.payload_bytes / 16);
+  const uint32_t N = a.n_meshlets;
+  const uint32_t h = lane >> 4, hl = lane & 15u;
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  uint32_t parity = 0;
+  for (;;) {
+    uint32_t m0 = 0;
+    if (lane == 0) m0 = atomicAdd(queue, per_grab);
+    m0 = __shfl_sync(kFull, m0, 0);
+    if (m0 >= N) break;
+    const uint32_t cnt = min(per_grab, N - m0);
+    const uint32_t nd = cnt + (m0 + cnt < N ? 1u : 0u);
+    fence_proxy_async();  // the previous grab's shared-memory accesses before the async writes
+    __syncwarp();
+    if (lane == 0) {
+      mbar_expect_tx(bar, 32 * nd);
+      bulk_g2s(smem_addr(wbase), a.desc + m0, 32 * nd, bar);
+    }
+    if (!mbar_wait(bar, parity)) {
+      if (lane == 0) set_status(status, MC_ERR_TIMEOUT);
+      mbar_wait(bar, parity);  // a second bounded wait for the copy in flight
+      return;
+    }
+    parity ^= 1u;
+    const uint32_t start16 = sdesc[0];
+    const uint32_t end16 = m0 + cnt < N ? sdesc[8 * cnt] : bytes16;
+    bool staged = end16 >= start16 && end16 - start16 <= cap16 && end16 <= bytes16;
+    if (staged && end16 > start16) {
+      if (lane == 0) {
+        mbar_expect_tx(bar, 16 * (end16 - start16));
+        bulk_g2s(smem_addr(spay), a.payload + 16ull * start16, 16 * (end16 - start16), bar);
+      }
+      if (!mbar_wait(bar, parity)) {
+        if (lane == 0) set_status(status, MC_ERR_TIMEOUT);
+        mbar_wait(bar, parity);  // a second bounded wait for the copy in flight
+        return;
+      }
+      parity ^= 1u;
+    }
+    for (uint32_t j = 0; j < cnt; j += 2) {
+      const uint32_t jj = j + h;
+      Desc d{};
+      bool live = jj < cnt;
+      if (live) {
+        const uint4 *sd = reinterpret_cast<const uint4 *>(sdesc) + 2 * jj;
+        d = with_attrs(unpack_desc(sd[0], sd[1]), a);
+        live = header_ok(d, a);
+        if (!live && hl == 0) set_status(status, MC_ERR_CORRUPT);
+        if (!live) d = Desc{};  // an idle half decodes nothing
+      }
+      const uint32_t *sw = spay;
+      bool in_range = true;
+      if (live) {
+        const uint32_t padded16 = ((block_words(d) + 3) & ~3u) / 4;
+        in_range = staged && d.off16 >= start16 && d.off16 - start16 + padded16 <= end16 - start16;
+        if (in_range) sw = spay + 4 * (d.off16 - start16);
+      }
+      if (__any_sync(kFull, !in_range)) {  // this pair's blocks, each into its own slot
+        staged = false;  // spay is reused pair by pair from here on
+        __syncwarp();
+        uint32_t *dst = spay + h * slot_words;
+        if (live) {
+          const uint4 *src = reinterpret_cast<const uint4 *>(a.payload) + d.off16;
+          const uint32_t n4 = (block_words(d) + 3) >> 2;
+          for (uint32_t i = hl; i < n4; i += 16) reinterpret_cast<uint4 *>(dst)[i] = __ldg(src + i);
+        }
+        __syncwarp();
+        sw = dst;
+      }
+      body(d, live, sw, m0 + jj);
+    }
+    __syncwarp();
+  }
+}
+
 }  // namespace mcdev

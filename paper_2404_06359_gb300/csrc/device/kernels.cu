@@ -112,6 +112,45 @@ __global__ void __launch_bounds__(512) decode_batch_kernel(BatchArgs a, uint32_t
   }
 }
 
+// Persistent batched decode with two meshlets per warp (16 lanes each):
+// the grab loop hands the meshlets of each grab out in pairs and both halves
+// decode at once (decode_pair), so the per-meshlet set-up (descriptor,
+// header check, grid, output pointers) is paid once per pair.  Per warp:
+// the grab loop's buffers, then one strip-stream buffer per half.
+uint32_t batch_pairs_smem_per_warp(uint32_t max_block_words, uint32_t per_grab) {
+  return grab_loop_bytes(max_block_words, per_grab) + 2 * kStreamBytes;
+}
+
+template <bool CHECKED>
+__global__ void __launch_bounds__(512) decode_batch_pairs_kernel(BatchArgs a, uint32_t per_grab,
+                                                                 uint32_t smem_per_warp,
+                                                                 uint8_t *out_local,
+                                                                 uint32_t *out_global,
+                                                                 float *out_pos, uint32_t *status,
+                                                                 uint32_t *scratch) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  uint8_t *base = smem + warp * smem_per_warp;
+  uint8_t *sI = base + smem_per_warp - (2 - (lane >> 4)) * kStreamBytes;  // this half's stream
+  grab_loop_pairs(a, per_grab, base, lane, scratch + kQueue, status,
+                  [&](const Desc &d, bool live, const uint32_t *sw, uint32_t) {
+                    const Grid g = load_grid(a.grids + d.grid);
+                    if (!decode_pair_dispatch<CHECKED>(d, live, g, sw, sI, lane, out_local,
+                                                       out_global, out_pos) &&
+                        (lane & 15u) == 0)
+                      set_status(status, MC_ERR_CORRUPT);
+                  });
+  // the last CTA to finish leaves the queue reset for the next launch
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(scratch + kDone, 1u) == gridDim.x - 1) {
+      atomicExch(scratch + kQueue, 0u);
+      atomicExch(scratch + kDone, 0u);
+    }
+  }
+}
+
 // Continuous-batching decode: persistent warps take `per_grab` work items
 // (meshlets of the concatenated request ranges); each item is mapped to its
 // request by binary search over work_start, its descriptor is renumbered
@@ -278,6 +317,29 @@ cudaError_t launch_batch_t(const BatchArgs &a, uint32_t ctas, uint32_t warps, ui
   return cudaGetLastError();
 }
 }  // namespace
+
+cudaError_t launch_batch_pairs(const BatchArgs &a, uint32_t ctas, uint32_t warps, uint32_t per_grab,
+                               uint32_t max_block_words, bool checked, uint8_t *out_local,
+                               uint32_t *out_global, float *out_pos, uint32_t *status,
+                               uint32_t *scratch, cudaStream_t s) {
+  const uint32_t spw = batch_pairs_smem_per_warp(max_block_words, per_grab);
+  if (checked) {
+    prepare(fn(decode_batch_pairs_kernel<true>));
+    decode_batch_pairs_kernel<true><<<ctas, warps * 32, spw * warps, s>>>(
+        a, per_grab, spw, out_local, out_global, out_pos, status, scratch);
+  } else {
+    prepare(fn(decode_batch_pairs_kernel<false>));
+    decode_batch_pairs_kernel<false><<<ctas, warps * 32, spw * warps, s>>>(
+        a, per_grab, spw, out_local, out_global, out_pos, status, scratch);
+  }
+  return cudaGetLastError();
+}
+
+int max_ctas_per_sm_batch_pairs(uint32_t warps, uint32_t max_block_words, uint32_t per_grab) {
+  const int smem = (int)(batch_pairs_smem_per_warp(max_block_words, per_grab) * warps);
+  prepare(fn(decode_batch_pairs_kernel<true>));
+  return occupancy(fn(decode_batch_pairs_kernel<false>), warps * 32, smem);
+}
 
 cudaError_t launch_batch(const BatchArgs &a, uint32_t ctas, uint32_t warps, uint32_t per_grab,
                          uint32_t max_block_words, bool checked, bool vertices,

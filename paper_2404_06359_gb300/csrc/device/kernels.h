@@ -41,6 +41,12 @@ cudaError_t launch_cull(const BatchArgs &a, const float *view_proj, const mc_con
 
 int max_ctas_per_sm_batch(uint32_t warps, uint32_t max_block_words, uint32_t per_grab,
                           bool vertices = false);
+// Two meshlets per warp, 16 lanes each (per_grab >= 2).
+cudaError_t launch_batch_pairs(const BatchArgs &a, uint32_t ctas, uint32_t warps, uint32_t per_grab,
+                               uint32_t max_block_words, bool checked, uint8_t *out_local,
+                               uint32_t *out_global, float *out_pos, uint32_t *status,
+                               uint32_t *scratch, cudaStream_t s);
+int max_ctas_per_sm_batch_pairs(uint32_t warps, uint32_t max_block_words, uint32_t per_grab);
 // Multi-view fused cull (1 <= n_views <= 8, per_grab <= 4): view v's
 // survivors go to tri_out + v * tri_stride, its count to tri_counts[v].
 uint32_t cull_views_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, uint32_t per_grab,

@@ -52,10 +52,16 @@ def test_plain_grid_8192(grid_blob):
         assert_same_decode(run_decode(db, "plain", {"warps_per_cta": warps}), ref, f"plain w{warps}")
 
 
+PAIR_TUNINGS = [{"lanes_per_meshlet": 16, "warps_per_cta": 4, "meshlets_per_grab": 4},
+                {"lanes_per_meshlet": 16, "warps_per_cta": 8, "meshlets_per_grab": 3},
+                {"lanes_per_meshlet": 16, "warps_per_cta": 16, "meshlets_per_grab": 16},
+                {"lanes_per_meshlet": 16, "warps_per_cta": 4, "meshlets_per_grab": 2, "checked": 1}]
+
+
 @pytest.mark.parametrize("tuning", [None, {"warps_per_cta": 4, "meshlets_per_grab": 1},
                                     {"warps_per_cta": 16, "meshlets_per_grab": 8},
                                     {"warps_per_cta": 8, "meshlets_per_grab": 3, "ctas_per_sm": 1},
-                                    {"warps_per_cta": 8, "checked": 1}])
+                                    {"warps_per_cta": 8, "checked": 1}] + PAIR_TUNINGS)
 def test_batch_mixed_vs_oracle(mixed_batch, tuning):
     ref = O.decode(mixed_batch)
     db = device_batch_from_oracle(mixed_batch)
@@ -91,6 +97,23 @@ def test_bruteforce_corpus(tp):
     db = mc.DeviceBatch.from_arrays(desc, payload, grids, blob.total_tris, blob.total_verts, 8)
     assert_same_decode(run_decode(db, "batch"), ref, f"bruteforce T'={tp}")
     assert_same_decode(run_decode(db, "batch", {"checked": 1}), ref, f"bruteforce checked T'={tp}")
+    for t in (PAIR_TUNINGS[0], PAIR_TUNINGS[-1]):  # two meshlets per warp
+        assert_same_decode(run_decode(db, "batch", t), ref, f"bruteforce T'={tp} {t}")
+
+
+@pytest.mark.parametrize("tuning", [None, {"meshlets_per_grab": 4}] + PAIR_TUNINGS[:2])
+def test_batch_descriptors_out_of_order(mixed_batch, tuning):
+    """Descriptors in another order than their payload blocks (the format
+    only needs each descriptor to point at its block): no grab's blocks form
+    one range, so every block is staged on its own (meshlet by meshlet, or
+    pair by pair with two meshlets per warp); the outputs follow the
+    descriptors' bases and equal the oracle's decode of the same blob."""
+    rng = np.random.Generator(np.random.PCG64(46))
+    perm = rng.permutation(mixed_batch.n_meshlets)
+    blob = O.Blob(mixed_batch.desc[perm].copy(), mixed_batch.payload, mixed_batch.grids)
+    ref = O.decode(blob)
+    db = device_batch_from_oracle(blob)
+    assert_same_decode(run_decode(db, "batch", tuning), ref, f"out of order {tuning}")
 
 
 def test_long_fans_reuse_widths_and_bits():
@@ -120,6 +143,8 @@ def test_long_fans_reuse_widths_and_bits():
                                             block_words_max(desc))
             assert_same_decode(run_decode(db, "batch"), ref, f"b={b} w={wmode}")
             assert_same_decode(run_decode(db, "plain", {"checked": 1}), ref, f"b={b} w={wmode}")
+            for t in (PAIR_TUNINGS[0], PAIR_TUNINGS[-1]):
+                assert_same_decode(run_decode(db, "batch", t), ref, f"b={b} w={wmode} {t}")
 
 
 def test_corrupt_streams_flagged_by_checked_kernel():
@@ -134,6 +159,12 @@ def test_corrupt_streams_flagged_by_checked_kernel():
     for mode in ("plain", "batch"):
         out = run_decode(db, mode, {"checked": 1})
         assert int(out["status"][0]) & (1 << mc.MC_ERR_CORRUPT)
+    out = run_decode(db, "batch", PAIR_TUNINGS[-1])
+    assert int(out["status"][0]) & (1 << mc.MC_ERR_CORRUPT)
+    # the pair's other meshlets are decoded regardless
+    ref = O.decode(O.Blob(desc, payload, grids))
+    assert np.array_equal(out["local"].reshape(-1, 3)[:5], ref[0][:5])
+    assert np.array_equal(out["local"].reshape(-1, 3)[10:], ref[0][10:])
     # a descriptor pointing outside the payload is rejected by every kernel
     d2 = desc.copy().view(np.uint32)
     d2[2, 0] = 10_000
@@ -244,7 +275,7 @@ def gts_batches():
 @pytest.mark.parametrize("which", [0, 1])
 @pytest.mark.parametrize("tuning", [None, {"warps_per_cta": 4, "meshlets_per_grab": 1},
                                     {"warps_per_cta": 16, "meshlets_per_grab": 8},
-                                    {"warps_per_cta": 8, "checked": 1}])
+                                    {"warps_per_cta": 8, "checked": 1}] + PAIR_TUNINGS)
 def test_plain_gts_batch_vs_oracle(gts_batches, which, tuning):
     blob = gts_batches[which]
     ref = O.decode(blob)
@@ -270,5 +301,8 @@ def test_plain_gts_corrupt_entry_flagged(gts_batches):
     for mode in ("batch", "plain"):
         res = run_decode(db, mode, {"checked": 1})
         assert int(res["status"][0]) & (1 << 3), mode
+    res = run_decode(db, "batch", PAIR_TUNINGS[-1])
+    assert int(res["status"][0]) & (1 << 3), "pairs"
+
     res = run_decode(db, "batch")
     assert int(res["status"][0]) == 0
