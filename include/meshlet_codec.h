@@ -241,6 +241,7 @@ typedef struct {
   const mc_attr_desc *attr_desc;  /* n_meshlets records (n_attr > 0) */
   const mc_attr_grid *attr_grids; /* n_attr_grids entries */
   uint32_t n_attr_grids;
+  uint32_t max_verts;         /* largest V */
 } mc_blob_view_t;
 
 mc_status mc_blob_view(const mc_blob *b, mc_blob_view_t *v);
@@ -268,6 +269,9 @@ typedef struct {
   const mc_attr_desc *attr_desc;  /* device copies (16-byte aligned), needed by */
   const mc_attr_grid *attr_grids; /* mc_decode_batch_vertices only */
   uint32_t n_attr_grids;
+  uint32_t max_verts;       /* largest V (from mc_blob_view, sizes the fused
+                             * culls' per-warp vertex buffers); 0 = max_tris
+                             * + 2; a meshlet with more vertices is corrupt */
 } mc_device_batch;
 
 /* Launch shape; zero fields take the library defaults or the autotuned

@@ -41,7 +41,7 @@ class mc_blob_view_t(C.Structure):
                 ("input_tris", u64), ("restarts", u64), ("split_meshlets", u64),
                 ("conn_bits", u64), ("pos_bits_total", u64), ("max_block_words", u32),
                 ("max_tris", u32), ("cones", P), ("n_attr", u32), ("attr_bits", u32),
-                ("attr_desc", P), ("attr_grids", P), ("n_attr_grids", u32)]
+                ("attr_desc", P), ("attr_grids", P), ("n_attr_grids", u32), ("max_verts", u32)]
 
 
 class mc_device_batch(C.Structure):
@@ -49,7 +49,7 @@ class mc_device_batch(C.Structure):
                 ("payload_bytes", u64), ("total_tris", u64), ("total_verts", u64),
                 ("max_block_words", u32), ("max_tris", u32), ("cones", P),
                 ("n_attr", u32), ("attr_bits", u32), ("attr_desc", P), ("attr_grids", P),
-                ("n_attr_grids", u32)]
+                ("n_attr_grids", u32), ("max_verts", u32)]
 
 
 class mc_request(C.Structure):
@@ -268,7 +268,7 @@ class Blob:
         v = self.view()
         keys = ("n_meshlets", "payload_bytes", "n_grids", "n_meshes", "total_tris", "total_verts",
                 "input_tris", "restarts", "split_meshlets", "conn_bits", "pos_bits_total",
-                "max_block_words", "max_tris", "n_attr", "attr_bits")
+                "max_block_words", "max_tris", "max_verts", "n_attr", "attr_bits")
         return {k: int(getattr(v, k)) for k in keys}
 
     def __del__(self):
@@ -321,16 +321,19 @@ class DeviceBatch:
 
     @classmethod
     def from_arrays(cls, desc, payload, grids, total_tris, total_verts, max_block_words,
-                    max_tris=256, device="cuda", cones=None, attrs: dict | None = None):
+                    max_tris=256, device="cuda", cones=None, attrs: dict | None = None,
+                    max_verts: int = 0):
         """Wrap blob arrays that did not come from ``mc_encode`` (e.g. a
         hand-packed stream); sizes are the caller's; cones (uint8 [M,32])
         optional; attrs: {"n_attr", "attr_bits", "adesc", "agrids"} of a blob
-        with attribute channels (optional)."""
+        with attribute channels (optional); max_verts: largest V (0 = bounded
+        by max_tris + 2)."""
         self = cls.__new__(cls)
         stats = {"n_meshlets": desc.shape[0], "n_grids": grids.shape[0],
                  "payload_bytes": payload.size, "total_tris": total_tris,
                  "total_verts": total_verts, "max_block_words": max_block_words,
-                 "max_tris": max_tris, "n_attr": attrs["n_attr"] if attrs else 0,
+                 "max_tris": max_tris, "max_verts": max_verts,
+                 "n_attr": attrs["n_attr"] if attrs else 0,
                  "attr_bits": attrs["attr_bits"] if attrs else 0}
         self._init(np.asarray(desc, np.uint8), np.asarray(payload, np.uint8),
                    np.asarray(grids, np.uint8), stats, device,
@@ -361,7 +364,8 @@ class DeviceBatch:
                                  s.get("n_attr", 0), s.get("attr_bits", 0),
                                  None if self.attr_desc is None else self.attr_desc.data_ptr(),
                                  None if self.attr_grids is None else self.attr_grids.data_ptr(),
-                                 0 if self.attr_grids is None else self.attr_grids.numel() // 48)
+                                 0 if self.attr_grids is None else self.attr_grids.numel() // 48,
+                                 s.get("max_verts", 0))
 
     def outputs(self, local=True, global_=True, device="cuda"):
         import torch

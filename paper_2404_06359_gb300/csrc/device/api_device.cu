@@ -58,6 +58,7 @@ mc_status check_batch(const mc_device_batch *b) {
   if (b->max_block_words == 0 || b->max_block_words > 2 * 8 + 64 + 768 + 1280 + 4)
     return MC_ERR_INVALID_ARG;
   if (b->payload_bytes % 16) return MC_ERR_INVALID_ARG;
+  if (b->max_verts > 256 || (b->max_verts && b->max_verts < 3)) return MC_ERR_INVALID_ARG;
   if (b->cones && !aligned(b->cones, 16)) return MC_ERR_INVALID_ARG;
   if (b->n_attr > 5 || (b->n_attr && (b->attr_bits < 1 || b->attr_bits > 32)))
     return MC_ERR_INVALID_ARG;
@@ -76,6 +77,7 @@ BatchArgs args_of(const mc_device_batch *b) {
   a.total_verts = b->total_verts;
   a.max_block_words = b->max_block_words;
   a.max_tris = (b->max_tris == 0 || b->max_tris > 256) ? 256 : b->max_tris;
+  a.max_verts = std::min<uint32_t>(b->max_verts ? b->max_verts : 256, std::min(a.max_tris + 2, 256u));
   a.n_attr = b->n_attr;
   a.attr_bits = b->n_attr ? b->attr_bits : 0;
   a.attr_desc = b->attr_desc;
@@ -276,8 +278,9 @@ mc_status launch_cull_checked(const mc_device_batch *b, const float *d_vp, uint3
   // a grab's survivors are buffered in shared memory: shrink the grab until
   // the requested number of warps fits on an SM
   uint32_t grab = per_grab;
-  int occ = max_ctas_per_sm_cull(warps, b->max_block_words, a.max_tris, grab);
-  while (occ <= 0 && grab > 1) occ = max_ctas_per_sm_cull(warps, b->max_block_words, a.max_tris, --grab);
+  int occ = max_ctas_per_sm_cull(warps, b->max_block_words, a.max_tris, a.max_verts, grab);
+  while (occ <= 0 && grab > 1)
+    occ = max_ctas_per_sm_cull(warps, b->max_block_words, a.max_tris, a.max_verts, --grab);
   if (occ <= 0) return MC_ERR_INVALID_ARG;
   uint32_t per_sm = (t && t->ctas_per_sm) ? std::min<uint32_t>(t->ctas_per_sm, occ) : (uint32_t)occ;
   uint32_t ctas = per_sm * (uint32_t)sm_count();
@@ -321,9 +324,11 @@ mc_status launch_cull_views_checked(const mc_device_batch *b, const float *d_vps
   per_grab = std::min(per_grab, kViewsGrabMax);
   const BatchArgs a = args_of(b);
   uint32_t grab = per_grab;
-  int occ = max_ctas_per_sm_cull_views(warps, b->max_block_words, a.max_tris, grab, n_views);
+  int occ = max_ctas_per_sm_cull_views(warps, b->max_block_words, a.max_tris, a.max_verts, grab,
+                                       n_views);
   while (occ <= 0 && grab > 1)
-    occ = max_ctas_per_sm_cull_views(warps, b->max_block_words, a.max_tris, --grab, n_views);
+    occ = max_ctas_per_sm_cull_views(warps, b->max_block_words, a.max_tris, a.max_verts, --grab,
+                                     n_views);
   if (occ <= 0) return MC_ERR_INVALID_ARG;
   uint32_t per_sm = (t && t->ctas_per_sm) ? std::min<uint32_t>(t->ctas_per_sm, occ) : (uint32_t)occ;
   uint32_t ctas = per_sm * (uint32_t)sm_count();
@@ -643,6 +648,7 @@ extern "C" mc_status mc_decode_batch_host(const mc_blob_view_t *v, mc_desc *d_de
   b.total_verts = v->total_verts;
   b.max_block_words = v->max_block_words;
   b.max_tris = v->max_tris;
+  b.max_verts = v->max_verts;
   mc_status st = check_batch(&b);
   if (st != MC_OK) return st;
   if (!d_scratch || !aligned(d_scratch, 16) || !aligned(d_local, 16) || !aligned(d_global, 16))

@@ -66,23 +66,24 @@ struct CullLayout {
 };
 // Per-warp shared memory of the fused cull: the grab loop's buffers, the
 // strip entries, clip-space x, y, w of the meshlet's vertices
-// (V <= T' + 2 <= max_tris + 2 entries), the vertex bases of the meshlets
-// the survivor buffer references, and the survivor buffer (cap triangles,
-// one word each: three local indices and the source slot).
+// (V <= max_verts entries), the vertex bases of the meshlets the survivor
+// buffer references, and the survivor buffer (cap triangles, one word each:
+// three local indices and the source slot).
 __host__ __device__ inline CullLayout cull_layout(uint32_t max_block_words, uint32_t max_tris,
-                                                  uint32_t per_grab) {
+                                                  uint32_t max_verts, uint32_t per_grab) {
   CullLayout l;
   l.stream = grab_loop_bytes(max_block_words, per_grab);
   l.clip = l.stream + kStreamBytes;
-  l.n_clip = ((max_tris + 2 < 256 ? max_tris + 2 : 256) + 7) & ~7u;
+  l.n_clip = (max_verts + 7) & ~7u;
   l.svb = l.clip + 12 * l.n_clip;
   l.surv = l.svb + 4 * kSurvSources;
   l.cap = kSurvMeshlets * max_tris;
   l.bytes = l.surv + ((4 * l.cap + 15) & ~15u);
   return l;
 }
-uint32_t cull_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, uint32_t per_grab) {
-  return cull_layout(max_block_words, max_tris, per_grab).bytes;
+uint32_t cull_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, uint32_t max_verts,
+                            uint32_t per_grab) {
+  return cull_layout(max_block_words, max_tris, max_verts, per_grab).bytes;
 }
 
 // Decode + cull of one staged meshlet; survivors are appended to surv[] from
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(MAX_THREADS) decode_cull_kernel(BatchArgs a, c
   __shared__ float s_M[16];
   __shared__ float s_eye[4];  // camera position, [3] = 1 when there is one
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-  const CullLayout L = cull_layout(a.max_block_words, a.max_tris, per_grab);
+  const CullLayout L = cull_layout(a.max_block_words, a.max_tris, a.max_verts, per_grab);
   uint8_t *base = smem + warp * L.bytes;
   uint8_t *sI = base + L.stream;
   float2 *cxy = reinterpret_cast<float2 *>(base + L.clip);
@@ -351,7 +352,8 @@ cudaError_t launch_cull_t(const BatchArgs &a, const float *view_proj, const mc_c
                           uint32_t ctas, uint32_t warps, uint32_t per_grab, uint32_t *tri_out,
                           uint32_t *tri_count, float *out_pos, uint32_t *status, uint32_t *scratch,
                           uint64_t *order_state, cudaStream_t s) {
-  const uint32_t smem = cull_smem_per_warp(a.max_block_words, a.max_tris, per_grab) * warps;
+  const uint32_t smem =
+      cull_smem_per_warp(a.max_block_words, a.max_tris, a.max_verts, per_grab) * warps;
   prepare(fn(decode_cull_kernel<CHECKED, MAX_THREADS, ORDERED>));
   decode_cull_kernel<CHECKED, MAX_THREADS, ORDERED><<<ctas, warps * 32, smem, s>>>(
       a, view_proj, cones, per_grab, tri_out, tri_count, out_pos, status, scratch, order_state);
@@ -391,8 +393,8 @@ cudaError_t launch_cull(const BatchArgs &a, const float *view_proj, const mc_con
 }
 
 int max_ctas_per_sm_cull(uint32_t warps, uint32_t max_block_words, uint32_t max_tris,
-                         uint32_t per_grab) {
-  const int smem = (int)(cull_smem_per_warp(max_block_words, max_tris, per_grab) * warps);
+                         uint32_t max_verts, uint32_t per_grab) {
+  const int smem = (int)(cull_smem_per_warp(max_block_words, max_tris, max_verts, per_grab) * warps);
   if (warps > 16) return 0;
   if (warps <= 4) {
     prepare(fn(decode_cull_kernel<true, 128, false>));

@@ -74,50 +74,70 @@ __device__ __forceinline__ uint32_t grab_outside_views(const BatchArgs &a, uint3
 }
 
 struct CullViewsLayout {
-  uint32_t stream, pos, n_vtx, clip, tri, surv, cap, bytes;
+  uint32_t stream, pos, n_vtx, clip, clip_w, tri, surv, cap, bytes;
 };
 // Per-warp shared memory of the multi-view cull: the grab loop's buffers,
-// the strip entries, the meshlet's positions (x, y, z arrays) and clip x, y,
-// w (V <= min(T' + 2, 256) entries), one packed word per triangle slot of
-// the strip walk (32 per word of flags), and one survivor buffer of cap
-// bytes per view (the survivors' triangle slots: a quarter of the shared
-// memory packed words would take, which leaves room for more warps per SM).
+// the strip entries, the meshlet's positions (x, y, z arrays of n_vtx >=
+// max_verts entries), the clip coordinates of two views per vertex (x, y of
+// both as one 16-byte slot, then w of both as one 8-byte slot), one packed
+// word per triangle slot of the strip walk (32 per word of flags), and one
+// survivor buffer of cap bytes per view (the survivors' triangle slots).
 __host__ __device__ inline CullViewsLayout cull_views_layout(uint32_t max_block_words,
-                                                             uint32_t max_tris, uint32_t per_grab,
-                                                             uint32_t n_views) {
+                                                             uint32_t max_tris, uint32_t max_verts,
+                                                             uint32_t per_grab, uint32_t n_views) {
   CullViewsLayout l;
   l.stream = grab_loop_bytes(max_block_words, per_grab);
   l.pos = l.stream + kStreamBytes;
-  l.n_vtx = ((max_tris + 2 < 256 ? max_tris + 2 : 256) + 7) & ~7u;
+  l.n_vtx = (max_verts + 7) & ~7u;
   l.clip = l.pos + 12 * l.n_vtx;
-  l.tri = l.clip + 12 * l.n_vtx;
+  l.clip_w = l.clip + 16 * l.n_vtx;
+  l.tri = l.clip_w + 8 * l.n_vtx;
   l.surv = l.tri + 4 * ((max_tris + 31) & ~31u);
   l.cap = (max_tris + 15) & ~15u;
   l.bytes = l.surv + ((l.cap * n_views + 15) & ~15u);
   return l;
 }
-uint32_t cull_views_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, uint32_t per_grab,
-                                  uint32_t n_views) {
-  return cull_views_layout(max_block_words, max_tris, per_grab, n_views).bytes;
+uint32_t cull_views_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, uint32_t max_verts,
+                                  uint32_t per_grab, uint32_t n_views) {
+  return cull_views_layout(max_block_words, max_tris, max_verts, per_grab, n_views).bytes;
+}
+
+// The per-triangle test of the fused cull (one view): kept when all three
+// indices differ (the packed word is non-zero) and either some clip w is not
+// positive or the determinant of the (x, y, w) rows, evaluated in this fixed
+// order, is positive.
+__device__ __forceinline__ bool tri_kept(bool live, float x0, float y0, float w0, float x1,
+                                         float y1, float w1, float x2, float y2, float w2) {
+  const float c0 = __fmaf_rn(y1, w2, -__fmul_rn(w1, y2));
+  const float c1 = __fmaf_rn(x1, w2, -__fmul_rn(w1, x2));
+  const float c2 = __fmaf_rn(x1, y2, -__fmul_rn(y1, x2));
+  const float det = __fmaf_rn(w0, c2, __fmaf_rn(-y0, c1, __fmul_rn(x0, c0)));
+  const bool behind = (w0 <= 0.0f) | (w1 <= 0.0f) | (w2 <= 0.0f);
+  return live & (behind | (det > 0.0f));
 }
 
 // One staged meshlet against the views in `views` (bit v = view v): the
-// positions go to out_pos and to shared memory, the strip walk leaves one
-// word per triangle slot (x | y << 8 | z << 16, or 0 for a dead slot or a
-// triangle with two equal indices), then per view the clip coordinates,
-// the back-face test and the compaction of the surviving slots (one byte
-// each) into that view's buffer.  Lane v
-// returns the survivor count of view v (0 for the others); the result is
-// false for a corrupt stream (checked build).
+// positions go to out_pos and to shared memory, the strip walk packs the
+// triangles with three distinct indices densely into stri, one word each
+// (x | y << 8 | z << 16; the restart degenerates and the slots past T' are
+// left out, which saves a pass over 32 slots per view in most meshlets),
+// then the views are taken two at a time:
+// the clip coordinates of both (pxy[v] = x, y of the first and second view,
+// pw[v] = their w), then one pass over the triangle slots that tests both
+// views from the same packed word and shared loads and compacts each view's
+// surviving slots (one byte each) into that view's buffer; a last odd view
+// runs the same steps alone.  Lane v returns the survivor count of view v
+// (0 for the others); the result is false for a corrupt stream (checked
+// build).
 template <bool CHECKED, bool B16, int RM>
 __device__ __forceinline__ bool cull_views_staged(const Desc &d, const Grid &g, const float *Ms,
                                                   uint32_t views, const uint32_t *sw, uint8_t *sI,
-                                                  float *px, uint32_t n_vtx, float2 *cxy, float *cw,
+                                                  float *px, uint32_t n_vtx, float4 *pxy, float2 *pw,
                                                   uint32_t *stri, uint32_t *surv, uint32_t cap,
                                                   uint32_t lane, float *out_pos, uint32_t &my_n) {
   my_n = 0;
   if (CHECKED && !stream_header_ok(d, sw)) return false;
-  const uint32_t *pw = sw + conn_words(d);
+  const uint32_t *qw = sw + conn_words(d);
   const bool small = small_coords(d);
   float *py = px + n_vtx, *pz = py + n_vtx;
   float *op = out_pos + 3ull * (d.vbase + lane);
@@ -126,7 +146,7 @@ __device__ __forceinline__ bool cull_views_staged(const Desc &d, const Grid &g, 
   for (uint32_t i = 0; i < vpasses; i++, v += 32, op += 96) {
     const uint32_t vv = min(v, d.V - 1);  // idle lanes recompute the last vertex
     uint32_t q[3];
-    vertex_q<B16>(pw, vv, d.b, q);
+    vertex_q<B16>(qw, vv, d.b, q);
     float p[3];
 #pragma unroll
     for (int c = 0; c < 3; c++)
@@ -137,44 +157,60 @@ __device__ __forceinline__ bool cull_views_staged(const Desc &d, const Grid &g, 
     pz[vv] = p[2];
   }
   const uint32_t a_tri = smem_addr(stri);
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t n_tri = 0;  // triangles with three distinct indices, packed densely in stri
   const bool ok = walk_triangles<CHECKED, RM>(
-      d, sw, sI, lane, [&](uint32_t k, uint32_t x, uint32_t y, uint32_t z, bool live) {
+      d, sw, sI, lane, [&](uint32_t, uint32_t x, uint32_t y, uint32_t z, bool live) {
         const bool keep = live & (x != y) & (y != z) & (x != z);
-        sts_u32_if(a_tri + 4 * k, keep ? (x | (y << 8) | (z << 16)) : 0u, true);
+        const uint32_t bal = __ballot_sync(kFull, keep);
+        sts_u32_if(a_tri + 4 * (n_tri + __popc(bal & lt)), x | (y << 8) | (z << 16), keep);
+        n_tri += __popc(bal);
       });
   if (CHECKED && !ok) return false;
-  const uint32_t tpasses = (d.T + 31) >> 5;
-  for (uint32_t vw = views; vw; vw &= vw - 1) {
-    const uint32_t view = __ffs(vw) - 1;
-    const ClipRows cr = clip_rows(Ms + 16 * view);
+  // zero the rest of the last 32-slot word: those lanes test index 0 and drop out
+  sts_u32_if(a_tri + 4 * (n_tri + lane), 0u, n_tri + lane < ((n_tri + 31) & ~31u));
+  const uint32_t tpasses = (n_tri + 31) >> 5;
+  const uint32_t a_xy = smem_addr(pxy), a_w = smem_addr(pw);
+  for (uint32_t vw = views; vw;) {
+    const uint32_t va = __ffs(vw) - 1;
+    vw &= vw - 1;
+    const bool two = vw != 0;
+    const uint32_t vb = two ? __ffs(vw) - 1 : va;
+    vw &= vw - 1;
+    const ClipRows ra = clip_rows(Ms + 16 * va), rb = clip_rows(Ms + 16 * vb);
     v = lane;
     for (uint32_t i = 0; i < vpasses; i++, v += 32) {
       const uint32_t vv = min(v, d.V - 1);
       const float x = px[vv], y = py[vv], z = pz[vv];
-      cxy[vv] = make_float2(clip_dot(cr, 0, x, y, z), clip_dot(cr, 1, x, y, z));
-      cw[vv] = clip_dot(cr, 2, x, y, z);
+      pxy[vv] = make_float4(clip_dot(ra, 0, x, y, z), clip_dot(ra, 1, x, y, z),
+                            clip_dot(rb, 0, x, y, z), clip_dot(rb, 1, x, y, z));
+      pw[vv] = make_float2(clip_dot(ra, 2, x, y, z), clip_dot(rb, 2, x, y, z));
     }
     __syncwarp();
-    const uint32_t a_surv = smem_addr(reinterpret_cast<uint8_t *>(surv) + cap * view);
-    uint32_t n = 0;
+    const uint32_t a_sa = smem_addr(reinterpret_cast<uint8_t *>(surv) + cap * va);
+    const uint32_t a_sb = smem_addr(reinterpret_cast<uint8_t *>(surv) + cap * vb);
+    uint32_t na = 0, nb = 0;
     uint32_t k = lane;
     for (uint32_t i = 0; i < tpasses; i++, k += 32) {
       const uint32_t t = lds_u32(a_tri + 4 * k);
-      const uint32_t xi = t & 0xFFu, yi = (t >> 8) & 0xFFu, zi = t >> 16;
-      const float2 p0 = cxy[xi], p1 = cxy[yi], p2 = cxy[zi];
-      const float w0 = cw[xi], w1 = cw[yi], w2 = cw[zi];
-      const float c0 = __fmaf_rn(p1.y, w2, -__fmul_rn(w1, p2.y));
-      const float c1 = __fmaf_rn(p1.x, w2, -__fmul_rn(w1, p2.x));
-      const float c2 = __fmaf_rn(p1.x, p2.y, -__fmul_rn(p1.y, p2.x));
-      const float det = __fmaf_rn(w0, c2, __fmaf_rn(-p0.y, c1, __fmul_rn(p0.x, c0)));
-      const bool behind = (w0 <= 0.0f) | (w1 <= 0.0f) | (w2 <= 0.0f);
-      const bool keep = (t != 0u) & (behind | (det > 0.0f));
-      const uint32_t bal = __ballot_sync(kFull, keep);
-      sts_u8_if(a_surv + n + __popc(bal & ((1u << lane) - 1u)), k, keep);
-      n += __popc(bal);
+      const uint32_t o0 = t & 0xFFu, o1 = (t >> 8) & 0xFFu, o2 = t >> 16;
+      const float4 p0 = lds_f4(a_xy + 16 * o0), p1 = lds_f4(a_xy + 16 * o1), p2 = lds_f4(a_xy + 16 * o2);
+      const float2 w0 = lds_f2(a_w + 8 * o0), w1 = lds_f2(a_w + 8 * o1), w2 = lds_f2(a_w + 8 * o2);
+      const bool live = t != 0u;
+      const bool ka = tri_kept(live, p0.x, p0.y, w0.x, p1.x, p1.y, w1.x, p2.x, p2.y, w2.x);
+      const uint32_t ba = __ballot_sync(kFull, ka);
+      sts_u8_if(a_sa + na + __popc(ba & lt), k, ka);
+      na += __popc(ba);
+      if (two) {
+        const bool kb = tri_kept(live, p0.z, p0.w, w0.y, p1.z, p1.w, w1.y, p2.z, p2.w, w2.y);
+        const uint32_t bb = __ballot_sync(kFull, kb);
+        sts_u8_if(a_sb + nb + __popc(bb & lt), k, kb);
+        nb += __popc(bb);
+      }
     }
-    if (lane == view) my_n = n;
-    __syncwarp();  // the next view rewrites the clip coordinates
+    if (lane == va) my_n = na;
+    if (two && lane == vb) my_n = nb;
+    __syncwarp();  // the next pair rewrites the clip coordinates
   }
   return true;
 }
@@ -182,12 +218,12 @@ __device__ __forceinline__ bool cull_views_staged(const Desc &d, const Grid &g, 
 template <bool CHECKED>
 __device__ __forceinline__ bool cull_views_dispatch(const Desc &d, const Grid &g, const float *Ms,
                                                     uint32_t views, const uint32_t *sw, uint8_t *sI,
-                                                    float *px, uint32_t n_vtx, float2 *cxy,
-                                                    float *cw, uint32_t *stri, uint32_t *surv,
+                                                    float *px, uint32_t n_vtx, float4 *pxy,
+                                                    float2 *pw, uint32_t *stri, uint32_t *surv,
                                                     uint32_t cap, uint32_t lane, float *out_pos,
                                                     uint32_t &my_n) {
 #define MC_CULLV(B, R)                                                                           \
-  cull_views_staged<CHECKED, B, R>(d, g, Ms, views, sw, sI, px, n_vtx, cxy, cw, stri, surv, cap, \
+  cull_views_staged<CHECKED, B, R>(d, g, Ms, views, sw, sI, px, n_vtx, pxy, pw, stri, surv, cap, \
                                    lane, out_pos, my_n)
   if (d.b == 16) {
     if (d.w == 8) return MC_CULLV(true, kReuseBytes);
@@ -209,12 +245,13 @@ __global__ void __launch_bounds__(MAX_THREADS) decode_cull_views_kernel(
   __shared__ float s_M[16 * kMaxViews];
   __shared__ float s_eye[4 * kMaxViews];  // camera positions, [3] = 1 when there is one
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-  const CullViewsLayout L = cull_views_layout(a.max_block_words, a.max_tris, per_grab, n_views);
+  const CullViewsLayout L =
+      cull_views_layout(a.max_block_words, a.max_tris, a.max_verts, per_grab, n_views);
   uint8_t *base = smem + warp * L.bytes;
   uint8_t *sI = base + L.stream;
   float *px = reinterpret_cast<float *>(base + L.pos);
-  float2 *cxy = reinterpret_cast<float2 *>(base + L.clip);
-  float *cw = reinterpret_cast<float *>(cxy + L.n_vtx);
+  float4 *pxy = reinterpret_cast<float4 *>(base + L.clip);
+  float2 *pw = reinterpret_cast<float2 *>(base + L.clip_w);
   uint32_t *stri = reinterpret_cast<uint32_t *>(base + L.tri);
   uint32_t *surv = reinterpret_cast<uint32_t *>(base + L.surv);
   for (uint32_t i = threadIdx.x; i < 16 * n_views; i += blockDim.x) s_M[i] = view_projs[i];
@@ -233,7 +270,7 @@ __global__ void __launch_bounds__(MAX_THREADS) decode_cull_views_kernel(
               if (!views) return;
               const Grid g = load_grid(a.grids + d.grid);
               uint32_t my_n = 0;
-              if (!cull_views_dispatch<CHECKED>(d, g, s_M, views, sw, sI, px, L.n_vtx, cxy, cw,
+              if (!cull_views_dispatch<CHECKED>(d, g, s_M, views, sw, sI, px, L.n_vtx, pxy, pw,
                                                 stri, surv, L.cap, lane, out_pos, my_n)) {
                 if (lane == 0) set_status(status, MC_ERR_CORRUPT);
                 __syncwarp();
@@ -283,7 +320,7 @@ cudaError_t launch_cull_views_t(const BatchArgs &a, const float *view_projs, uin
                                 uint32_t *tri_counts, float *out_pos, uint32_t *status,
                                 uint32_t *scratch, cudaStream_t s) {
   const uint32_t smem =
-      cull_views_smem_per_warp(a.max_block_words, a.max_tris, per_grab, n_views) * warps;
+      cull_views_smem_per_warp(a.max_block_words, a.max_tris, a.max_verts, per_grab, n_views) * warps;
   prepare(fn(decode_cull_views_kernel<CHECKED, MAX_THREADS>));
   decode_cull_views_kernel<CHECKED, MAX_THREADS><<<ctas, warps * 32, smem, s>>>(
       a, view_projs, n_views, cones, per_grab, tri_out, tri_stride, tri_counts, out_pos, status,
@@ -313,9 +350,9 @@ cudaError_t launch_cull_views(const BatchArgs &a, const float *view_projs, uint3
 }
 
 int max_ctas_per_sm_cull_views(uint32_t warps, uint32_t max_block_words, uint32_t max_tris,
-                               uint32_t per_grab, uint32_t n_views) {
+                               uint32_t max_verts, uint32_t per_grab, uint32_t n_views) {
   const int smem =
-      (int)(cull_views_smem_per_warp(max_block_words, max_tris, per_grab, n_views) * warps);
+      (int)(cull_views_smem_per_warp(max_block_words, max_tris, max_verts, per_grab, n_views) * warps);
   if (warps > 16) return 0;
   if (warps <= 4) {
     prepare(fn(decode_cull_views_kernel<true, 128>));

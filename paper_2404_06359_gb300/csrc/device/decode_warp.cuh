@@ -103,6 +103,7 @@ struct BatchArgs {
   uint64_t payload_bytes, total_tris, total_verts;
   uint32_t max_block_words;  // capacity of one meshlet's shared-memory slot
   uint32_t max_tris;         // largest T' of the batch (sizes per-warp output buffers)
+  uint32_t max_verts;        // largest V of the batch (sizes per-warp vertex buffers)
   uint32_t n_attr, attr_bits;  // attribute channels after the positions (0 = none)
   const mc_attr_desc *attr_desc;
   const mc_attr_grid *attr_grids;
@@ -129,7 +130,7 @@ __device__ __forceinline__ bool header_ok(const Desc &d, const BatchArgs &a) {
   // evaluated without short-circuit branches (all terms are cheap)
   const bool shape = (d.V - 3u <= 253u) & (d.T - 1u <= 255u) & (d.V <= d.T + 2) &
                      (d.w <= 8u) & (d.b - 1u <= 31u) & (d.grid < a.n_grids) &
-                     (d.T <= a.max_tris);
+                     (d.T <= a.max_tris) & (d.V <= a.max_verts);
   const uint32_t top = ~field_max(d.b);  // largest L with L + 2^b - 1 < 2^32
   const bool box = (d.L[0] <= top) & (d.L[1] <= top) & (d.L[2] <= top);
   const uint32_t padded = (block_words(d) + 3) & ~3u;
@@ -185,6 +186,19 @@ __device__ __forceinline__ uint32_t lds_u16(uint32_t a) {
 __device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
   uint32_t v;
   asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ float4 lds_f4(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ float2 lds_f2(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
   return v;
 }
 __device__ __forceinline__ void sts_u8(uint32_t a, uint32_t v) {

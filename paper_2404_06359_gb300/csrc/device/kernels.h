@@ -19,7 +19,8 @@ const void *fn(K k) {
 }
 
 uint32_t decode_smem_per_warp(uint32_t max_block_words);
-uint32_t cull_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, uint32_t per_grab);
+uint32_t cull_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, uint32_t max_verts,
+                            uint32_t per_grab);
 uint32_t batch_smem_per_warp(uint32_t max_block_words, uint32_t per_grab);
 
 cudaError_t launch_plain(const BatchArgs &a, uint32_t first, uint32_t count, uint32_t warps,
@@ -49,17 +50,17 @@ cudaError_t launch_batch_pairs(const BatchArgs &a, uint32_t ctas, uint32_t warps
 int max_ctas_per_sm_batch_pairs(uint32_t warps, uint32_t max_block_words, uint32_t per_grab);
 // Multi-view fused cull (1 <= n_views <= 8, per_grab <= 4): view v's
 // survivors go to tri_out + v * tri_stride, its count to tri_counts[v].
-uint32_t cull_views_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, uint32_t per_grab,
-                                  uint32_t n_views);
+uint32_t cull_views_smem_per_warp(uint32_t max_block_words, uint32_t max_tris, uint32_t max_verts,
+                                  uint32_t per_grab, uint32_t n_views);
 cudaError_t launch_cull_views(const BatchArgs &a, const float *view_projs, uint32_t n_views,
                               const mc_cone *cones, uint32_t ctas, uint32_t warps,
                               uint32_t per_grab, bool checked, uint32_t *tri_out,
                               uint64_t tri_stride, uint32_t *tri_counts, float *out_pos,
                               uint32_t *status, uint32_t *scratch, cudaStream_t s);
 int max_ctas_per_sm_cull_views(uint32_t warps, uint32_t max_block_words, uint32_t max_tris,
-                               uint32_t per_grab, uint32_t n_views);
+                               uint32_t max_verts, uint32_t per_grab, uint32_t n_views);
 int max_ctas_per_sm_cull(uint32_t warps, uint32_t max_block_words, uint32_t max_tris,
-                         uint32_t per_grab);
+                         uint32_t max_verts, uint32_t per_grab);
 
 cudaError_t launch_requests(const BatchArgs &a, const mc_request *reqs, uint32_t n_reqs,
                             uint32_t total_work, uint32_t ctas, uint32_t warps, uint32_t per_grab,

@@ -453,6 +453,7 @@ extern "C" mc_status mc_encode(const mc_meshlets *m, const float *pos, uint32_t 
       blob->pos_bits_total += 3ull * x.V * x.b;
       blob->max_block_words = std::max(blob->max_block_words, x.words);
       blob->max_tris = std::max(blob->max_tris, x.tp);
+      blob->max_verts = std::max(blob->max_verts, x.V);
     }
   } catch (const std::bad_alloc &) {
     delete blob;
@@ -537,6 +538,7 @@ extern "C" mc_status mc_blob_concat(const mc_blob *const *blobs, uint32_t n, mc_
       b->pos_bits_total += s->pos_bits_total;
       b->max_block_words = std::max(b->max_block_words, s->max_block_words);
       b->max_tris = std::max(b->max_tris, s->max_tris);
+      b->max_verts = std::max(b->max_verts, s->max_verts);
     }
     b->total_tris = tb;
     b->total_verts = vb;
@@ -569,6 +571,7 @@ extern "C" mc_status mc_blob_view(const mc_blob *b, mc_blob_view_t *v) {
   v->pos_bits_total = b->pos_bits_total;
   v->max_block_words = b->max_block_words;
   v->max_tris = b->max_tris;
+  v->max_verts = b->max_verts;
   v->cones = b->cones.data();
   v->n_attr = b->n_attr;
   v->attr_bits = b->attr_bits;

@@ -66,5 +66,5 @@ struct mc_blob {
   std::vector<mc_attr_grid> attr_grids;
   uint64_t total_tris = 0, total_verts = 0, input_tris = 0;
   uint64_t restarts = 0, split_meshlets = 0, conn_bits = 0, pos_bits_total = 0;
-  uint32_t max_block_words = 0, max_tris = 0;
+  uint32_t max_block_words = 0, max_tris = 0, max_verts = 0;
 };

@@ -26,6 +26,11 @@ def max_tris(desc: np.ndarray) -> int:
     return int((w[:, 3] >> 16).max()) if w.shape[0] else 1
 
 
+def max_verts(desc: np.ndarray) -> int:
+    w = desc.view(np.uint32).reshape(-1, 8)
+    return int((w[:, 3] & 0xFFFF).max()) if w.shape[0] else 3
+
+
 def device_batch_from_oracle(blob: O.Blob, cones: bool = False) -> mc.DeviceBatch:
     at = blob.attrs
     return mc.DeviceBatch.from_arrays(blob.desc, blob.payload, blob.grids, blob.total_tris,
@@ -33,7 +38,7 @@ def device_batch_from_oracle(blob: O.Blob, cones: bool = False) -> mc.DeviceBatc
                                       block_words_max(blob.desc, at["n_attr"] if at else 0,
                                                       at["attr_bits"] if at else 0),
                                       max_tris(blob.desc), cones=blob.cones if cones else None,
-                                      attrs=at)
+                                      attrs=at, max_verts=max_verts(blob.desc))
 
 
 def run_decode(db: mc.DeviceBatch, mode="batch", tuning=None, local=True, global_=True):

@@ -58,6 +58,7 @@ def _run_forms(db, T, V):
     res = {}
     d_vp = torch.from_numpy(_vp()).cuda()
     d_vps = torch.from_numpy(np.ascontiguousarray(np.stack([_vp(), _vp()]))).cuda()
+    M = db.stats["n_meshlets"]
     for form in ("plain", "batch", "noalloc", "cull", "ordered", "views", "requests"):
         out = db.outputs()
         out["local"].fill_(0xAA)
@@ -66,7 +67,7 @@ def _run_forms(db, T, V):
         tri = torch.zeros(2 * (3 * T + 3), dtype=torch.int32, device="cuda")
         cnt = torch.zeros(2, dtype=torch.int32, device="cuda")
         if form == "plain":
-            mc.mc_decode_plain(db, 0, 3, out["local"], out["global"], out["pos"], out["status"])
+            mc.mc_decode_plain(db, 0, M, out["local"], out["global"], out["pos"], out["status"])
         elif form == "batch":
             mc.mc_decode_batch(db, out["local"], out["global"], out["pos"], out["status"], scratch)
         elif form == "noalloc":
@@ -80,12 +81,12 @@ def _run_forms(db, T, V):
                                     scratch)
         else:
             r = np.zeros(1, mc.REQUEST_DTYPE)
-            r["n_meshlets"] = 3
+            r["n_meshlets"] = M
             r["tri_count"], r["vert_count"] = T, V
             r["d_local"], r["d_global"] = out["local"].data_ptr(), out["global"].data_ptr()
             r["d_pos"] = out["pos"].data_ptr()
             d_r = torch.from_numpy(r.view(np.uint8).copy()).cuda()
-            mc.mc_decode_requests(db, d_r, 1, 3, out["status"], scratch)
+            mc.mc_decode_requests(db, d_r, 1, M, out["status"], scratch)
         torch.cuda.synchronize()
         assert int(scratch.abs().sum()) == 0, form
         cull = form in ("cull", "ordered", "views")
@@ -132,3 +133,33 @@ def test_top_of_grid_decodes_and_one_past_is_corrupt(b):
                 assert np.array_equal(l[:t0], loc[:t0]) and np.array_equal(l[t1:], loc[t1:]), form
                 assert np.array_equal(p[:v0].view(np.uint32), pos[:v0].view(np.uint32)), form
                 assert np.array_equal(p[v1:].view(np.uint32), pos[v1:].view(np.uint32)), form
+
+
+def test_max_verts_bounds_every_meshlet():
+    """mc_device_batch.max_verts sizes the fused culls' per-warp vertex
+    buffers, so a meshlet with more vertices than it claims is rejected as
+    corrupt (by every form) instead of overrunning them; the true largest V
+    (or 0, the T' + 2 bound) decodes like the oracle."""
+    import torch
+    from paper_2404_06359_gb300 import meshgen as G
+    from tests.gpu_util import max_tris, max_verts
+    blob = O.encode_mesh(G.grid_mesh(12), (64, 126), 16, 0)
+    vmax = max_verts(blob.desc)
+    loc, _, pos, _ = O.decode(blob)
+    T, V = blob.total_tris, blob.total_verts
+    args = (blob.desc, blob.payload, blob.grids, T, V, block_words_max(blob.desc), max_tris(blob.desc))
+    for mv in (0, vmax):
+        res = _run_forms(mc.DeviceBatch.from_arrays(*args, max_verts=mv), T, V)
+        for form, (st, l, p, tri) in res.items():
+            assert st == 0, (mv, form)
+            if l is not None:
+                assert np.array_equal(l, loc), (mv, form)
+    Vs = blob.fields()["V"].astype(np.int64)
+    res = _run_forms(mc.DeviceBatch.from_arrays(*args, max_verts=vmax - 1), T, V)
+    for form, (st, l, p, tri) in res.items():
+        assert st & (1 << mc.MC_ERR_CORRUPT), form
+        if l is not None:  # meshlets within the bound still decode
+            f = blob.fields()
+            for m in np.nonzero(Vs < vmax)[0][:5]:
+                tb, tp = int(f["tri_base"][m]), int(f["Tp"][m])
+                assert np.array_equal(l[tb:tb + tp], loc[tb:tb + tp]), form
