@@ -196,6 +196,13 @@ typedef struct {
                                    * texture coordinate; Sec. 4.4) */
   uint32_t n_attr;                /* 0..5 */
   uint32_t attr_bits;             /* b of every attribute channel (1..32) */
+  uint32_t strip_search_nodes;    /* 0: the greedy strips; else per meshlet a
+                                   * branch and bound for the fewest strips
+                                   * (Sec. 4.1's objective: the most shared
+                                   * edges used, no fork, no cycle) runs from
+                                   * the greedy cover for at most this many
+                                   * nodes, and its cover is used when it has
+                                   * fewer strips (fewer restart degenerates) */
 } mc_encode_params;
 
 /* Encode the meshlets of one mesh (Sec. 4.2-4.4) into a blob.

@@ -65,8 +65,9 @@ def lib():
             P = C.c_void_p
             u32, u64 = C.c_uint32, C.c_uint64
             L.orc_meshletize.argtypes = [u32, P, u32, P, P, u32, P, P, P, P]
-            L.orc_stripify.argtypes = [P, P, u32, P, P, P, P, P]
-            L.orc_encode.argtypes = [P, u32, P, P, P, u32, P, u32, P, u32, P, u32, u32,
+            L.orc_stripify.argtypes = [P, P, u32, u32, P, P, P, P, P]
+            L.orc_min_strips.argtypes = [P, P, u32, u32, u32, P, P, P]
+            L.orc_encode.argtypes = [P, u32, P, P, P, u32, P, u32, P, u32, P, u32, u32, u32,
                                      C.POINTER(C.POINTER(_Blob))]
             L.orc_decode_attrs.argtypes = [P, P, u32, P, u64, P, u32, u32, u32, u32, u32, P]
             L.orc_blob_free.argtypes = [C.POINTER(_Blob)]
@@ -149,8 +150,10 @@ def meshletize(tris: np.ndarray, n_verts: int, limits, tri_class: np.ndarray | N
     return mtri, mstart[: nm.value + 1].copy(), ng.value
 
 
-def stripify(tris: np.ndarray, ids: np.ndarray):
-    """Greedy strip of tris[ids]; returns (stream, flags, order, T', strips)."""
+def stripify(tris: np.ndarray, ids: np.ndarray, search_nodes: int = 0):
+    """Strip of tris[ids] (greedy; with search_nodes > 0, the fewest-strips
+    cover found within that budget when it is better); returns (stream,
+    flags, order, T', strips)."""
     tris = np.ascontiguousarray(tris, np.uint32)
     ids = np.ascontiguousarray(ids, np.uint32)
     T = ids.size
@@ -158,15 +161,29 @@ def stripify(tris: np.ndarray, ids: np.ndarray):
     flags = np.zeros(5 * T + 8, np.uint8)
     order = np.zeros(T, np.uint32)
     tp, ns = C.c_uint32(0), C.c_uint32(0)
-    _check(lib().orc_stripify(_p(tris), _p(ids), T, _p(stream), _p(flags), _p(order),
+    _check(lib().orc_stripify(_p(tris), _p(ids), T, search_nodes, _p(stream), _p(flags), _p(order),
                               C.byref(tp), C.byref(ns)), "orc_stripify")
     return stream[: tp.value + 2].copy(), flags[: tp.value].copy(), order, tp.value, ns.value
 
 
+def min_strips(tris: np.ndarray, ids: np.ndarray, greedy_strips: int, max_nodes: int = 2_000_000,
+               best_found: bool = False):
+    """(fewest strips or 0 when the search gave up after max_nodes nodes,
+    lower bound[, fewest found within the budget]) for the triangles
+    tris[ids] (orc_min_strips)."""
+    tris = np.ascontiguousarray(tris, np.uint32)
+    ids = np.ascontiguousarray(ids, np.uint32)
+    mn, lo, bf = C.c_uint32(0), C.c_uint32(0), C.c_uint32(0)
+    _check(lib().orc_min_strips(_p(tris), _p(ids), ids.size, greedy_strips, max_nodes,
+                                C.byref(mn), C.byref(lo), C.byref(bf)), "orc_min_strips")
+    return (mn.value, lo.value, bf.value) if best_found else (mn.value, lo.value)
+
+
 def encode(pos: np.ndarray, tris: np.ndarray, mtri: np.ndarray, mstart: np.ndarray,
            bits, reuse_mode: int = 0, perm: np.ndarray | None = None, mesh_id: int = 0,
-           attrs: np.ndarray | None = None, attr_bits: int = 16) -> Blob:
-    """attrs: optional float32 [n_verts, n_attr] extra attribute channels (n_attr <= 5)."""
+           attrs: np.ndarray | None = None, attr_bits: int = 16, search_nodes: int = 0) -> Blob:
+    """attrs: optional float32 [n_verts, n_attr] extra attribute channels (n_attr <= 5);
+    search_nodes: node budget of the fewest-strips search per meshlet (0 = greedy)."""
     pos = np.ascontiguousarray(pos, np.float32)
     at = None if attrs is None else np.ascontiguousarray(attrs, np.float32).reshape(pos.shape[0], -1)
     n_attr = 0 if at is None else at.shape[1]
@@ -178,7 +195,7 @@ def encode(pos: np.ndarray, tris: np.ndarray, mtri: np.ndarray, mstart: np.ndarr
     _check(lib().orc_encode(_p(pos), pos.shape[0], _p(tris), _p(np.ascontiguousarray(mtri, np.uint32)),
                             _p(np.ascontiguousarray(mstart, np.uint32)), nm, _p(bits), reuse_mode,
                             _p(perm), mesh_id, _p(at), n_attr, attr_bits if n_attr else 0,
-                            C.byref(out)), "orc_encode")
+                            search_nodes, C.byref(out)), "orc_encode")
     b = out.contents
     try:
         desc = np.ctypeslib.as_array(b.desc, (b.n_meshlets * 32,)).copy().reshape(-1, 32) \
@@ -204,14 +221,16 @@ def encode(pos: np.ndarray, tris: np.ndarray, mtri: np.ndarray, mstart: np.ndarr
 
 
 def encode_mesh(mesh, limits=(64, 126), bits=16, reuse_mode: int = 0, perm=None,
-                mesh_id: int = 0, attrs: np.ndarray | None = None, attr_bits: int = 16) -> Blob:
+                mesh_id: int = 0, attrs: np.ndarray | None = None, attr_bits: int = 16,
+                search_nodes: int = 0) -> Blob:
     """meshletize + encode of a ``meshgen.Mesh``; ``bits`` scalar or callable(n)->array."""
     lim = np.asarray(limits, np.uint32).reshape(-1)
     mtri, mstart, ng = meshletize(mesh.tris, mesh.n_verts, lim, mesh.tri_class)
     nm = mstart.size - 1
     b = bits(nm) if callable(bits) else np.full(nm, bits, np.uint8)
     p = perm(nm) if callable(perm) else perm
-    blob = encode(mesh.pos, mesh.tris, mtri, mstart, b, reuse_mode, p, mesh_id, attrs, attr_bits)
+    blob = encode(mesh.pos, mesh.tris, mtri, mstart, b, reuse_mode, p, mesh_id, attrs, attr_bits,
+                  search_nodes)
     blob.stats["grown_meshlets"] = ng
     blob.stats["input_tris"] = mesh.n_tris
     blob.stats["mtri"], blob.stats["mstart"] = mtri, mstart

@@ -148,13 +148,13 @@ static uint32_t ceil_log2(uint32_t v) {
 }
 
 static int build_meshlet(const uint32_t *tris, const uint32_t *ids, uint32_t T,
-                         uint32_t reuse_mode, meshlet_t *m) {
+                         uint32_t reuse_mode, uint32_t search_nodes, meshlet_t *m) {
   uint32_t stream[5 * 256 + 8];
   uint8_t flags[5 * 256 + 8];
   uint32_t order[257];
   uint32_t tp = 0, strips = 0;
   if (T == 0 || T > 256) return ORC_ERR_LIMIT;
-  int rc = orc_stripify(tris, ids, T, stream, flags, order, &tp, &strips);
+  int rc = orc_stripify(tris, ids, T, search_nodes, stream, flags, order, &tp, &strips);
   if (rc != ORC_OK) return rc;
   if (tp > 256) return ORC_ERR_LIMIT;
   m->tp = tp;
@@ -256,7 +256,7 @@ int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
                const uint32_t *mtri, const uint32_t *mstart,
                uint32_t n_meshlets, const uint8_t *bits, uint32_t reuse_mode,
                const uint32_t *perm, uint32_t mesh_id, const float *attrs, uint32_t n_attr,
-               uint32_t attr_bits, orc_blob **out) {
+               uint32_t attr_bits, uint32_t strip_search_nodes, orc_blob **out) {
   if (!pos || !tris || !mtri || !mstart || !bits || !out || n_verts == 0 || reuse_mode > 2 ||
       n_attr > 5 || (n_attr && (!attrs || attr_bits < 1 || attr_bits > 32)))
     return ORC_ERR_ARG;
@@ -267,7 +267,8 @@ int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
   if (!ms) return ORC_ERR_NOMEM;
   int rc = ORC_OK;
   for (uint32_t m = 0; m < n_meshlets && rc == ORC_OK; m++) {
-    rc = build_meshlet(tris, mtri + mstart[m], mstart[m + 1] - mstart[m], reuse_mode, &ms[m]);
+    rc = build_meshlet(tris, mtri + mstart[m], mstart[m + 1] - mstart[m], reuse_mode,
+                       strip_search_nodes, &ms[m]);
     ms[m].b = bits[m];
   }
   if (rc != ORC_OK) { free(ms); return rc; }

@@ -81,7 +81,7 @@ static int emit_final(const uint32_t *tris, const uint32_t *ids, uint32_t T,
   uint32_t tp = 0, strips = 0;
   int rc = ORC_ERR_NOMEM;
   if (!stream || !flags || !order) goto done;
-  rc = orc_stripify(tris, ids, T, stream, flags, order, &tp, &strips);
+  rc = orc_stripify(tris, ids, T, 0, stream, flags, order, &tp, &strips);
   if (rc != ORC_OK) goto done;
   if (tp <= max_tris) {
     out_start[*n_meshlets] = *n_out_tri;

@@ -79,10 +79,27 @@ int orc_meshletize(uint32_t n_verts, const uint32_t *tris, uint32_t n_tris,
 /* Greedy strip of the T triangles tris[ids[i]] (i = list position).
  * stream: T' + 2 global vertex ids; flags: T' entries (0 = L, 1 = R; entry 0
  * is 0); strip_order: the T list positions in strip order.
+ * search_nodes > 0: the branch and bound of orc_min_strips then runs from the
+ * greedy cover with that node budget, and the fewest-strips cover it finds is
+ * taken when it has fewer strips than the greedy one; its strips are emitted
+ * from each path end in list order that is not yet emitted, walking the path.
  * Capacity needed: stream 5*T, flags 5*T. */
-int orc_stripify(const uint32_t *tris, const uint32_t *ids, uint32_t T,
+int orc_stripify(const uint32_t *tris, const uint32_t *ids, uint32_t T, uint32_t search_nodes,
                  uint32_t *stream, uint8_t *flags, uint32_t *strip_order,
                  uint32_t *out_tp, uint32_t *out_strips);
+
+/* Fewest strips (path cover of the triangles' adjacency graph) of the
+ * triangles ids[0..T), by exhaustive branch and bound starting from the
+ * greedy count greedy_strips (Sec. 4.1 maximises the used adjacency edges
+ * under the same no-fork / no-cycle conditions).  *out_min = the minimum, or
+ * 0 when the search needed more than max_nodes nodes (max_nodes = 0: not
+ * searched); *out_lower = a lower bound valid at any size (each connected
+ * part needs max(1, ceil(e / 2)) strips, e = its triangles with at most one
+ * neighbour); *out_best (may be NULL) = the fewest strips the search found
+ * within max_nodes nodes, proven minimal or not. */
+int orc_min_strips(const uint32_t *tris, const uint32_t *ids, uint32_t T, uint32_t greedy_strips,
+                   uint32_t max_nodes, uint32_t *out_min, uint32_t *out_lower, uint32_t *out_best);
+
 
 typedef struct {
   uint32_t n_meshlets;
@@ -111,12 +128,14 @@ typedef struct {
  * meshlet perm[p].  mesh_id is written into the grid entries.  attrs (may be
  * NULL with n_attr = 0): n_attr (<= 5) extra attribute channels per input
  * vertex (attrs[n_attr v + c]), quantised crack-free at attr_bits bits on one
- * grid for the mesh, by the rules of the positions (Sec. 4.4). */
+ * grid for the mesh, by the rules of the positions (Sec. 4.4).
+ * strip_search_nodes: the node budget of the fewest-strips search per
+ * meshlet (orc_stripify; 0 = the greedy strips). */
 int orc_encode(const float *pos, uint32_t n_verts, const uint32_t *tris,
                const uint32_t *mtri, const uint32_t *mstart,
                uint32_t n_meshlets, const uint8_t *bits, uint32_t reuse_mode,
                const uint32_t *perm, uint32_t mesh_id, const float *attrs,
-               uint32_t n_attr, uint32_t attr_bits, orc_blob **out);
+               uint32_t n_attr, uint32_t attr_bits, uint32_t strip_search_nodes, orc_blob **out);
 void orc_blob_free(orc_blob *b);
 
 /* FP32 dequantisation of a grid coordinate g (Sec. 4.4):

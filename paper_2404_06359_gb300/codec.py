@@ -26,7 +26,7 @@ class mc_limits(C.Structure):
 class mc_encode_params(C.Structure):
     _fields_ = [("pos_bits", u32), ("pos_bits_per_meshlet", P), ("reuse_mode", u32),
                 ("order", P), ("mesh_id", u32), ("n_threads", u32), ("attrs", P),
-                ("n_attr", u32), ("attr_bits", u32)]
+                ("n_attr", u32), ("attr_bits", u32), ("strip_search_nodes", u32)]
 
 
 class mc_mesh_info(C.Structure):
@@ -279,8 +279,10 @@ class Blob:
 
 def mc_encode(meshlets: Meshlets, pos: np.ndarray, pos_bits=16, reuse_mode: int = 0, order=None,
               mesh_id: int = 0, n_threads: int = 0, attrs: np.ndarray | None = None,
-              attr_bits: int = 16) -> Blob:
-    """attrs: optional float32 [n_verts, n_attr] extra attribute channels (n_attr <= 5)."""
+              attr_bits: int = 16, strip_search_nodes: int = 0) -> Blob:
+    """attrs: optional float32 [n_verts, n_attr] extra attribute channels (n_attr <= 5);
+    strip_search_nodes: node budget of the fewest-strips search per meshlet
+    (0 = the greedy strips)."""
     pos = np.ascontiguousarray(pos, np.float32)
     per = None
     if np.ndim(pos_bits) > 0:
@@ -290,7 +292,7 @@ def mc_encode(meshlets: Meshlets, pos: np.ndarray, pos_bits=16, reuse_mode: int 
     n_attr = 0 if at is None else at.shape[1]
     p = mc_encode_params(int(pos_bits) if per is None else 0, _np_ptr(per), reuse_mode,
                          _np_ptr(order), mesh_id, n_threads, _np_ptr(at), n_attr,
-                         attr_bits if n_attr else 0)
+                         attr_bits if n_attr else 0, strip_search_nodes)
     h = P()
     _check(lib().mc_encode(meshlets._h, _np_ptr(pos), pos.shape[0], C.byref(p), C.byref(h)),
            "mc_encode")

@@ -159,11 +159,24 @@ extern "C" mc_status mc_encode(const mc_meshlets *m, const float *pos, uint32_t 
         [&](uint64_t i) {
           Packed &x = pk[i];
           const uint64_t s0 = m->stream_start[i];
-          const uint32_t tp = m->tp[i];
+          uint32_t tp = m->tp[i];
           const uint32_t *st = m->stream.data() + s0;
           const uint8_t *fl = m->flags.data() + s0;
-          x.tp = tp;
           x.strips = m->strips[i];
+          thread_local StripScratch scratch;
+          thread_local StripOut searched;
+          if (p->strip_search_nodes && x.strips > 1) {  // fewer strips by the search
+            const uint32_t t0 = m->start[i], T = m->start[i + 1] - t0;
+            build_strip(nullptr, m->tri.data() + t0, T, scratch, searched, p->strip_search_nodes,
+                        m->corners.data() + 3 * (size_t)t0);
+            if (searched.strips < x.strips) {
+              tp = searched.tp;
+              st = searched.stream.data();
+              fl = searched.flags.data();
+              x.strips = searched.strips;
+            }
+          }
+          x.tp = tp;
           x.b = p->pos_bits_per_meshlet ? p->pos_bits_per_meshlet[i] : p->pos_bits;
           x.gv.clear();
           std::memset(x.flag_words, 0, sizeof(x.flag_words));

@@ -32,11 +32,19 @@ struct StripScratch {
   std::vector<int32_t> nb, adj, pos;
   std::vector<uint8_t> visited;
   std::vector<uint32_t> path, order, lens, best_order, best_lens;
+  // fewest-strips search
+  std::vector<uint32_t> eu, ev, rem, end_of;
+  std::vector<uint8_t> deg, sel, best_sel;
+  std::vector<int32_t> chosen_nb;
 };
 
-// Greedy strip over the triangles tri[ids[i]], i = list position.
+// Strip over the triangles tri[ids[i]], i = list position (or, with
+// list_corners, the triangle whose corners are list_corners[3i..3i+2]; ids
+// then only seed the random choices): the best of the randomised greedy
+// covers and, with search_nodes > 0, the fewest-strips cover a branch and
+// bound finds within that many nodes when it has fewer strips.
 void build_strip(const uint32_t *tri, const uint32_t *ids, uint32_t T, StripScratch &s,
-                 StripOut &out);
+                 StripOut &out, uint32_t search_nodes = 0, const uint32_t *list_corners = nullptr);
 
 }  // namespace mc
 

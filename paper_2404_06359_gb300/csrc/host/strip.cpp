@@ -37,9 +37,103 @@ constexpr uint32_t kTries = 16;      // randomised covers per meshlet
 constexpr uint32_t kRotations = 32;  // rotations per strip
 }  // namespace
 
+namespace {
+// Fewest strips by branch and bound (Sec. 4.1's objective: the most
+// adjacency edges used with no triangle on three of them and no cycle).
+// Edges (u, v), u < v, are taken in the order of u and its edge slots; at
+// each edge the branch that takes it (when both ends have room and they do
+// not end one path) is searched before the one that leaves it; a branch is
+// cut when the edges taken plus the most still reachable -- half the sum over
+// triangles of min(room, undecided edges) -- cannot beat the best so far.
+// Every call counts one node; past node_limit the search stops.
+struct CoverSearch {
+  StripScratch &s;
+  uint32_t T, n_edges, nodes = 0, node_limit, chosen = 0, best;
+  bool stopped = false, improved = false;
+
+  uint32_t reachable() const {
+    uint32_t sum = 0;
+    for (uint32_t x = 0; x < T; x++) sum += std::min<uint32_t>(s.rem[x], 2u - s.deg[x]);
+    return sum / 2;
+  }
+
+  void run(uint32_t i) {
+    if (stopped) return;
+    if (++nodes > node_limit) {
+      stopped = true;
+      return;
+    }
+    if (chosen > best) {
+      best = chosen;
+      improved = true;
+      std::copy(s.sel.begin(), s.sel.begin() + n_edges, s.best_sel.begin());
+    }
+    if (i == n_edges || chosen + reachable() <= best) return;
+    const uint32_t u = s.eu[i], v = s.ev[i];
+    s.rem[u]--;
+    s.rem[v]--;
+    if (s.deg[u] < 2 && s.deg[v] < 2 && s.end_of[u] != v) {
+      const uint32_t a = s.end_of[u], b = s.end_of[v];  // joined path: a .. u - v .. b
+      s.deg[u]++;
+      s.deg[v]++;
+      s.end_of[a] = b;
+      s.end_of[b] = a;
+      chosen++;
+      s.sel[i] = 1;
+      run(i + 1);
+      s.sel[i] = 0;
+      chosen--;
+      s.end_of[a] = u;
+      s.end_of[b] = v;
+      s.end_of[u] = a;
+      s.end_of[v] = b;
+      s.deg[u]--;
+      s.deg[v]--;
+    }
+    run(i + 1);
+    s.rem[u]++;
+    s.rem[v]++;
+  }
+};
+
+// Strips of the chosen edges in s.best_sel: from every path end (at most one
+// chosen edge) in list order not yet emitted, the path walked to its other
+// end, into s.order / s.lens.  Returns the number of strips (0 if some
+// triangle was not reached).
+uint32_t chosen_paths(StripScratch &s, uint32_t T, uint32_t n_edges) {
+  s.chosen_nb.assign(2 * (size_t)T, -1);
+  for (uint32_t i = 0; i < n_edges; i++) {
+    if (!s.best_sel[i]) continue;
+    const uint32_t u = s.eu[i], v = s.ev[i];
+    s.chosen_nb[2 * u + (s.chosen_nb[2 * u] >= 0 ? 1 : 0)] = (int32_t)v;
+    s.chosen_nb[2 * v + (s.chosen_nb[2 * v] >= 0 ? 1 : 0)] = (int32_t)u;
+  }
+  std::fill(s.visited.begin(), s.visited.begin() + T, 0);
+  uint32_t n_order = 0, n_strips = 0;
+  for (uint32_t t = 0; t < T; t++) {
+    if (s.visited[t] || (s.chosen_nb[2 * t] >= 0 && s.chosen_nb[2 * t + 1] >= 0)) continue;
+    uint32_t len = 0;
+    int32_t prev = -1, cur = (int32_t)t;
+    while (cur >= 0) {
+      s.visited[cur] = 1;
+      s.order[n_order++] = (uint32_t)cur;
+      len++;
+      int32_t nxt = s.chosen_nb[2 * cur] != prev ? s.chosen_nb[2 * cur] : s.chosen_nb[2 * cur + 1];
+      if (nxt >= 0 && s.visited[nxt]) nxt = -1;
+      prev = cur;
+      cur = nxt;
+    }
+    s.lens[n_strips++] = len;
+  }
+  return n_order == T ? n_strips : 0;
+}
+}  // namespace
+
 void build_strip(const uint32_t *tri, const uint32_t *ids, uint32_t T, StripScratch &s,
-                 StripOut &out) {
-  auto vert = [&](uint32_t t, uint32_t i) { return tri[3 * (size_t)ids[t] + (i % 3)]; };
+                 StripOut &out, uint32_t search_nodes, const uint32_t *list_corners) {
+  auto vert = [&](uint32_t t, uint32_t i) {
+    return list_corners ? list_corners[3 * (size_t)t + (i % 3)] : tri[3 * (size_t)ids[t] + (i % 3)];
+  };
   // directed edges t*3+e, sorted by (x, y, position) of edge x -> y
   s.keys.resize(3 * (size_t)T);
   for (uint32_t i = 0; i < 3 * T; i++) s.keys[i] = i;
@@ -180,6 +274,41 @@ void build_strip(const uint32_t *tri, const uint32_t *ids, uint32_t T, StripScra
       best_strips = n_strips;
       std::copy(s.order.begin(), s.order.begin() + T, s.best_order.begin());
       std::copy(s.lens.begin(), s.lens.begin() + n_strips, s.best_lens.begin());
+    }
+  }
+
+  // optionally, fewer strips by the search, started from the greedy count
+  if (search_nodes && best_strips > 1) {
+    s.eu.clear();
+    s.ev.clear();
+    s.rem.assign(T, 0);
+    for (uint32_t t = 0; t < T; t++)
+      for (uint32_t e = 0; e < 3; e++) {
+        const int32_t j = s.adj[3 * t + e];
+        if (j > (int32_t)t) {
+          s.eu.push_back(t);
+          s.ev.push_back((uint32_t)j);
+          s.rem[t]++;
+          s.rem[j]++;
+        }
+      }
+    const uint32_t n_edges = (uint32_t)s.eu.size();
+    s.deg.assign(T, 0);
+    s.end_of.resize(T);
+    for (uint32_t t = 0; t < T; t++) s.end_of[t] = t;
+    s.sel.assign(n_edges, 0);
+    s.best_sel.assign(n_edges, 0);
+    CoverSearch cs{s, T, n_edges};
+    cs.node_limit = search_nodes;
+    cs.best = T - best_strips;
+    cs.run(0);
+    if (cs.improved) {
+      const uint32_t n = chosen_paths(s, T, n_edges);
+      if (n && n == T - cs.best) {
+        best_strips = n;
+        std::copy(s.order.begin(), s.order.begin() + T, s.best_order.begin());
+        std::copy(s.lens.begin(), s.lens.begin() + n, s.best_lens.begin());
+      }
     }
   }
 

@@ -148,3 +148,42 @@ def test_argument_errors_are_synchronous():
         mc.mc_encode(m, np.zeros((3, 3), np.float32), 16, order=np.array([1], np.uint32))
     assert mc.mc_status_string(3) == "MC_ERR_CORRUPT"
     assert mc.mc_scratch_bytes() >= 12
+
+
+def _canon(t: np.ndarray) -> np.ndarray:
+    """Each triangle rotated so that its smallest index comes first (winding
+    kept), rows sorted."""
+    t = np.asarray(t, np.int64).reshape(-1, 3)
+    r = np.argmin(t, 1)
+    rot = np.stack([t[np.arange(len(t)), (r + k) % 3] for k in range(3)], 1)
+    return rot[np.lexsort(rot.T[::-1])]
+
+
+@pytest.mark.parametrize("name", ["sphere_64_126", "torus_128_128", "hf_mixed", "torus_64_126_plain_gts"])
+def test_strip_search_bytes_identical_and_round_trip(name):
+    """With the fewest-strips search on, both encoders still produce the same
+    bytes, never more restarts than the greedy strips, and every meshlet still
+    decodes to exactly its input triangles with their winding."""
+    mesh, lim, bits, mode, shuffle = CASES[name]
+    nodes = 50_000
+    m = mc.mc_meshletize(mesh.tris, mesh.n_verts, lim, mesh.tri_class, n_threads=4)
+    n = m.count
+    b = G.meshlet_bits(n, 9) if bits == "mixed" else bits
+    order = G.meshlet_permutation(n, 10) if shuffle else None
+    blob = mc.mc_encode(m, mesh.pos, b, mode, order, n_threads=4, strip_search_nodes=nodes)
+    greedy = mc.mc_encode(m, mesh.pos, b, mode, order, n_threads=4)
+    mtri, mstart, _ = O.meshletize(mesh.tris, mesh.n_verts, np.asarray(lim).reshape(-1), mesh.tri_class)
+    bb = b if np.ndim(b) else np.full(mstart.size - 1, b)
+    ob = O.encode(mesh.pos, mesh.tris, mtri, mstart, bb, mode, order, search_nodes=nodes)
+    a = blob.arrays()
+    assert np.array_equal(a["desc"], ob.desc)
+    assert np.array_equal(a["payload"], ob.payload)
+    s, g = blob.stats(), greedy.stats()
+    assert s["restarts"] == ob.stats["restarts"] <= g["restarts"]
+    assert s["restarts"] < g["restarts"]  # the search improves some meshlets here
+    loc, glob, _, _ = O.decode(ob, want_pos64=False)
+    vmap = ob.stats["vmap"].astype(np.int64)
+    tri = vmap[glob.astype(np.int64)]
+    keep = (tri[:, 0] != tri[:, 1]) & (tri[:, 1] != tri[:, 2]) & (tri[:, 0] != tri[:, 2])
+    assert np.array_equal(_canon(tri[keep]), _canon(mesh.tris))
+    print(f"\n{name}: restarts {g['restarts']} -> {s['restarts']} with {nodes} search nodes per meshlet")
