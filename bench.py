@@ -193,13 +193,16 @@ def _barrier(ws):
 
 
 def build_workload(cfg: int, rank: int, codec: str = "reuse", attrs: bool = False,
-                   cfg4_tris: int = 50_000_000):
+                   cfg4_tris: int = 50_000_000, strip_search: int = 0):
     from paper_2404_06359_gb300 import workloads as W
+    if strip_search and cfg != 2:
+        raise SystemExit("--strip-search applies to config 2")
     if cfg == 1:
         blob, meshes = W.cfg1()
         return blob, meshes, None
     if cfg == 2:
-        blob, meshes = W.cfg2(rank, plain_gts=codec == "gts", attrs=attrs)
+        blob, meshes = W.cfg2(rank, plain_gts=codec == "gts", attrs=attrs,
+                              strip_search_nodes=strip_search)
         return blob, meshes, None
     if cfg == 3:
         blob, meshes = W.cfg3(rank, plain_gts=codec == "gts")
@@ -550,8 +553,9 @@ def measure_decode(args, cfg, blob, ws, local, stream, flush, main=True):
     return rec, host
 
 
-def _config_dict(cfg, stats, codec="reuse", attrs=False, cfg4_tris=50_000_000, ws=1):
+def _config_dict(cfg, stats, codec="reuse", attrs=False, cfg4_tris=50_000_000, ws=1, strip_search=0):
     return {"workload": WORKLOADS[cfg] + (" [plain GTS connectivity]" if codec == "gts" else "")
+            + (f" [fewest-strips search, {strip_search} nodes per meshlet]" if strip_search else "")
             + (" [8-channel vertices: position, normal, texture coordinate; 32 B out]" if attrs else "")
             + (f" [reduced to >= {cfg4_tris} triangles]" if cfg == 4 and cfg4_tris != 50_000_000 else ""),
             "connectivity_bits_per_triangle": round(stats["conn_bits"] / stats["input_tris"], 3),
@@ -846,6 +850,8 @@ def main():
     ap.add_argument("--codec", choices=("reuse", "gts"), default="reuse",
                     help="connectivity encoding of configs 2/3: GTS-Reuse (default) or plain GTS "
                          "(one stored 8-bit entry per triangle)")
+    ap.add_argument("--strip-search", type=int, default=0, metavar="NODES",
+                    help="config 2 encoded with the fewest-strips search (node budget per meshlet)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
@@ -866,7 +872,8 @@ def main():
     if args.attrs and args.config != 2:
         raise SystemExit("--attrs applies to config 2")
     t_build = time.time()
-    blob, meshes, vps = build_workload(args.config, rank, args.codec, args.attrs, args.cfg4_tris)
+    blob, meshes, vps = build_workload(args.config, rank, args.codec, args.attrs, args.cfg4_tris,
+                                       args.strip_search)
     t_build = time.time() - t_build
     stats = blob.stats()
     stream = torch.cuda.Stream()
@@ -882,7 +889,8 @@ def main():
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec.pop("ms_per_step"),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32",
            "data": "synthetic",
-           "config": _config_dict(args.config, stats, args.codec, args.attrs, args.cfg4_tris, ws),
+           "config": _config_dict(args.config, stats, args.codec, args.attrs, args.cfg4_tris, ws,
+                                  args.strip_search),
            "l2_flush": {"bytes_written": flush_mb << 20, "l2_bytes": l2}}
     res.update(rec)
     res["build_s"] = round(t_build, 1)
@@ -895,7 +903,8 @@ def main():
         parity_ok = res["parity"]["mismatches"] == 0
         del smp
     del host
-    if args.config == 2 and not args.no_cfg3 and args.codec == "reuse" and not args.attrs:
+    if (args.config == 2 and not args.no_cfg3 and args.codec == "reuse" and not args.attrs
+            and not args.strip_search):
         res["cfg3"] = run_cfg3_record(args, ws, rank, local, stream, flush)
         if "parity" in res["cfg3"]:
             parity_ok = parity_ok and res["cfg3"]["parity"]["mismatches"] == 0

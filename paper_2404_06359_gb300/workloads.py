@@ -32,16 +32,18 @@ def _threads():
     return os.cpu_count() or 4
 
 
-def encode_meshes(meshes, limits=((64, 126),), pos_bits=16, reuse_mode=0, attrs=False):
+def encode_meshes(meshes, limits=((64, 126),), pos_bits=16, reuse_mode=0, attrs=False,
+                  strip_search_nodes: int = 0):
     """Encode each mesh (in parallel, one thread per mesh) and concatenate.
     attrs: also encode normals and texture coordinates (5 channels at 16
-    bits, the rest of an 8-channel attribute vector)."""
+    bits, the rest of an 8-channel attribute vector); strip_search_nodes:
+    node budget of the fewest-strips search per meshlet (0 = greedy strips)."""
     def enc(i):
         m = meshes[i]
         ml = mc.mc_meshletize(m.tris, m.n_verts, limits, m.tri_class, n_threads=1)
         at = G.vertex_attributes(m) if attrs else None
         return mc.mc_encode(ml, m.pos, pos_bits, reuse_mode, mesh_id=i, n_threads=1, attrs=at,
-                            attr_bits=16)
+                            attr_bits=16, strip_search_nodes=strip_search_nodes)
     with ThreadPoolExecutor(_threads()) as ex:
         blobs = list(ex.map(enc, range(len(meshes))))
     return mc.mc_blob_concat(blobs)
@@ -53,12 +55,13 @@ def cfg1():
     return mc.mc_encode(ml, mesh.pos, 16, 0), [mesh]
 
 
-def cfg2(rank: int = 0, plain_gts: bool = False, attrs: bool = False):
+def cfg2(rank: int = 0, plain_gts: bool = False, attrs: bool = False, strip_search_nodes: int = 0):
     """plain_gts: store every strip entry at 8 bits (Sec. 4.2) instead of the
     GTS-Reuse packing; attrs: 8-channel vertices (position, normal, texture
-    coordinate)."""
+    coordinate); strip_search_nodes: fewest-strips search budget per meshlet."""
     meshes = G.surface_batch(256, 10_000, 200_000, SEEDS[2] + 1000 * rank)
-    return encode_meshes(meshes, reuse_mode=2 if plain_gts else 0, attrs=attrs), meshes
+    return encode_meshes(meshes, reuse_mode=2 if plain_gts else 0, attrs=attrs,
+                         strip_search_nodes=strip_search_nodes), meshes
 
 
 def cfg3(rank: int = 0, total_tris: int = 50_000_000, plain_gts: bool = False):
