@@ -70,8 +70,8 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal, for the second fraction beside 
 # triangle slot and keyed by the hash of the kernel source it was taken on;
 # reported only while the sources match.
 NCU_TRAFFIC = {  # config -> (device-code hash, DRAM bytes per decoded triangle slot)
-    2: ("846363d9384b0863", (86.488064e6 + 328.722688e6) / 17124622),
-    4: ("61f54bf40e08143c", (114.16832e6 + 1030.18e6) / 21162408),
+    2: ("e07898ebcd09e527", (86620928 + 327980032) / 16932154),
+    4: ("83b7f018bda2bde9", (113230848 + 1032584704) / 20923636),
 }
 
 
