@@ -17,7 +17,8 @@
  *   - stop when the pick would exceed V~ vertices or T~ triangles.
  * A meshlet whose strip (restart degenerates included) is longer than T~ is
  * split into the first ceil(T/2) triangles of its strip order and the rest,
- * recursively (Sec. 4.2: "we must split the meshlet").
+ * recursively (Sec. 4.2: restart degenerates can push a meshlet past T~,
+ * which forces a split).
  */
 #include <stdlib.h>
 #include <string.h>
