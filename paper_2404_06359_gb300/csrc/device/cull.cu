@@ -208,8 +208,9 @@ __device__ __forceinline__ uint32_t grab_lookback(uint64_t *state, uint32_t g, u
   if (g == 0) return 0;
   uint32_t excl = 0;
   int64_t j = (int64_t)g - 1;
-  const long long limit = wait_cycles ? (long long)wait_cycles : kWaitCycles;
-  const long long t0 = clock64();
+  // elapsed cycles in 32 bits (the limit is below 2^32; unsigned differences survive the wrap)
+  const uint32_t limit = wait_cycles ? wait_cycles : (uint32_t)kWaitCycles;
+  const uint32_t t0 = (uint32_t)clock64();
   for (;;) {
     const int64_t idx = j - (int64_t)lane;
     const uint64_t v = idx >= 0 ? ld_relaxed_u64(state + idx) : kInc;  // before grab 0: prefix 0
@@ -219,7 +220,7 @@ __device__ __forceinline__ uint32_t grab_lookback(uint64_t *state, uint32_t g, u
     const uint32_t stop = inc_mask ? (uint32_t)__ffs(inc_mask) - 1u : 31u;  // lanes 0..stop count
     const uint32_t upto = stop == 31u ? kFull : ((2u << stop) - 1u);
     if (wait_mask & upto) {
-      if (__any_sync(kFull, clock64() - t0 > limit)) return 0xFFFFFFFFu;
+      if (__any_sync(kFull, (uint32_t)clock64() - t0 > limit)) return 0xFFFFFFFFu;
       continue;
     }
     excl += __reduce_add_sync(kFull, lane <= stop ? (uint32_t)v : 0u);

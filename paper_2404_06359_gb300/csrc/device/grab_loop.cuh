@@ -144,16 +144,25 @@ __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab,
       parity ^= 1u;
     }
     const uint32_t word = pre(m0, sdesc, cnt);
+    // the grab's header checks and staged ranges, one lane per meshlet
+    bool ok_l = false, in_l = false;
+    if (lane < cnt) {
+      const uint4 *sd = reinterpret_cast<const uint4 *>(sdesc) + 2 * lane;
+      const Desc d = with_attrs(unpack_desc(sd[0], sd[1]), a);
+      ok_l = header_ok(d, a);
+      const uint32_t padded16 = ((block_words(d) + 3) & ~3u) / 4;
+      in_l = d.off16 >= start16 && d.off16 - start16 + padded16 <= end16 - start16;
+    }
+    const uint32_t ok_mask = __ballot_sync(kFull, ok_l), in_mask = __ballot_sync(kFull, in_l);
     for (uint32_t j = 0; j < cnt; j++) {
       const uint4 *sd = reinterpret_cast<const uint4 *>(sdesc) + 2 * j;
       const Desc d = with_attrs(unpack_desc(sd[0], sd[1]), a);
-      if (!header_ok(d, a)) {
+      if (!((ok_mask >> j) & 1u)) {
         if (lane == 0) set_status(status, MC_ERR_CORRUPT);
         continue;
       }
-      const uint32_t padded16 = ((block_words(d) + 3) & ~3u) / 4;
       const uint32_t *sw;
-      if (staged && d.off16 >= start16 && d.off16 - start16 + padded16 <= end16 - start16) {
+      if (staged && ((in_mask >> j) & 1u)) {
         sw = spay + 4 * (d.off16 - start16);
       } else {
         staged = false;  // spay is reused meshlet by meshlet from here on
