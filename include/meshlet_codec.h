@@ -261,7 +261,9 @@ typedef struct {
   const mc_desc *desc;
   const uint8_t *payload;
   const mc_grid *grids;
-  uint32_t n_meshlets;
+  uint32_t n_meshlets;      /* at most 2^31 (the persistent kernels' 32-bit
+                             * work counter needs headroom); more is
+                             * MC_ERR_LIMIT from every device call */
   uint32_t n_grids;
   uint64_t payload_bytes;
   uint64_t total_tris;  /* capacity of the outputs, triangles (sum of T') */

@@ -58,6 +58,7 @@ mc_status check_batch(const mc_device_batch *b) {
   if (b->max_block_words == 0 || b->max_block_words > 2 * 8 + 64 + 768 + 1280 + 4)
     return MC_ERR_INVALID_ARG;
   if (b->payload_bytes % 16) return MC_ERR_INVALID_ARG;
+  if (b->n_meshlets > (1u << 31)) return MC_ERR_LIMIT;  // headroom of the 32-bit work counter
   if (b->max_verts > 256 || (b->max_verts && b->max_verts < 3)) return MC_ERR_INVALID_ARG;
   if (b->cones && !aligned(b->cones, 16)) return MC_ERR_INVALID_ARG;
   if (b->n_attr > 5 || (b->n_attr && (b->attr_bits < 1 || b->attr_bits > 32)))

@@ -57,3 +57,17 @@ def test_ordered_cull_state_buffer_checked_on_the_host():
     assert lib.mc_decode_cull_ordered(C.byref(b), P(0x400000), P(0x500000), P(0x600000),
                                       P(0x700000), P(0x800000), P(0x900000), None, None,
                                       None) == BAD
+
+
+def test_meshlet_count_limit_refused_on_the_host():
+    """More than 2^31 meshlets is MC_ERR_LIMIT (2) from the batch decoders and the culls."""
+    lib = mc.lib()
+    bb = _batch()
+    bb.n_meshlets = (1 << 31) + 1
+    out = (P(0x400000), P(0x500000), P(0x600000), P(0x700000), P(0x800000))
+    assert lib.mc_decode_batch(C.byref(bb), *out, None, None) == 2
+    assert lib.mc_decode_cull_views(C.byref(bb), P(0x400000), 2, P(0x500000), 300, P(0x600000),
+                                    P(0x700000), P(0x800000), P(0x900000), None, None) == 2
+    bb.n_meshlets = 1 << 31  # the bound itself passes the count check (then fails on alignment)
+    assert lib.mc_decode_batch(C.byref(bb), P(0x400000), P(0x500000), P(0x600000), P(0x700000),
+                               P(0x800004), None, None) == BAD
