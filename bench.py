@@ -70,8 +70,8 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal, for the second fraction beside 
 # triangle slot and keyed by the hash of the kernel source it was taken on;
 # reported only while the sources match.
 NCU_TRAFFIC = {  # config -> (device-code hash, DRAM bytes per decoded triangle slot)
-    2: ("e07898ebcd09e527", (86620928 + 327980032) / 16932154),
-    4: ("83b7f018bda2bde9", (113230848 + 1032584704) / 20923636),
+    2: ("a01da51e95d27a70", (86594560 + 327884800) / 16932154),
+    4: ("c104161449ea4548", (113344000 + 1033006080) / 20923636),
 }
 
 
