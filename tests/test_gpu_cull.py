@@ -9,7 +9,7 @@ import pytest
 import oracle as O
 from paper_2404_06359_gb300 import codec as mc
 from paper_2404_06359_gb300 import meshgen as G
-from tests.gpu_util import device_batch_from_oracle
+from tests.gpu_util import assert_same_decode, device_batch_from_oracle, run_decode
 
 pytestmark = pytest.mark.gpu
 
@@ -393,3 +393,37 @@ def test_corrupt_stream_flagged_by_checked_cull_kernels():
         assert int(st.item()) & (1 << mc.MC_ERR_CORRUPT), form
         assert int(scratch.abs().sum()) == 0, form
 
+
+
+@pytest.mark.parametrize("grab", [1, 2, 5])
+def test_fixed_grab_rounds_on_a_small_grid(scene, grab):
+    """One warp per CTA and one CTA per SM make the grid's warps few enough
+    for this batch to run the grab loop's fixed rounds (warp w takes grabs w,
+    w + W, ... for 3/4 of an even split's rounds), then the queue's tail and,
+    for grabs of 5 (1992 meshlets), a partial last grab: the batch decode, the one-view cull
+    and the multi-view cull still give the oracle's results."""
+    blob, vps = scene
+    n_grabs = -(-blob.fields()["V"].size // grab)
+    assert n_grabs // (152 * 1) * 3 // 4 >= 1  # the fixed rounds run on a 152-SM part
+    tuning = {"warps_per_cta": 1, "ctas_per_sm": 1, "meshlets_per_grab": grab}
+    db = device_batch_from_oracle(blob)
+    assert_same_decode(run_decode(db, "batch", tuning), O.decode(blob), f"batch grab {grab}")
+    f = blob.fields()
+    ref_pos = O.decode(blob)[2]
+    for vp in vps[:2]:
+        ref_tri, ref_cpos, passed = O.decode_cull(blob, vp)
+        tri, pos, st = _run(db, vp, tuning)
+        assert st == 0
+        assert np.array_equal(_sorted_rows(tri), _sorted_rows(ref_tri))
+        vm = np.repeat(passed, f["V"].astype(np.int64)).astype(bool)
+        assert np.array_equal(pos.reshape(-1, 3)[vm].view(np.uint32), ref_cpos[vm].view(np.uint32))
+    views = _views_of(blob, vps, 3)
+    outs, pos, st = _run_views(db, views, tuning)
+    assert st == 0
+    any_pass = np.zeros(f["V"].size, bool)
+    for v in range(3):
+        ref, _, passed = O.decode_cull(blob, views[v])
+        assert np.array_equal(_sorted_rows(outs[v]), _sorted_rows(ref)), v
+        any_pass |= passed.astype(bool)
+    vm = np.repeat(any_pass, f["V"].astype(np.int64))
+    assert np.array_equal(pos.reshape(-1, 3)[vm].view(np.uint32), ref_pos[vm].view(np.uint32))
