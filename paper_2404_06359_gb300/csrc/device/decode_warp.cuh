@@ -393,11 +393,27 @@ __device__ __forceinline__ void vertex_stage_full(const Desc &d, const Grid &g, 
   __syncwarp();
 }
 
+// Positions of one staged meshlet by the general path: q from vertex_q,
+// dequantised with the 2^24 split where needed.
+template <bool B16>
+__device__ __forceinline__ void positions_general(const Desc &d, const Grid &g, const uint32_t *pw,
+                                                  float *op, uint32_t lane) {
+  const uint32_t vpasses = (d.V + 31) >> 5;
+  uint32_t v = lane;
+  for (uint32_t i = 0; i < vpasses; i++, v += 32, op += 96) {
+    uint32_t q[3];
+    vertex_q<B16>(pw, min(v, d.V - 1), d.b, q);  // idle lanes re-read the last vertex
+    stg3_f32_if(op, dequant(d.L[0] + q[0], g.G[0], g.D[0]), dequant(d.L[1] + q[1], g.G[1], g.D[1]),
+                dequant(d.L[2] + q[2], g.G[2], g.D[2]), v < d.V);
+  }
+}
+
 // Full decode of one staged meshlet into the batch outputs: the strip walk
 // of walk_triangles (same arithmetic) written out flat, with predicated
 // stores and per-lane output pointers advanced by one word of triangles per
-// pass.
-template <bool CHECKED, bool B16, int RM, bool VTX>
+// pass.  The walk does not depend on the position width, so one build per
+// reuse form serves every b (the vertex stage branches on b = 16).
+template <bool CHECKED, int RM, bool VTX>
 __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, const uint32_t *sw,
                                               uint8_t *sI, uint32_t lane, uint8_t *out_local,
                                               uint32_t *out_global, float *out_pos,
@@ -455,14 +471,17 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
   }
   if (CHECKED && __any_sync(kFull, bad)) return false;
   if (VTX) {
-    vertex_stage_full<B16>(d, g, sw, sa, n_attr, attr_bits, lane, out_pos);
+    if (d.b == 16)
+      vertex_stage_full<true>(d, g, sw, sa, n_attr, attr_bits, lane, out_pos);
+    else
+      vertex_stage_full<false>(d, g, sw, sa, n_attr, attr_bits, lane, out_pos);
     return true;
   }
   // positions
   const uint32_t *pw = sw + conn_words(d);
   float *op = out_pos + 3ull * (d.vbase + lane);
-  const uint32_t vpasses = (d.V + 31) >> 5;
-  if (B16 && small_coords(d)) {
+  if (d.b == 16 && small_coords(d)) {
+    const uint32_t vpasses = (d.V + 31) >> 5;
     uint32_t a = smem_addr(pw) + 6 * lane;
     uint32_t v = lane;
     for (uint32_t i = 0; i < vpasses; i++, v += 32, a += 192, op += 96) {
@@ -471,14 +490,10 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
       const float z = dequant_small(d.L[2] + lds_u16(a + 4), g.G[2], g.D[2]);
       stg3_f32_if(op, x, y, z, v < d.V);
     }
+  } else if (d.b == 16) {
+    positions_general<true>(d, g, pw, op, lane);
   } else {
-    uint32_t v = lane;
-    for (uint32_t i = 0; i < vpasses; i++, v += 32, op += 96) {
-      uint32_t q[3];
-      vertex_q<B16>(pw, min(v, d.V - 1), d.b, q);  // idle lanes re-read the last vertex
-      stg3_f32_if(op, dequant(d.L[0] + q[0], g.G[0], g.D[0]), dequant(d.L[1] + q[1], g.G[1], g.D[1]),
-                  dequant(d.L[2] + q[2], g.G[2], g.D[2]), v < d.V);
-    }
+    positions_general<false>(d, g, pw, op, lane);
   }
   __syncwarp();
   return true;
@@ -621,16 +636,11 @@ __device__ __forceinline__ bool decode_dispatch(const Desc &d, const Grid &g, co
                                                 uint32_t *out_global, float *out_pos,
                                                 const uint32_t *sa = nullptr, uint32_t n_attr = 0,
                                                 uint32_t attr_bits = 0) {
-#define MC_DEC(B, R) \
-  decode_staged<CHECKED, B, R, VTX>(d, g, sw, sI, lane, out_local, out_global, out_pos, sa, n_attr, attr_bits)
-  if (d.b == 16) {
-    if (d.w == 8) return MC_DEC(true, kReuseBytes);
-    if (d.w == 0) return MC_DEC(true, kPlainGts);
-    return MC_DEC(true, kReuseBits);
-  }
-  if (d.w == 8) return MC_DEC(false, kReuseBytes);
-  if (d.w == 0) return MC_DEC(false, kPlainGts);
-  return MC_DEC(false, kReuseBits);
+#define MC_DEC(R) \
+  decode_staged<CHECKED, R, VTX>(d, g, sw, sI, lane, out_local, out_global, out_pos, sa, n_attr, attr_bits)
+  if (d.w == 8) return MC_DEC(kReuseBytes);
+  if (d.w == 0) return MC_DEC(kPlainGts);
+  return MC_DEC(kReuseBits);
 #undef MC_DEC
 }
 
