@@ -70,8 +70,8 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal, for the second fraction beside 
 # triangle slot and keyed by the hash of the kernel source it was taken on;
 # reported only while the sources match.
 NCU_TRAFFIC = {  # config -> (device-code hash, DRAM bytes per decoded triangle slot)
-    2: ("5d45eac54066b32f", (86756096 + 327848960) / 16932154),
-    4: ("30e1fa39c5f3eaf8", (116967168 + 1046032896) / 20923636),
+    2: ("828a526ec602fbdf", (86794752 + 328082688) / 16932154),
+    4: ("9316ed5563b285d2", (116658176 + 1046313472) / 20923636),
 }
 
 
