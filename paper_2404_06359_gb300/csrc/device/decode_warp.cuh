@@ -334,6 +334,20 @@ __device__ __forceinline__ void vertex_q(const uint32_t *pw, uint32_t v, uint32_
     q[2] = extract(pw, bit + 2 * b, b);
   }
 }
+// vertex_q for b <= 21: the vertex's 3b bits read as one 64-bit window of
+// three words (two funnel shifts) instead of three two-word extractions.
+__device__ __forceinline__ void vertex_q_window(const uint32_t *pw, uint32_t v, uint32_t b,
+                                                uint32_t q[3]) {
+  const uint32_t bit = 3 * v * b;
+  const uint32_t i = bit >> 5, sh = bit & 31u;
+  const uint32_t lo = __funnelshift_r(pw[i], pw[i + 1], sh);
+  const uint32_t hi = __funnelshift_r(pw[i + 1], pw[i + 2], sh);
+  const unsigned long long win = ((unsigned long long)hi << 32) | lo;
+  const uint32_t m = (1u << b) - 1u;
+  q[0] = lo & m;
+  q[1] = (uint32_t)(win >> b) & m;
+  q[2] = (uint32_t)(win >> (2 * b)) & m;
+}
 
 // true when every grid coordinate of the meshlet is below 2^24
 __device__ __forceinline__ bool small_coords(const Desc &d) {
@@ -394,17 +408,26 @@ __device__ __forceinline__ void vertex_stage_full(const Desc &d, const Grid &g, 
 }
 
 // Positions of one staged meshlet by the general path: q from vertex_q,
-// dequantised with the 2^24 split where needed.
-template <bool B16>
+// dequantised with the 2^24 split where needed (SMALL: every coordinate of
+// the meshlet is below 2^24, so the split never applies).
+template <bool B16, bool SMALL>
 __device__ __forceinline__ void positions_general(const Desc &d, const Grid &g, const uint32_t *pw,
                                                   float *op, uint32_t lane) {
   const uint32_t vpasses = (d.V + 31) >> 5;
   uint32_t v = lane;
   for (uint32_t i = 0; i < vpasses; i++, v += 32, op += 96) {
     uint32_t q[3];
-    vertex_q<B16>(pw, min(v, d.V - 1), d.b, q);  // idle lanes re-read the last vertex
-    stg3_f32_if(op, dequant(d.L[0] + q[0], g.G[0], g.D[0]), dequant(d.L[1] + q[1], g.G[1], g.D[1]),
-                dequant(d.L[2] + q[2], g.G[2], g.D[2]), v < d.V);
+    if (!B16 && SMALL)  // SMALL implies b <= 24; the window takes b <= 21
+      d.b <= 21 ? vertex_q_window(pw, min(v, d.V - 1), d.b, q) : vertex_q<false>(pw, min(v, d.V - 1), d.b, q);
+    else
+      vertex_q<B16>(pw, min(v, d.V - 1), d.b, q);  // idle lanes re-read the last vertex
+    if (SMALL)
+      stg3_f32_if(op, dequant_small(d.L[0] + q[0], g.G[0], g.D[0]),
+                  dequant_small(d.L[1] + q[1], g.G[1], g.D[1]),
+                  dequant_small(d.L[2] + q[2], g.G[2], g.D[2]), v < d.V);
+    else
+      stg3_f32_if(op, dequant(d.L[0] + q[0], g.G[0], g.D[0]), dequant(d.L[1] + q[1], g.G[1], g.D[1]),
+                  dequant(d.L[2] + q[2], g.G[2], g.D[2]), v < d.V);
   }
 }
 
@@ -490,10 +513,12 @@ __device__ __forceinline__ bool decode_staged(const Desc &d, const Grid &g, cons
       const float z = dequant_small(d.L[2] + lds_u16(a + 4), g.G[2], g.D[2]);
       stg3_f32_if(op, x, y, z, v < d.V);
     }
+  } else if (small_coords(d)) {  // b != 16
+    positions_general<false, true>(d, g, pw, op, lane);
   } else if (d.b == 16) {
-    positions_general<true>(d, g, pw, op, lane);
+    positions_general<true, false>(d, g, pw, op, lane);
   } else {
-    positions_general<false>(d, g, pw, op, lane);
+    positions_general<false, false>(d, g, pw, op, lane);
   }
   __syncwarp();
   return true;
