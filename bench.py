@@ -70,8 +70,8 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal, for the second fraction beside 
 # triangle slot and keyed by the hash of the kernel source it was taken on;
 # reported only while the sources match.
 NCU_TRAFFIC = {  # config -> (device-code hash, DRAM bytes per decoded triangle slot)
-    2: ("828a526ec602fbdf", (86794752 + 328082688) / 16932154),
-    4: ("9316ed5563b285d2", (116658176 + 1046313472) / 20923636),
+    2: ("398883ae383f17fe", (86807552 + 328218624) / 16932154),
+    4: ("2579e04225f430ba", (117057792 + 1046112256) / 20923636),
 }
 
 
