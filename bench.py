@@ -70,8 +70,8 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal, for the second fraction beside 
 # triangle slot and keyed by the hash of the kernel source it was taken on;
 # reported only while the sources match.
 NCU_TRAFFIC = {  # config -> (device-code hash, DRAM bytes per decoded triangle slot)
-    2: ("398883ae383f17fe", (86807552 + 328218624) / 16932154),
-    4: ("2579e04225f430ba", (117057792 + 1046112256) / 20923636),
+    2: ("aef35e5977e78b5f", (86807552 + 328218624) / 16932154),
+    4: ("20611629a748ae90", (117057792 + 1046112256) / 20923636),
 }
 
 
@@ -79,15 +79,20 @@ def _kernel_hash(config: int):
     """Hash of the device code the config's dominant kernel is built from: the
     shared device headers and its kernel file (kernels.cu for the decoders,
     cull_views.cu with the cull helpers for the multi-view cull), each up to
-    its host launchers."""
+    its host launchers, with comments and whitespace left out (an edit of a
+    comment leaves the captured counters valid)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     files = ["cull_views.cu", "cull_common.cuh"] if config == 4 else ["kernels.cu"]
     for p in ["paper_2404_06359_gb300/csrc/device/" + f
               for f in files + ["decode_warp.cuh", "grab_loop.cuh"]]:
         with open(os.path.join(ROOT, p), "rb") as f:
             b = f.read()
-        h.update(b.split(b"// ------------------------------------------------------------- launchers")[0])
+        b = b.split(b"// ------------------------------------------------------------- launchers")[0]
+        b = re.sub(rb"/\*.*?\*/", b" ", b, flags=re.S)
+        b = re.sub(rb"//[^\n]*", b" ", b)
+        h.update(re.sub(rb"\s+", b" ", b).strip())
     return h.hexdigest()[:16]
 
 
