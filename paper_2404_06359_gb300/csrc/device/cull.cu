@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(MAX_THREADS) decode_cull_kernel(BatchArgs a, c
     cull_write_at(surv + h * half_cap, svb + h * half_src, n, lane, tri_out, excl);
     if (lane == 0 && m0 + per_grab >= a.n_meshlets) *tri_count = excl + n;
   };
-  grab_loop<!ORDERED>(a, per_grab, base, lane, scratch + kQueue, status,
+  grab_loop<ORDERED ? 0 : 1>(a, per_grab, base, lane, scratch + kQueue, status,
                 [&](uint32_t m0, const uint32_t *sdesc, uint32_t cnt) {
                   return grab_outside(a, m0, sdesc, cnt, s_M, cones, s_eye, eye_ok, lane);
                 },

@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(MAX_THREADS) decode_cull_views_kernel(
         cones && view_eye(s_M + 16 * threadIdx.x, s_eye + 4 * threadIdx.x) ? 1.0f : 0.0f;
   __syncthreads();
   const uint32_t all = (1u << n_views) - 1u;
-  grab_loop<true>(a, per_grab, base, lane, scratch + kQueue, status,
+  grab_loop<1>(a, per_grab, base, lane, scratch + kQueue, status,
             [&](uint32_t m0, const uint32_t *sdesc, uint32_t cnt) {
               return grab_outside_views(a, m0, sdesc, cnt, s_M, s_eye, n_views, cones, lane);
             },

@@ -70,9 +70,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 
 // Shared-memory layout of the loop (bytes, per warp): the grab's descriptors
 // and the next one, the mbarrier (16 bytes), then the payload blocks of a
-// grab and the over-read slack.
-__host__ __device__ inline uint32_t grab_loop_bytes(uint32_t max_block_words, uint32_t per_grab) {
+// grab and the over-read slack, then a second descriptor buffer with its
+// mbarrier (the next fixed grab's descriptors, fetched while this grab
+// decodes).
+__host__ __device__ inline uint32_t grab_desc_offset(uint32_t max_block_words, uint32_t per_grab) {
   return 32 * (per_grab + 1) + 16 + 4 * (per_grab * ((max_block_words + 3) & ~3u) + kSlackWords);
+}
+__host__ __device__ inline uint32_t grab_loop_bytes(uint32_t max_block_words, uint32_t per_grab) {
+  return grab_desc_offset(max_block_words, per_grab) + 32 * (per_grab + 1) + 16;
 }
 
 // Runs the warp's share of the work queue.  Per grab, pre(m0, sdesc, cnt) is
@@ -93,31 +98,40 @@ struct NoPost {
   __device__ __forceinline__ void operator()(uint32_t, uint32_t) const {}
 };
 //
+// MODE 0: every grab from the queue (the ordered cull, whose grabs are taken
+// in increasing order); 1: STATIC; 2: STATIC, and each fixed grab's
+// descriptors are fetched into the second buffer while the grab before it
+// decodes (the batch decoder; in the culls the extra state costs registers).
+//
 // STATIC: the first rounds take no atomic.  Warp w of the grid's W warps
 // takes grabs w, w + W, w + 2W, ... for R rounds, R = 3/4 of the rounds an
 // even split of the batch's grabs would need; the queue then hands out the
 // grabs from R W on, which absorbs the imbalance the fixed rounds leave.
 // (The atomic's cost depends on where the queue word lands in memory: with
 // every grab from the queue, one 50 M-triangle batch decoded 20-40 % slower
-// on some placements than on others.)  The ordered cull keeps every grab on
-// the queue, whose grabs are taken in increasing order.
-template <bool STATIC, class Pre, class Body, class Post = NoPost>
+// on some placements than on others.)
+template <int MODE, class Pre, class Body, class Post = NoPost>
 __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab, uint8_t *wbase,
                                           uint32_t lane, uint32_t *queue, uint32_t *status,
                                           Pre &&pre, Body &&body, Post &&post = Post{}) {
-  const uint32_t *sdesc = reinterpret_cast<const uint32_t *>(wbase);
-  const uint32_t bar = smem_addr(wbase + 32 * (per_grab + 1));
+  constexpr bool STATIC = MODE >= 1, PREFETCH = MODE == 2;
+  // descriptor buffer s (0, 1) at wbase + s * off1, its mbarrier after it
+  const uint32_t off1 = grab_desc_offset(a.max_block_words, per_grab);
+  const uint32_t bar0 = smem_addr(wbase + 32 * (per_grab + 1));
   uint32_t *spay = reinterpret_cast<uint32_t *>(wbase + 32 * (per_grab + 1) + 16);
   const uint32_t cap16 = (per_grab * ((a.max_block_words + 3) & ~3u)) / 4;
   const uint32_t bytes16 =
       a.payload_bytes / 16 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)(a.payload_bytes / 16);
   const uint32_t N = a.n_meshlets;
   if (lane == 0) {
-    mbar_init(bar, 1);
+    mbar_init(bar0, 1);
+    mbar_init(bar0 + off1, 1);
     fence_mbar_init();
   }
   __syncwarp();
-  uint32_t parity = 0;
+  uint32_t parity = 0;          // bit s: the next phase's parity of mbarrier s
+  uint32_t sel = 0;             // the buffer holding this grab's descriptors
+  uint32_t m_pre = 0xFFFFFFFFu;  // the grab whose descriptors were fetched ahead
   // STATIC: this warp's next fixed grab (meshlet index), the stride between
   // its fixed grabs and the end of the fixed range
   uint32_t m_fix = 0, stride = 0, fix_end = 0;
@@ -142,16 +156,18 @@ __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab,
     const uint32_t nd = cnt + (m0 + cnt < N ? 1u : 0u);
     fence_proxy_async();  // the previous grab's shared-memory accesses before the async writes
     __syncwarp();
-    if (lane == 0) {
+    const uint32_t *sdesc = reinterpret_cast<const uint32_t *>(wbase + sel * off1);
+    const uint32_t bar = bar0 + sel * off1;
+    if (!(PREFETCH && m0 == m_pre) && lane == 0) {  // not fetched ahead: fetch now
       mbar_expect_tx(bar, 32 * nd);
-      bulk_g2s(smem_addr(wbase), a.desc + m0, 32 * nd, bar);
+      bulk_g2s(smem_addr(sdesc), a.desc + m0, 32 * nd, bar);
     }
-    if (!mbar_wait(bar, parity)) {
+    if (!mbar_wait(bar, (parity >> sel) & 1u)) {
       if (lane == 0) set_status(status, MC_ERR_TIMEOUT);
-      mbar_wait(bar, parity);  // a second bounded wait for the copy in flight
+      mbar_wait(bar, (parity >> sel) & 1u);  // a second bounded wait for the copy in flight
       return;
     }
-    parity ^= 1u;
+    parity ^= 1u << sel;
     const uint32_t start16 = sdesc[0];
     const uint32_t end16 = m0 + cnt < N ? sdesc[8 * cnt] : bytes16;
     bool staged = end16 >= start16 && end16 - start16 <= cap16 && end16 <= bytes16;
@@ -160,12 +176,25 @@ __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab,
         mbar_expect_tx(bar, 16 * (end16 - start16));
         bulk_g2s(smem_addr(spay), a.payload + 16ull * start16, 16 * (end16 - start16), bar);
       }
-      if (!mbar_wait(bar, parity)) {
+      if (!mbar_wait(bar, (parity >> sel) & 1u)) {
         if (lane == 0) set_status(status, MC_ERR_TIMEOUT);
-        mbar_wait(bar, parity);  // a second bounded wait for the copy in flight
+        mbar_wait(bar, (parity >> sel) & 1u);  // a second bounded wait for the copy in flight
         return;
       }
-      parity ^= 1u;
+      parity ^= 1u << sel;
+    }
+    // the next fixed grab's descriptors into the other buffer, while this
+    // grab decodes (the warp takes that grab next, so none is left in flight)
+    m_pre = 0xFFFFFFFFu;
+    if (PREFETCH && m_fix < fix_end) {
+      const uint32_t cn = min(per_grab, N - m_fix);
+      const uint32_t ndn = cn + (m_fix + cn < N ? 1u : 0u);
+      if (lane == 0) {
+        mbar_expect_tx(bar0 + (sel ^ 1u) * off1, 32 * ndn);
+        bulk_g2s(smem_addr(wbase + (sel ^ 1u) * off1), a.desc + m_fix, 32 * ndn,
+                 bar0 + (sel ^ 1u) * off1);
+      }
+      m_pre = m_fix;
     }
     const uint32_t word = pre(m0, sdesc, cnt);
     // the grab's header checks and staged ranges, one lane per meshlet
@@ -199,6 +228,7 @@ __device__ __forceinline__ void grab_loop(const BatchArgs &a, uint32_t per_grab,
     }
     __syncwarp();
     post(m0, cnt);
+    if (PREFETCH && m_pre != 0xFFFFFFFFu) sel ^= 1u;
   }
 }
 

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(512) decode_batch_kernel(BatchArgs a, uint32_t
   uint8_t *base = smem + warp * smem_per_warp;
   uint8_t *sI = base + smem_per_warp - kStreamBytes;
   uint32_t *sa = reinterpret_cast<uint32_t *>(sI - 64);
-  grab_loop<true>(a, per_grab, base, lane, scratch + kQueue, status, NoPre{},
+  grab_loop<2>(a, per_grab, base, lane, scratch + kQueue, status, NoPre{},
             [&](const Desc &d, const uint32_t *sw, uint32_t, uint32_t, uint32_t m) {
               const Grid g = load_grid(a.grids + d.grid);
               if (VTX) {
