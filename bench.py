@@ -70,8 +70,8 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal, for the second fraction beside 
 # triangle slot and keyed by the hash of the kernel source it was taken on;
 # reported only while the sources match.
 NCU_TRAFFIC = {  # config -> (device-code hash, DRAM bytes per decoded triangle slot)
-    2: ("aef35e5977e78b5f", (86807552 + 328218624) / 16932154),
-    4: ("20611629a748ae90", (117057792 + 1046112256) / 20923636),
+    2: ("e25682d000018455", (86884608 + 327910912) / 16932154),
+    4: ("b09b78db4776337e", (113451008 + 1033029120) / 20923636),
 }
 
 
