@@ -1,13 +1,15 @@
 // Per-warp work loop of the persistent kernels.
 //
-// A warp takes `per_grab` consecutive meshlets at a time from a device work
-// queue (one atomicAdd per grab).  Consecutive meshlets have consecutive
+// A warp takes `per_grab` consecutive meshlets at a time: first in fixed
+// rounds (warp w of the grid's W warps takes grabs w, w + W, ...), then from
+// a device work queue (one atomicAdd per grab).  Consecutive meshlets have consecutive
 // payload blocks, so a grab is staged in shared memory by two bulk copies
 // (`cp.async.bulk` global -> shared, issued by lane 0 and completed on an
 // mbarrier): first its descriptors plus the next meshlet's (whose payload
 // offset ends the range), then its whole payload range.  The meshlets are
 // then handed one by one to the kernel's body.  A grab whose range does not
-// look contiguous falls back to staging meshlet by meshlet.
+// look contiguous falls back to staging meshlet by meshlet.  The batch
+// decoder fetches the next fixed grab's descriptors while a grab decodes.
 //
 // Every mbarrier wait is bounded (about a second): a wait that gives up sets
 // MC_ERR_TIMEOUT in the status word and ends the warp's work; the copy it
